@@ -1,0 +1,164 @@
+/*
+ * slrcount.h - C ABI of the GB300 exact #DNN-Verification counter.
+ *
+ * The counter follows the problem statement T = <N, P, Q> of Sec. 2.1: a ReLU
+ * network N, an input box P (a hyperrectangle) and an output property Q.
+ * It bounds every box of one branch-and-bound level at once (Sec. 3) with
+ * Symbolic Linear Relaxation (Sec. 2.2, Eq. 1; two linear equations per
+ * neuron, Sec. 3), checks the unsafe set against the output bounds (Sec. 3
+ * containment check), counts the unsafe volume of decided boxes and bisects
+ * the undecided ones (Alg. 1), down to a depth cap D.
+ *
+ * Conventions for every call:
+ *   - Every function returns an slr_status (0 = SLR_OK, negative = error); on
+ *     error slr_last_error() holds a one-line message.  No call aborts, throws
+ *     or exits across the ABI.
+ *   - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *   - Outputs are written into caller buffers.  Pointer arguments are host
+ *     pointers unless a call says otherwise.
+ *   - One context serves one problem on one GPU and is not thread-safe; use one
+ *     context per host thread.
+ *   - All device work runs on the context's CUDA stream; every call that
+ *     returns results synchronises that stream before returning.
+ */
+#ifndef SLRCOUNT_H
+#define SLRCOUNT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slr_ctx slr_ctx;
+
+typedef enum {
+    SLR_OK = 0,
+    SLR_EINVAL = -1,       /* bad argument: sizes, lo > hi, non-finite values, D out of range */
+    SLR_ENOMEM = -2,       /* device or host allocation failed */
+    SLR_ECUDA = -3,        /* a CUDA runtime call failed (message names it) */
+    SLR_ESTATE = -4,       /* call order: count/bounds before network, box and property are set */
+    SLR_EOVERFLOW = -5,    /* a level produced more boxes than frontier_cap */
+    SLR_ETIMEOUT = -6,     /* a bounded device wait gave up */
+    SLR_EUNSUPPORTED = -7  /* shape or option not supported by this build */
+} slr_status;
+
+/* Box classes (Sec. 3): the reachable set R of the box is inside the unsafe
+ * set Y (UNSAFE), disjoint from it (SAFE), or neither (UNDECIDED). */
+enum { SLR_SAFE = 0, SLR_UNSAFE = 1, SLR_UNDECIDED = 2 };
+
+/* Reading of Eq. 1 (Sec. 2.2).
+ * NEURIFY: the upper line uses the bounds (l_u, u_u) of the upper equation and
+ *   the lower slope those (l_l, u_l) of the lower equation (default).
+ * PAPER_LITERAL: one pair (l, u) = (min of Eq_l, max of Eq_u) serves both. */
+enum { SLR_RELAX_NEURIFY = 0, SLR_RELAX_PAPER_LITERAL = 1 };
+
+/* Arithmetic of the symbolic contraction U' = W+ U + W- L + b, L' = W+ L + W- U + b.
+ * FP32: IEEE FP32 FMA on the CUDA cores (the constant terms as float-float
+ *   pairs); every rounding is bounded a priori and the bounds are widened
+ *   outward by that amount, so every bound stays sound. */
+enum { SLR_PREC_FP32 = 0 };
+
+typedef struct {
+    int32_t precision;      /* SLR_PREC_*; default SLR_PREC_FP32 */
+    int32_t relax_mode;     /* SLR_RELAX_*; default SLR_RELAX_NEURIFY */
+    int32_t fp64_recheck;   /* 1: re-bound in FP64 the undecided boxes that the FP32
+                               bounds would decide without their widening; default 1 */
+    int32_t record_leaves;  /* 1: keep the leaves of the last count for slr_leaves(); default 0 */
+    int64_t frontier_cap;   /* most boxes one level may hold; default 1<<24 */
+    int64_t leaf_cap;       /* most leaves recorded when record_leaves; default 1<<22 */
+} slr_options;
+
+#define SLR_MAX_LEVELS 63
+
+/* Result of slr_count.  Volumes are exact integers in units of 2^-D of the root
+ * box volume; the violation rate lies in [unsafe_lo, unsafe_hi] / 2^D. */
+typedef struct {
+    uint64_t unsafe_lo;     /* volume of the boxes proved UNSAFE */
+    uint64_t unsafe_hi;     /* unsafe_lo + boxes still UNDECIDED at depth D */
+    uint64_t boxes;         /* boxes bounded over all levels */
+    uint64_t rechecked;     /* boxes re-bounded in FP64 */
+    uint64_t tie_leaves;    /* re-bounded boxes whose FP64 class still depends on its widening */
+    int32_t depth;          /* D */
+    int32_t levels;         /* levels evaluated (D + 1 unless the frontier emptied first) */
+    uint64_t level_boxes[SLR_MAX_LEVELS + 1];
+    uint64_t level_safe[SLR_MAX_LEVELS + 1];
+    uint64_t level_unsafe[SLR_MAX_LEVELS + 1];
+    uint64_t level_undecided[SLR_MAX_LEVELS + 1];
+    double device_ms;       /* device time of the count (CUDA events on the context stream) */
+} slr_result;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
+ * run on, or NULL for a stream the context creates and owns.  *out receives the
+ * context (NULL on error). */
+int slr_create(slr_ctx **out, int device, void *cuda_stream);
+
+/* Free every device and host resource of the context.  NULL is accepted. */
+int slr_destroy(slr_ctx *ctx);
+
+/* Default options (see slr_options). */
+void slr_default_options(slr_options *opt);
+
+/* Set options; takes effect at the next count or bounds call. */
+int slr_set_options(slr_ctx *ctx, const slr_options *opt);
+
+/* The network N (Sec. 2.1): K affine layers (1 <= K <= 16), widths[0..K] with
+ * widths[0] = d inputs and widths[K] outputs (each 1..1024).  W[k] points to a
+ * row-major widths[k+1] x widths[k] float32 matrix and b[k] to widths[k+1]
+ * float32 biases; ReLU follows every layer except the last.  All values must be
+ * finite.  Copied to the device. */
+int slr_load_network(slr_ctx *ctx, int K, const int32_t *widths,
+                     const float *const *W, const float *const *b);
+
+/* The input box P (Sec. 2.1): d float32 endpoints with lo[i] <= hi[i], finite. */
+int slr_set_box(slr_ctx *ctx, int d, const float *lo, const float *hi);
+
+/* The unsafe set Y, i.e. the negated postcondition Q (Sec. 3): an OR over
+ * n_clauses clauses, clause c being an AND over rows_per_clause[c] rows; row r
+ * holds when C[r] . y + e[r] >= 0 (> 0 if strict[r]).  C is row-major
+ * R x n_out float32 with R = sum(rows_per_clause) <= 64 and n_out equal to the
+ * network's output width.  e is float32[R], strict uint8[R]. */
+int slr_set_property(slr_ctx *ctx, int n_clauses, const int32_t *rows_per_clause,
+                     int n_out, const float *C, const float *e, const uint8_t *strict);
+
+/* Count to depth D (0 <= D <= 62): Alg. 1 level by level (Sec. 3), bisecting the
+ * widest side of each undecided box (ties to the lowest index).  An UNSAFE box
+ * at depth t adds 2^(D-t) to unsafe_lo; an UNDECIDED box at depth D adds 1 to
+ * unsafe_hi - unsafe_lo.  Needs network, box and property (SLR_ESTATE). */
+int slr_count(slr_ctx *ctx, int D, slr_result *out);
+
+/* Bound n boxes given by float32 endpoints box_lo/box_hi (n x d, row-major) and
+ * write, for each box, the SLR lower/upper bound of every property row
+ * (row_lo/row_hi, n x R), the rigorous bound E of the rounding error of that
+ * row (row_err, n x R) and the box class (cls, n bytes).  Any output may be
+ * NULL, but row_lo and row_hi go together.  `on_device` = 1 means every
+ * pointer is a device pointer (CUDA global memory of the context's device); 0
+ * means host memory.  row_lo/row_hi are sound for the float32 network: they
+ * are the FP32 SLR bounds widened outward by E, so row_lo + row_err and
+ * row_hi - row_err are the FP32 SLR bounds themselves.  No FP64 re-check is
+ * applied here.  Needs network and property (SLR_ESTATE); with host pointers
+ * lo > hi or non-finite endpoints give SLR_EINVAL. */
+int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi,
+               float *row_lo, float *row_hi, float *row_err, uint8_t *cls, int on_device);
+
+/* Leaves of the last slr_count when record_leaves was set: for each leaf its
+ * path code (bit t-1-j = half taken at split j, 1 = upper), depth and class.
+ * Leaves are the SAFE and UNSAFE boxes of every level and the UNDECIDED boxes of
+ * depth D, in no particular order.  Writes at most `cap` entries and sets *n to
+ * the total number recorded (SLR_EOVERFLOW if leaf_cap was exceeded). */
+int slr_leaves(slr_ctx *ctx, int64_t cap, uint64_t *codes, uint8_t *depth,
+               uint8_t *cls, int64_t *n);
+
+/* The split dimension of each of the first D levels of the last count (the
+ * widest-side schedule), D entries. */
+int slr_schedule(slr_ctx *ctx, int D, int32_t *dims);
+
+/* Message of the last failed call on this context ("" if none).  With a NULL
+ * context, the message of the last failed slr_create on this thread. */
+const char *slr_last_error(const slr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLRCOUNT_H */

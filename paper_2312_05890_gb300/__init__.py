@@ -1,0 +1,283 @@
+"""Python binding of libslrcount, the GB300 exact #DNN-Verification counter.
+
+The functions below carry the names of the C ABI in ``include/slrcount.h`` and
+only marshal arguments (numpy arrays or CUDA tensors in, numbers out); every
+step of the computation runs in the library's CUDA kernels.  ``Counter`` wraps
+one context for convenience.  There is no CPU fallback: when the shared library
+has not been built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libslrcount.so")
+
+SLR_OK = 0
+STATUS = {0: "SLR_OK", -1: "SLR_EINVAL", -2: "SLR_ENOMEM", -3: "SLR_ECUDA", -4: "SLR_ESTATE",
+          -5: "SLR_EOVERFLOW", -6: "SLR_ETIMEOUT", -7: "SLR_EUNSUPPORTED"}
+SAFE, UNSAFE, UNDECIDED = 0, 1, 2
+RELAX_NEURIFY, RELAX_PAPER_LITERAL = 0, 1
+PREC_FP32 = 0
+MAX_LEVELS = 63
+
+# Names the header declares (checked by the CPU test that loads the library).
+EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
+           "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
+           "slr_last_error")
+
+
+class SlrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class slr_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
+                ("fp64_recheck", ctypes.c_int32), ("record_leaves", ctypes.c_int32),
+                ("frontier_cap", ctypes.c_int64), ("leaf_cap", ctypes.c_int64)]
+
+
+_U64A = ctypes.c_uint64 * (MAX_LEVELS + 1)
+
+
+class slr_result(ctypes.Structure):
+    _fields_ = [("unsafe_lo", ctypes.c_uint64), ("unsafe_hi", ctypes.c_uint64), ("boxes", ctypes.c_uint64),
+                ("rechecked", ctypes.c_uint64), ("tie_leaves", ctypes.c_uint64), ("depth", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("level_boxes", _U64A), ("level_safe", _U64A),
+                ("level_unsafe", _U64A), ("level_undecided", _U64A), ("device_ms", ctypes.c_double)]
+
+    def to_dict(self):
+        n = self.depth + 1
+        return dict(unsafe_lo=int(self.unsafe_lo), unsafe_hi=int(self.unsafe_hi), boxes=int(self.boxes),
+                    rechecked=int(self.rechecked), tie_leaves=int(self.tie_leaves), depth=int(self.depth),
+                    levels=int(self.levels), device_ms=float(self.device_ms),
+                    level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
+                    level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
+
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"libslrcount.so not built at {path}; run paper_2312_05890_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "slr_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
+        "slr_destroy": (ctypes.c_int, [P]),
+        "slr_default_options": (None, [ctypes.POINTER(slr_options)]),
+        "slr_set_options": (ctypes.c_int, [P, ctypes.POINTER(slr_options)]),
+        "slr_load_network": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
+        "slr_set_box": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+        "slr_set_property": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, P, P, P]),
+        "slr_count": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
+        "slr_bounds": (ctypes.c_int, [P, i64, P, P, P, P, P, P, ctypes.c_int]),
+        "slr_leaves": (ctypes.c_int, [P, i64, P, P, P, ctypes.POINTER(i64)]),
+        "slr_schedule": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "slr_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _ = i32
+    _lib_handle = lib
+    return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(lib, ctx, rc):
+    if rc != SLR_OK:
+        raise SlrError(rc, lib.slr_last_error(ctx).decode())
+
+
+# ---------------------------------------------------------------------------
+# functions named as in the C ABI
+# ---------------------------------------------------------------------------
+
+def slr_create(device: int = 0, stream: int | None = None):
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    _check(lib, None, lib.slr_create(ctypes.byref(ctx), device, stream))
+    return ctx
+
+
+def slr_destroy(ctx):
+    lib = load_library()
+    _check(lib, ctx, lib.slr_destroy(ctx))
+
+
+def slr_default_options() -> slr_options:
+    o = slr_options()
+    load_library().slr_default_options(ctypes.byref(o))
+    return o
+
+
+def slr_set_options(ctx, opt: slr_options):
+    lib = load_library()
+    _check(lib, ctx, lib.slr_set_options(ctx, ctypes.byref(opt)))
+
+
+def slr_load_network(ctx, W, b):
+    lib = load_library()
+    Ws = [np.ascontiguousarray(w, dtype=np.float32) for w in W]
+    bs = [np.ascontiguousarray(x, dtype=np.float32).reshape(-1) for x in b]
+    K = len(Ws)
+    widths = np.array([Ws[0].shape[1]] + [w.shape[0] for w in Ws], dtype=np.int32)
+    wp = (ctypes.c_void_p * K)(*[w.ctypes.data for w in Ws])
+    bp = (ctypes.c_void_p * K)(*[x.ctypes.data for x in bs])
+    _check(lib, ctx, lib.slr_load_network(ctx, K, _ptr(widths), wp, bp))
+
+
+def slr_set_box(ctx, lo, hi):
+    lib = load_library()
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    _check(lib, ctx, lib.slr_set_box(ctx, int(lo.shape[0]), _ptr(lo), _ptr(hi)))
+
+
+def slr_set_property(ctx, rows_per_clause, C, e, strict):
+    lib = load_library()
+    rpc = np.ascontiguousarray(rows_per_clause, dtype=np.int32)
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    e = np.ascontiguousarray(e, dtype=np.float32)
+    st = np.ascontiguousarray(strict, dtype=np.uint8)
+    _check(lib, ctx, lib.slr_set_property(ctx, int(rpc.shape[0]), _ptr(rpc), int(C.shape[1]), _ptr(C), _ptr(e), _ptr(st)))
+
+
+def slr_count(ctx, D: int) -> dict:
+    lib = load_library()
+    res = slr_result()
+    rc = lib.slr_count(ctx, int(D), ctypes.byref(res))
+    _check(lib, ctx, rc)
+    return res.to_dict()
+
+
+def slr_bounds(ctx, box_lo, box_hi, R: int, want_rows=True, want_cls=True, want_err=False):
+    """Bounds of n boxes: (row_lo, row_hi, cls) or, with want_err, (row_lo, row_hi, cls, row_err).
+
+    numpy inputs use host memory; CUDA tensors (with .data_ptr) stay on the device.
+    """
+    lib = load_library()
+    if hasattr(box_lo, "data_ptr"):
+        import torch
+        n = int(box_lo.shape[0])
+        dev = box_lo.device
+        rl = torch.empty((n, R), dtype=torch.float32, device=dev) if want_rows else None
+        rh = torch.empty((n, R), dtype=torch.float32, device=dev) if want_rows else None
+        re_ = torch.empty((n, R), dtype=torch.float32, device=dev) if want_err else None
+        cl = torch.empty((n,), dtype=torch.uint8, device=dev) if want_cls else None
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        _check(lib, ctx, lib.slr_bounds(ctx, n, p(box_lo.contiguous()), p(box_hi.contiguous()), p(rl), p(rh),
+                                        p(re_), p(cl), 1))
+        return (rl, rh, cl, re_) if want_err else (rl, rh, cl)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float32)
+    hi = np.ascontiguousarray(box_hi, dtype=np.float32)
+    n = int(lo.shape[0])
+    rl = np.empty((n, R), dtype=np.float32) if want_rows else None
+    rh = np.empty((n, R), dtype=np.float32) if want_rows else None
+    re_ = np.empty((n, R), dtype=np.float32) if want_err else None
+    cl = np.empty((n,), dtype=np.uint8) if want_cls else None
+    q = lambda a: _ptr(a) if a is not None else None  # noqa: E731
+    _check(lib, ctx, lib.slr_bounds(ctx, n, _ptr(lo), _ptr(hi), q(rl), q(rh), q(re_), q(cl), 0))
+    return (rl, rh, cl, re_) if want_err else (rl, rh, cl)
+
+
+def slr_leaves(ctx, cap: int):
+    lib = load_library()
+    codes = np.empty(cap, dtype=np.uint64)
+    depth = np.empty(cap, dtype=np.uint8)
+    cls = np.empty(cap, dtype=np.uint8)
+    n = ctypes.c_int64()
+    _check(lib, ctx, lib.slr_leaves(ctx, cap, _ptr(codes), _ptr(depth), _ptr(cls), ctypes.byref(n)))
+    m = min(cap, n.value)
+    return codes[:m], depth[:m], cls[:m]
+
+
+def slr_schedule(ctx, D: int):
+    lib = load_library()
+    out = np.empty(D, dtype=np.int32)
+    _check(lib, ctx, lib.slr_schedule(ctx, D, _ptr(out)))
+    return out
+
+
+def slr_last_error(ctx) -> str:
+    return load_library().slr_last_error(ctx).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Counter:
+    """One counting context on one GPU: network, box, property, options."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.ctx = slr_create(device, stream)
+        self.R = None
+
+    def close(self):
+        if self.ctx is not None:
+            slr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def load_network(self, W, b):
+        slr_load_network(self.ctx, W, b)
+
+    def set_box(self, lo, hi):
+        slr_set_box(self.ctx, lo, hi)
+
+    def set_property(self, rows_per_clause, C, e, strict):
+        slr_set_property(self.ctx, rows_per_clause, C, e, strict)
+        self.R = int(np.asarray(e).shape[0])
+
+    def set_problem(self, problem):
+        """Load a workloads.Problem (network, box and property)."""
+        self.load_network(problem.net.W, problem.net.b)
+        self.set_box(problem.lo, problem.hi)
+        p = problem.prop
+        self.set_property(p.rows_per_clause, p.C, p.e, p.strict)
+
+    def set_options(self, **kw):
+        o = slr_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        slr_set_options(self.ctx, o)
+
+    def count(self, D: int) -> dict:
+        return slr_count(self.ctx, D)
+
+    def bounds(self, lo, hi, want_rows=True, want_cls=True, want_err=False):
+        return slr_bounds(self.ctx, lo, hi, self.R, want_rows, want_cls, want_err)
+
+    def leaves(self, cap: int = 1 << 22):
+        return slr_leaves(self.ctx, cap)
+
+    def schedule(self, D: int):
+        return slr_schedule(self.ctx, D)

@@ -1,0 +1,723 @@
+// C ABI of the SLR counter: context, validation, device copies of the
+// network and the level-by-level driver of the count (Alg. 1, Sec. 3).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "slrcount.h"
+#include "slr_kernels.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxSmem = 232448;   // 227 KB of dynamic shared memory per CTA
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+float round_up_to_float(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+template <typename Real>
+struct HostLayers {
+    // layer 0 row-major, layers >= 1 transposed, the last folded with the property
+    std::vector<std::vector<Real>> W;
+    std::vector<std::vector<Real>> b;
+    std::vector<Real> fold_err, fold_berr;
+};
+
+}  // namespace
+
+struct slr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    slr_options opt{};
+
+    int K = 0;
+    std::vector<int> widths;
+    std::vector<std::vector<float>> W, b;
+    std::vector<float> lo, hi;
+    int n_clauses = 0;
+    std::vector<int> rpc;
+    std::vector<float> C, e;
+    std::vector<uint8_t> strict;
+    bool has_net = false, has_box = false, has_prop = false;
+
+    bool dev_dirty = true;
+    void *net_buf = nullptr;
+    slr::NetParams<float> nf{};
+    slr::NetParams<double> nd{};
+    int T32 = 0, T64 = 0;
+    size_t smem32 = 0, smem64 = 0;
+    int grid32 = 0, grid64 = 0;
+
+    int64_t cap = 0, near_cap = 0;
+    uint64_t *codes[2] = {nullptr, nullptr};
+    uint8_t *cls = nullptr;
+    int64_t *near_list = nullptr;
+    slr::LevelCounters *ctr = nullptr;
+    unsigned int *status = nullptr;
+    double *root = nullptr;
+    unsigned long long *masks = nullptr;
+    int root_d = 0;
+
+    int64_t leaf_cap_alloc = 0;
+    uint64_t *leaf_codes = nullptr;
+    uint8_t *leaf_depth = nullptr, *leaf_cls = nullptr;
+    bool leaves_valid = false;
+    int64_t n_leaves = 0;
+    std::vector<int> sched;
+
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int sm_count = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    slr::LevelCounters *h_ctr = nullptr;
+    unsigned int *h_status = nullptr;
+    std::vector<unsigned char> h_stage;
+};
+
+namespace {
+
+int fail(slr_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(slr_ctx *ctx, cudaError_t e, const char *what) {
+    const int code = e == cudaErrorMemoryAllocation ? SLR_ENOMEM : SLR_ECUDA;
+    return fail(ctx, code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+bool finite_all(const float *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Fold the property rows into the last layer in float64 (Sec. 3 check on the
+// rows C y + e): W' = C W_K, b' = C b_K + e, with a bound on the float64
+// rounding error, then round to the working precision and add that rounding.
+template <typename Real>
+void build_layers(const slr_ctx *ctx, HostLayers<Real> &L) {
+    const int K = ctx->K;
+    const int R = (int)ctx->e.size();
+    const int n_out = ctx->widths[K];
+    const int n_prev = ctx->widths[K - 1];
+    const double g64 = (double)(n_out + 3) * std::ldexp(1.0, -52);
+    std::vector<double> Wf((size_t)R * n_prev), Wf_err((size_t)R * n_prev), bf(R), bf_err(R);
+    const std::vector<float> &WK = ctx->W[K - 1];
+    const std::vector<float> &bK = ctx->b[K - 1];
+    for (int r = 0; r < R; ++r) {
+        for (int i = 0; i < n_prev; ++i) {
+            double s = 0.0, a = 0.0;
+            for (int o = 0; o < n_out; ++o) {
+                const double c = ctx->C[(size_t)r * n_out + o];
+                const double w = WK[(size_t)o * n_prev + i];
+                s += c * w;
+                a += std::fabs(c * w);
+            }
+            Wf[(size_t)r * n_prev + i] = s;
+            Wf_err[(size_t)r * n_prev + i] = g64 * a;
+        }
+        double s = ctx->e[r], a = std::fabs((double)ctx->e[r]);
+        for (int o = 0; o < n_out; ++o) {
+            const double c = ctx->C[(size_t)r * n_out + o];
+            s += c * (double)bK[o];
+            a += std::fabs(c * (double)bK[o]);
+        }
+        bf[r] = s;
+        bf_err[r] = g64 * a;
+    }
+    L.W.assign(K, {});
+    L.b.assign(K, {});
+    for (int k = 0; k < K; ++k) {
+        const int ni = ctx->widths[k];
+        const bool last = k == K - 1;
+        const int no = last ? R : ctx->widths[k + 1];
+        std::vector<Real> &w = L.W[k];
+        w.resize((size_t)ni * no);
+        for (int p = 0; p < no; ++p) {
+            for (int i = 0; i < ni; ++i) {
+                const Real v = last ? (Real)Wf[(size_t)p * ni + i] : (Real)ctx->W[k][(size_t)p * ni + i];
+                if (k == 0) w[(size_t)p * ni + i] = v;       // row-major
+                else w[(size_t)i * no + p] = v;              // transposed
+            }
+        }
+        L.b[k].resize(no);
+        for (int p = 0; p < no; ++p) L.b[k][p] = last ? (Real)bf[p] : (Real)ctx->b[k][p];
+    }
+    L.fold_err.resize((size_t)R * n_prev);
+    L.fold_berr.resize(R);
+    for (size_t i = 0; i < (size_t)R * n_prev; ++i) {
+        const double rounded = (double)(Real)Wf[i];
+        const double tot = std::fabs(rounded - Wf[i]) + Wf_err[i];
+        L.fold_err[i] = sizeof(Real) == 4 ? (Real)round_up_to_float(tot * (1 + 1e-15)) : (Real)(tot * (1 + 1e-15));
+    }
+    for (int r = 0; r < R; ++r) {
+        const double rounded = (double)(Real)bf[r];
+        const double tot = std::fabs(rounded - bf[r]) + bf_err[r];
+        L.fold_berr[r] = sizeof(Real) == 4 ? (Real)round_up_to_float(tot * (1 + 1e-15)) : (Real)(tot * (1 + 1e-15));
+    }
+}
+
+template <typename Real>
+size_t layers_bytes(const HostLayers<Real> &L) {
+    size_t s = 0;
+    for (auto &w : L.W) s += align_up(w.size() * sizeof(Real));
+    for (auto &b : L.b) s += align_up(b.size() * sizeof(Real));
+    s += align_up(L.fold_err.size() * sizeof(Real)) + align_up(L.fold_berr.size() * sizeof(Real));
+    return s;
+}
+
+template <typename Real>
+void layout_params(slr_ctx *ctx, const HostLayers<Real> &L, unsigned char *dev, unsigned char *host,
+                   size_t &off, slr::NetParams<Real> &p) {
+    auto put = [&](const std::vector<Real> &v) -> const Real * {
+        const Real *dp = reinterpret_cast<const Real *>(dev + off);
+        std::memcpy(host + off, v.data(), v.size() * sizeof(Real));
+        off += align_up(v.size() * sizeof(Real));
+        return dp;
+    };
+    const int K = ctx->K;
+    std::memset(&p, 0, sizeof p);
+    p.K = K;
+    p.d = ctx->widths[0];
+    p.R = (int)ctx->e.size();
+    for (int k = 0; k < K; ++k) p.n[k] = ctx->widths[k];
+    p.n[K] = p.R;
+    int nmax = 0, nin = 0;
+    for (int k = 1; k <= K; ++k) nmax = std::max(nmax, p.n[k]);
+    for (int k = 1; k < K; ++k) nin = std::max(nin, p.n[k]);
+    p.n_max_pad = (nmax + 7) & ~7;
+    p.n_in_max = std::max(nin, 1);
+    p.W0 = put(L.W[0]);
+    for (int k = 1; k < K; ++k) p.Wt[k] = put(L.W[k]);
+    for (int k = 0; k < K; ++k) p.b[k] = put(L.b[k]);
+    p.fold_err = put(L.fold_err);
+    p.fold_berr = put(L.fold_berr);
+    p.n_clauses = ctx->n_clauses;
+    int end = 0;
+    for (int c = 0; c < ctx->n_clauses; ++c) {
+        end += ctx->rpc[c];
+        p.clause_end[c] = end;
+    }
+    for (int r = 0; r < p.R; ++r) p.strict[r] = ctx->strict[r];
+    p.relax_mode = ctx->opt.relax_mode;
+}
+
+// Pick the tile size with the most boxes resident per SM that fits.
+template <typename Real>
+int choose_tile(const slr::NetParams<Real> &p, size_t &smem, int &blocks_per_sm) {
+    int bestT = 0;
+    long best = 0;
+    for (int T : slr::kTileSizes) {
+        const size_t s = slr::eval_smem_bytes<Real>(T, p.d, p.R, p.n_max_pad, p.n_in_max);
+        if (s > (size_t)kMaxSmem) continue;
+        const int nb = sizeof(Real) == 4 ? slr::eval_blocks_per_sm_f32(T, s) : slr::eval_blocks_per_sm_f64(T, s);
+        if (nb <= 0) continue;
+        const long boxes = (long)nb * T;
+        if (boxes > best) {
+            best = boxes;
+            bestT = T;
+            smem = s;
+            blocks_per_sm = nb;
+        }
+    }
+    return bestT;
+}
+
+int prepare_device(slr_ctx *ctx) {
+    if (!ctx->dev_dirty) return SLR_OK;
+    if (ctx->widths.back() != (int)(ctx->C.size() / std::max<size_t>(1, ctx->e.size())))
+        return fail(ctx, SLR_EINVAL, "property has %zu outputs per row but the network has %d outputs",
+                    ctx->C.size() / std::max<size_t>(1, ctx->e.size()), ctx->widths.back());
+    HostLayers<float> Lf;
+    HostLayers<double> Ld;
+    build_layers(ctx, Lf);
+    build_layers(ctx, Ld);
+    const size_t bytes = layers_bytes(Lf) + layers_bytes(Ld);
+    if (ctx->net_buf) {
+        cudaFree(ctx->net_buf);
+        ctx->net_buf = nullptr;
+    }
+    CK(ctx, cudaMalloc(&ctx->net_buf, bytes));
+    std::vector<unsigned char> host(bytes, 0);
+    size_t off = 0;
+    layout_params(ctx, Lf, (unsigned char *)ctx->net_buf, host.data(), off, ctx->nf);
+    layout_params(ctx, Ld, (unsigned char *)ctx->net_buf, host.data(), off, ctx->nd);
+    CK(ctx, cudaMemcpyAsync(ctx->net_buf, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    int bps = 0;
+    ctx->T32 = choose_tile(ctx->nf, ctx->smem32, bps);
+    if (ctx->T32 == 0)
+        return fail(ctx, SLR_EUNSUPPORTED, "network too large for the fused FP32 kernel (d=%d, widest=%d)",
+                    ctx->nf.d, ctx->nf.n_max_pad);
+    ctx->grid32 = bps * ctx->sm_count;
+    ctx->T64 = choose_tile(ctx->nd, ctx->smem64, bps);
+    ctx->grid64 = ctx->T64 ? bps * ctx->sm_count : 0;
+    ctx->dev_dirty = false;
+    return SLR_OK;
+}
+
+int ensure_scratch(slr_ctx *ctx, size_t bytes) {
+    if (ctx->scratch_bytes >= bytes) return SLR_OK;
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    CK(ctx, cudaMalloc(&ctx->scratch, bytes));
+    ctx->scratch_bytes = bytes;
+    return SLR_OK;
+}
+
+void free_count_buffers(slr_ctx *ctx) {
+    cudaFree(ctx->codes[0]);
+    cudaFree(ctx->codes[1]);
+    cudaFree(ctx->cls);
+    cudaFree(ctx->near_list);
+    ctx->codes[0] = ctx->codes[1] = nullptr;
+    ctx->cls = nullptr;
+    ctx->near_list = nullptr;
+    ctx->cap = 0;
+}
+
+int ensure_count_buffers(slr_ctx *ctx) {
+    const int64_t cap = ctx->opt.frontier_cap;
+    if (ctx->cap != cap) {
+        free_count_buffers(ctx);
+        CK(ctx, cudaMalloc(&ctx->codes[0], (size_t)cap * sizeof(uint64_t)));
+        CK(ctx, cudaMalloc(&ctx->codes[1], (size_t)cap * sizeof(uint64_t)));
+        CK(ctx, cudaMalloc(&ctx->cls, (size_t)cap));
+        ctx->near_cap = std::max<int64_t>(1024, cap / 4);
+        CK(ctx, cudaMalloc(&ctx->near_list, (size_t)ctx->near_cap * sizeof(int64_t)));
+        ctx->cap = cap;
+    }
+    if (!ctx->ctr) {
+        CK(ctx, cudaMalloc(&ctx->ctr, sizeof(slr::LevelCounters)));
+        CK(ctx, cudaMalloc(&ctx->status, sizeof(unsigned int)));
+        CK(ctx, cudaMallocHost(&ctx->h_ctr, sizeof(slr::LevelCounters)));
+        CK(ctx, cudaMallocHost(&ctx->h_status, sizeof(unsigned int)));
+    }
+    const int d = ctx->widths[0];
+    if (ctx->root_d != d) {
+        cudaFree(ctx->root);
+        cudaFree(ctx->masks);
+        ctx->root = nullptr;
+        ctx->masks = nullptr;
+        CK(ctx, cudaMalloc(&ctx->root, 2 * (size_t)d * sizeof(double)));
+        CK(ctx, cudaMalloc(&ctx->masks, (size_t)d * sizeof(unsigned long long)));
+        ctx->root_d = d;
+    }
+    if (ctx->opt.record_leaves && ctx->leaf_cap_alloc != ctx->opt.leaf_cap) {
+        cudaFree(ctx->leaf_codes);
+        cudaFree(ctx->leaf_depth);
+        cudaFree(ctx->leaf_cls);
+        ctx->leaf_codes = nullptr;
+        ctx->leaf_depth = ctx->leaf_cls = nullptr;
+        ctx->leaf_cap_alloc = 0;
+        const size_t lc = (size_t)ctx->opt.leaf_cap;
+        CK(ctx, cudaMalloc(&ctx->leaf_codes, lc * sizeof(uint64_t)));
+        CK(ctx, cudaMalloc(&ctx->leaf_depth, lc));
+        CK(ctx, cudaMalloc(&ctx->leaf_cls, lc));
+        ctx->leaf_cap_alloc = ctx->opt.leaf_cap;
+    }
+    return SLR_OK;
+}
+
+int check_ready(slr_ctx *ctx) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!ctx->has_net || !ctx->has_box || !ctx->has_prop)
+        return fail(ctx, SLR_ESTATE, "network, box and property must be set before counting");
+    if ((int)ctx->lo.size() != ctx->widths[0])
+        return fail(ctx, SLR_EINVAL, "box has %zu dimensions but the network has %d inputs", ctx->lo.size(),
+                    ctx->widths[0]);
+    return SLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void slr_default_options(slr_options *opt) {
+    if (!opt) return;
+    opt->precision = SLR_PREC_FP32;
+    opt->relax_mode = SLR_RELAX_NEURIFY;
+    opt->fp64_recheck = 1;
+    opt->record_leaves = 0;
+    opt->frontier_cap = (int64_t)1 << 24;
+    opt->leaf_cap = (int64_t)1 << 22;
+}
+
+int slr_create(slr_ctx **out, int device, void *cuda_stream) {
+    if (!out) return fail(nullptr, SLR_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess) return fail(nullptr, SLR_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= n_dev) return fail(nullptr, SLR_EINVAL, "device %d out of range (%d devices)", device, n_dev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, SLR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    slr_ctx *ctx = new (std::nothrow) slr_ctx();
+    if (!ctx) return fail(nullptr, SLR_ENOMEM, "host allocation failed");
+    ctx->device = device;
+    slr_default_options(&ctx->opt);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, SLR_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        ctx->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    *out = ctx;
+    return SLR_OK;
+}
+
+int slr_destroy(slr_ctx *ctx) {
+    if (!ctx) return SLR_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_count_buffers(ctx);
+    cudaFree(ctx->net_buf);
+    cudaFree(ctx->ctr);
+    cudaFree(ctx->status);
+    cudaFree(ctx->root);
+    cudaFree(ctx->masks);
+    cudaFree(ctx->leaf_codes);
+    cudaFree(ctx->leaf_depth);
+    cudaFree(ctx->leaf_cls);
+    cudaFree(ctx->scratch);
+    if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SLR_OK;
+}
+
+int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
+    if (!ctx || !opt) return fail(ctx, SLR_EINVAL, "null argument");
+    if (opt->precision != SLR_PREC_FP32) return fail(ctx, SLR_EUNSUPPORTED, "precision %d not built", opt->precision);
+    if (opt->relax_mode != SLR_RELAX_NEURIFY && opt->relax_mode != SLR_RELAX_PAPER_LITERAL)
+        return fail(ctx, SLR_EINVAL, "relax_mode %d unknown", opt->relax_mode);
+    if (opt->frontier_cap < 2 || opt->frontier_cap > ((int64_t)1 << 34))
+        return fail(ctx, SLR_EINVAL, "frontier_cap %lld out of range", (long long)opt->frontier_cap);
+    if (opt->record_leaves && (opt->leaf_cap < 1 || opt->leaf_cap > ((int64_t)1 << 34)))
+        return fail(ctx, SLR_EINVAL, "leaf_cap %lld out of range", (long long)opt->leaf_cap);
+    if (opt->relax_mode != ctx->opt.relax_mode) ctx->dev_dirty = true;
+    ctx->opt = *opt;
+    return SLR_OK;
+}
+
+int slr_load_network(slr_ctx *ctx, int K, const int32_t *widths, const float *const *W, const float *const *b) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (K < 1 || K > slr::kMaxLayers) return fail(ctx, SLR_EINVAL, "K=%d out of range [1, %d]", K, slr::kMaxLayers);
+    if (!widths || !W || !b) return fail(ctx, SLR_EINVAL, "null widths/W/b");
+    for (int k = 0; k <= K; ++k)
+        if (widths[k] < 1 || widths[k] > slr::kMaxWidth)
+            return fail(ctx, SLR_EINVAL, "widths[%d]=%d out of range [1, %d]", k, widths[k], slr::kMaxWidth);
+    std::vector<std::vector<float>> Wv(K), bv(K);
+    for (int k = 0; k < K; ++k) {
+        if (!W[k] || !b[k]) return fail(ctx, SLR_EINVAL, "null W[%d] or b[%d]", k, k);
+        const size_t nw = (size_t)widths[k + 1] * widths[k];
+        if (!finite_all(W[k], nw) || !finite_all(b[k], widths[k + 1]))
+            return fail(ctx, SLR_EINVAL, "non-finite value in layer %d", k);
+        Wv[k].assign(W[k], W[k] + nw);
+        bv[k].assign(b[k], b[k] + widths[k + 1]);
+    }
+    ctx->K = K;
+    ctx->widths.assign(widths, widths + K + 1);
+    ctx->W.swap(Wv);
+    ctx->b.swap(bv);
+    ctx->has_net = true;
+    ctx->dev_dirty = true;
+    ctx->leaves_valid = false;
+    return SLR_OK;
+}
+
+int slr_set_box(slr_ctx *ctx, int d, const float *lo, const float *hi) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (d < 1 || d > slr::kMaxWidth || !lo || !hi) return fail(ctx, SLR_EINVAL, "bad box arguments (d=%d)", d);
+    for (int i = 0; i < d; ++i) {
+        if (!std::isfinite(lo[i]) || !std::isfinite(hi[i]))
+            return fail(ctx, SLR_EINVAL, "non-finite box endpoint in dimension %d", i);
+        if (lo[i] > hi[i]) return fail(ctx, SLR_EINVAL, "lo > hi in dimension %d", i);
+    }
+    ctx->lo.assign(lo, lo + d);
+    ctx->hi.assign(hi, hi + d);
+    ctx->has_box = true;
+    ctx->leaves_valid = false;
+    return SLR_OK;
+}
+
+int slr_set_property(slr_ctx *ctx, int n_clauses, const int32_t *rows_per_clause, int n_out, const float *C,
+                     const float *e, const uint8_t *strict) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (n_clauses < 1 || !rows_per_clause || !C || !e || !strict || n_out < 1 || n_out > slr::kMaxWidth)
+        return fail(ctx, SLR_EINVAL, "bad property arguments");
+    int R = 0;
+    for (int c = 0; c < n_clauses; ++c) {
+        if (rows_per_clause[c] < 1) return fail(ctx, SLR_EINVAL, "clause %d has no rows", c);
+        R += rows_per_clause[c];
+        if (R > slr::kMaxRows) return fail(ctx, SLR_EINVAL, "more than %d property rows", slr::kMaxRows);
+    }
+    if (!finite_all(C, (size_t)R * n_out) || !finite_all(e, R))
+        return fail(ctx, SLR_EINVAL, "non-finite value in the property");
+    ctx->n_clauses = n_clauses;
+    ctx->rpc.assign(rows_per_clause, rows_per_clause + n_clauses);
+    ctx->C.assign(C, C + (size_t)R * n_out);
+    ctx->e.assign(e, e + R);
+    ctx->strict.assign(strict, strict + R);
+    ctx->has_prop = true;
+    ctx->dev_dirty = true;
+    ctx->leaves_valid = false;
+    return SLR_OK;
+}
+
+int slr_count(slr_ctx *ctx, int D, slr_result *out) {
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (!out) return fail(ctx, SLR_EINVAL, "out is NULL");
+    if (D < 0 || D > slr::kMaxDepth) return fail(ctx, SLR_EINVAL, "D=%d out of range [0, %d]", D, slr::kMaxDepth);
+    CK(ctx, cudaSetDevice(ctx->device));
+    if ((rc = prepare_device(ctx))) return rc;
+    if ((rc = ensure_count_buffers(ctx))) return rc;
+    const int d = ctx->widths[0];
+
+    // split schedule: widest side first, ties to the lowest index (Sec. 2.2 bisection)
+    std::vector<double> root(2 * (size_t)d);
+    std::vector<unsigned long long> masks(d, 0ull);
+    std::vector<int> cnt(d, 0);
+    for (int i = 0; i < d; ++i) {
+        root[i] = (double)ctx->lo[i];
+        root[d + i] = (double)ctx->hi[i] - (double)ctx->lo[i];
+    }
+    ctx->sched.assign(D, 0);
+    for (int t = 0; t < D; ++t) {
+        int best = 0;
+        double bw = -1.0;
+        for (int i = 0; i < d; ++i) {
+            const double w = std::ldexp(root[d + i], -cnt[i]);
+            if (w > bw) {
+                bw = w;
+                best = i;
+            }
+        }
+        ctx->sched[t] = best;
+        cnt[best] += 1;
+        masks[best] |= 1ull << (D - 1 - t);
+    }
+    ctx->h_stage.resize(root.size() * sizeof(double) + masks.size() * sizeof(unsigned long long));
+    std::memcpy(ctx->h_stage.data(), root.data(), root.size() * sizeof(double));
+    std::memcpy(ctx->h_stage.data() + root.size() * sizeof(double), masks.data(), masks.size() * sizeof(unsigned long long));
+    CK(ctx, cudaMemcpyAsync(ctx->root, ctx->h_stage.data(), root.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->masks, ctx->h_stage.data() + root.size() * sizeof(double),
+                            masks.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(slr::LevelCounters), ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
+    CK(ctx, slr::launch_init_count(ctx->codes[0], ctx->ctr, ctx->stream));
+
+    const bool leaves = ctx->opt.record_leaves != 0;
+    const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0;
+    const int compact_grid = std::max(1, ctx->sm_count * 4);
+    CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+    for (int t = 0; t <= D; ++t) {
+        slr::BoxSource src{};
+        src.mode = 0;
+        src.codes = ctx->codes[t & 1];
+        src.count = &ctx->ctr->frontier_n[t];
+        src.t = t;
+        src.D = D;
+        src.dim_mask = ctx->masks;
+        src.root_lo = ctx->root;
+        src.root_w = ctx->root + d;
+        src.cap = ctx->cap;
+        slr::EvalOutputs o{};
+        o.cls = ctx->cls;
+        o.near_list = recheck ? ctx->near_list : nullptr;
+        o.near_count = &ctx->ctr->near_n[t];
+        o.near_cap = ctx->near_cap;
+        o.tie_count = &ctx->ctr->ties;
+        o.status = ctx->status;
+        CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->grid32, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+        if (recheck) {
+            slr::BoxSource s2 = src;
+            s2.index = ctx->near_list;
+            s2.index_count = &ctx->ctr->near_n[t];
+            s2.cap = ctx->near_cap;
+            slr::EvalOutputs o2{};
+            o2.cls = ctx->cls;
+            o2.tie_count = &ctx->ctr->ties;
+            o2.status = ctx->status;
+            CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->sm_count, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
+        }
+        CK(ctx, slr::launch_compact(ctx->codes[t & 1], ctx->cls, ctx->codes[(t + 1) & 1], ctx->ctr, ctx->status,
+                                    ctx->cap, t, D, leaves ? ctx->leaf_codes : nullptr, ctx->leaf_depth,
+                                    ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream));
+    }
+    CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+
+    const slr::LevelCounters &c = *ctx->h_ctr;
+    std::memset(out, 0, sizeof *out);
+    out->unsafe_lo = c.unsafe_lo;
+    out->unsafe_hi = c.unsafe_lo + c.undecided_at_D;
+    out->boxes = c.boxes;
+    out->tie_leaves = c.ties;
+    out->depth = D;
+    int levels = 0;
+    unsigned long long rech = 0;
+    for (int t = 0; t <= D; ++t) {
+        out->level_boxes[t] = c.level_boxes[t];
+        out->level_safe[t] = c.level_safe[t];
+        out->level_unsafe[t] = c.level_unsafe[t];
+        out->level_undecided[t] = c.level_undecided[t];
+        rech += std::min<unsigned long long>(c.near_n[t], (unsigned long long)ctx->near_cap);
+        if (c.level_boxes[t]) levels = t + 1;
+    }
+    out->rechecked = recheck ? rech : 0;
+    out->levels = levels;
+    out->device_ms = ms;
+    ctx->n_leaves = leaves ? (int64_t)c.leaves : 0;
+    ctx->leaves_valid = leaves;
+    const unsigned st = *ctx->h_status;
+    if (st & slr::kStatusOverflow)
+        return fail(ctx, SLR_EOVERFLOW, "a level exceeded frontier_cap=%lld boxes", (long long)ctx->cap);
+    if (st & slr::kStatusNearOverflow)
+        return fail(ctx, SLR_EOVERFLOW, "FP64 re-check list exceeded %lld boxes", (long long)ctx->near_cap);
+    if (st & slr::kStatusLeafOverflow)
+        return fail(ctx, SLR_EOVERFLOW, "leaf recording exceeded leaf_cap=%lld", (long long)ctx->opt.leaf_cap);
+    return SLR_OK;
+}
+
+int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, float *row_lo, float *row_hi,
+               float *row_err, uint8_t *cls, int on_device) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!ctx->has_net || !ctx->has_prop) return fail(ctx, SLR_ESTATE, "network and property must be set");
+    if (n < 0 || (n > 0 && (!box_lo || !box_hi))) return fail(ctx, SLR_EINVAL, "bad box arguments");
+    if ((row_lo == nullptr) != (row_hi == nullptr)) return fail(ctx, SLR_EINVAL, "row_lo and row_hi go together");
+    if (n == 0) return SLR_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    int rc = prepare_device(ctx);
+    if (rc) return rc;
+    const int d = ctx->widths[0];
+    const int R = (int)ctx->e.size();
+    const float *dlo = box_lo, *dhi = box_hi;
+    float *drl = row_lo, *drh = row_hi, *dre = row_err;
+    uint8_t *dcls = cls;
+    if (!on_device) {
+        for (int64_t k = 0; k < n * d; ++k) {
+            if (!std::isfinite(box_lo[k]) || !std::isfinite(box_hi[k]) || box_lo[k] > box_hi[k])
+                return fail(ctx, SLR_EINVAL, "box %lld: bad endpoints in dimension %d", (long long)(k / d), (int)(k % d));
+        }
+        const size_t need = align_up(2 * (size_t)n * d * sizeof(float)) + align_up(3 * (size_t)n * R * sizeof(float)) +
+                            align_up((size_t)n);
+        if ((rc = ensure_scratch(ctx, need))) return rc;
+        unsigned char *p = (unsigned char *)ctx->scratch;
+        float *slo = (float *)p;
+        float *shi = slo + (size_t)n * d;
+        p += align_up(2 * (size_t)n * d * sizeof(float));
+        drl = row_lo ? (float *)p : nullptr;
+        drh = row_lo ? (float *)p + (size_t)n * R : nullptr;
+        dre = row_err ? (float *)p + 2 * (size_t)n * R : nullptr;
+        p += align_up(3 * (size_t)n * R * sizeof(float));
+        dcls = cls ? (uint8_t *)p : nullptr;
+        CK(ctx, cudaMemcpyAsync(slo, box_lo, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(shi, box_hi, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        dlo = slo;
+        dhi = shi;
+    }
+    slr::BoxSource src{};
+    src.mode = 1;
+    src.n_explicit = n;
+    src.lo = dlo;
+    src.hi = dhi;
+    src.cap = n;
+    slr::EvalOutputs o{};
+    o.cls = dcls;
+    o.row_lo = drl;
+    o.row_hi = drh;
+    o.row_err = dre;
+    if (!ctx->status) {
+        CK(ctx, cudaMalloc(&ctx->status, sizeof(unsigned int)));
+        CK(ctx, cudaMallocHost(&ctx->h_status, sizeof(unsigned int)));
+    }
+    o.status = ctx->status;
+    const int64_t tiles = (n + ctx->T32 - 1) / ctx->T32;
+    const int grid = (int)std::min<int64_t>(tiles, ctx->grid32);
+    CK(ctx, slr::launch_eval_f32(ctx->T32, grid, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+    if (!on_device) {
+        if (row_lo) {
+            CK(ctx, cudaMemcpyAsync(row_lo, drl, (size_t)n * R * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(ctx, cudaMemcpyAsync(row_hi, drh, (size_t)n * R * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        if (row_err)
+            CK(ctx, cudaMemcpyAsync(row_err, dre, (size_t)n * R * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        if (cls) CK(ctx, cudaMemcpyAsync(cls, dcls, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SLR_OK;
+}
+
+int slr_leaves(slr_ctx *ctx, int64_t cap, uint64_t *codes, uint8_t *depth, uint8_t *cls, int64_t *n) {
+    if (!ctx || !n) return fail(ctx, SLR_EINVAL, "null argument");
+    if (!ctx->leaves_valid) return fail(ctx, SLR_ESTATE, "no leaves recorded (set record_leaves and count)");
+    *n = ctx->n_leaves;
+    const int64_t m = std::min(std::min(cap, ctx->n_leaves), ctx->leaf_cap_alloc);
+    CK(ctx, cudaSetDevice(ctx->device));
+    if (m > 0) {
+        if (codes) CK(ctx, cudaMemcpy(codes, ctx->leaf_codes, (size_t)m * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        if (depth) CK(ctx, cudaMemcpy(depth, ctx->leaf_depth, (size_t)m, cudaMemcpyDeviceToHost));
+        if (cls) CK(ctx, cudaMemcpy(cls, ctx->leaf_cls, (size_t)m, cudaMemcpyDeviceToHost));
+    }
+    if (ctx->n_leaves > ctx->leaf_cap_alloc)
+        return fail(ctx, SLR_EOVERFLOW, "%lld leaves exceeded leaf_cap=%lld", (long long)ctx->n_leaves,
+                    (long long)ctx->leaf_cap_alloc);
+    return SLR_OK;
+}
+
+int slr_schedule(slr_ctx *ctx, int D, int32_t *dims) {
+    if (!ctx || !dims) return fail(ctx, SLR_EINVAL, "null argument");
+    if (D < 0 || D > (int)ctx->sched.size())
+        return fail(ctx, SLR_EINVAL, "D=%d exceeds the last count's depth %zu", D, ctx->sched.size());
+    for (int t = 0; t < D; ++t) dims[t] = ctx->sched[t];
+    return SLR_OK;
+}
+
+const char *slr_last_error(const slr_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Frontier kernels of the level-by-level count (Alg. 1, Sec. 3).
+//
+// compact_kernel is the split/volume step of one level: it reads the path
+// codes and classes of the level's boxes and
+//   UNSAFE     adds 2^(D-t) to the unsafe volume (one unit = 2^-D of the root),
+//   SAFE       drops the box,
+//   UNDECIDED  writes the two children codes 2c, 2c+1 to the next level when
+//              t < D, or adds one unit to the undecided volume when t = D.
+// Each warp aggregates its counts and its output slots with one atomic per
+// warp (ballot + popc); integer sums make the result independent of order.
+#include "slr_device.cuh"
+#include "slr_kernels.h"
+
+namespace slr {
+
+__global__ void init_count_kernel(uint64_t *codes0, LevelCounters *ctr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        codes0[0] = 0ull;
+        ctr->frontier_n[0] = 1ull;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
+               uint64_t *__restrict__ codes_out, LevelCounters *ctr, unsigned int *status,
+               int64_t cap, int t, int D, uint64_t *leaf_codes, uint8_t *leaf_depth,
+               uint8_t *leaf_cls, int64_t leaf_cap) {
+    const unsigned long long n_raw = ctr->frontier_n[t];
+    const int64_t n = (int64_t)n_raw < cap ? (int64_t)n_raw : cap;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->level_boxes[t] = (unsigned long long)n;
+        atomicAdd(&ctr->boxes, (unsigned long long)n);
+    }
+    unsigned long long n_unsafe = 0, n_safe = 0, n_und = 0;
+    for (int64_t base = warp_global * 32; base < n; base += n_warps * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        const uint8_t c = valid ? cls[i] : (uint8_t)255;
+        const uint64_t code = valid ? codes_in[i] : 0ull;
+        const bool und = c == kUndecided;
+        const unsigned m_und = __ballot_sync(0xffffffffu, und);
+        const unsigned m_uns = __ballot_sync(0xffffffffu, c == kUnsafe);
+        const unsigned m_safe = __ballot_sync(0xffffffffu, c == kSafe);
+        n_unsafe += __popc(m_uns);
+        n_safe += __popc(m_safe);
+        n_und += __popc(m_und);
+        if (t < D) {
+            unsigned long long slot = 0;
+            if (lane == 0 && m_und != 0u)
+                slot = atomicAdd(&ctr->frontier_n[t + 1], 2ull * (unsigned long long)__popc(m_und));
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (und) {
+                const int64_t pos = (int64_t)slot + 2 * __popc(m_und & lt_mask);
+                if (pos + 1 < cap) {
+                    codes_out[pos] = code << 1;
+                    codes_out[pos + 1] = (code << 1) | 1ull;
+                } else {
+                    atomicOr(status, kStatusOverflow);
+                }
+            }
+        }
+        if (leaf_codes != nullptr) {
+            const bool leaf = (c == kUnsafe) || (c == kSafe) || (und && t == D);
+            const unsigned m_leaf = __ballot_sync(0xffffffffu, leaf);
+            unsigned long long slot = 0;
+            if (lane == 0 && m_leaf != 0u) slot = atomicAdd(&ctr->leaves, (unsigned long long)__popc(m_leaf));
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (leaf) {
+                const int64_t pos = (int64_t)slot + __popc(m_leaf & lt_mask);
+                if (pos < leaf_cap) {
+                    leaf_codes[pos] = code;
+                    leaf_depth[pos] = (uint8_t)t;
+                    leaf_cls[pos] = c;
+                } else {
+                    atomicOr(status, kStatusLeafOverflow);
+                }
+            }
+        }
+    }
+    // one atomic per warp for the level statistics and the volumes
+    if (lane == 0) {
+        if (n_unsafe) {
+            atomicAdd(&ctr->level_unsafe[t], n_unsafe);
+            atomicAdd(&ctr->unsafe_lo, n_unsafe << (D - t));
+        }
+        if (n_safe) atomicAdd(&ctr->level_safe[t], n_safe);
+        if (n_und) {
+            atomicAdd(&ctr->level_undecided[t], n_und);
+            if (t == D) atomicAdd(&ctr->undecided_at_D, n_und);
+        }
+    }
+}
+
+cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s) {
+    init_count_kernel<<<1, 32, 0, s>>>(codes0, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
+                           LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
+                           uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
+                           int64_t leaf_cap, int grid, cudaStream_t s) {
+    compact_kernel<<<grid, 256, 0, s>>>(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes,
+                                        leaf_depth, leaf_cls, leaf_cap);
+    return cudaGetLastError();
+}
+
+}  // namespace slr

@@ -1,0 +1,31 @@
+// Host-side launch wrappers of the SLR kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "slr_device.cuh"
+
+namespace slr {
+
+// Tile sizes (boxes per CTA) the evaluation kernel is built for.
+constexpr int kTileSizes[] = {64, 32, 16, 8, 4};
+constexpr int kEvalThreads = 256;
+
+// Fused evaluation (kernel (b) plus its contraction); one instantiation per
+// working precision.  `T` must be one of kTileSizes.
+cudaError_t launch_eval_f32(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
+                            const BoxSource &src, const EvalOutputs &out, int pass);
+cudaError_t launch_eval_f64(int T, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
+                            const BoxSource &src, const EvalOutputs &out, int pass);
+// Resident CTAs per SM of the evaluation kernel at tile size T and this smem.
+int eval_blocks_per_sm_f32(int T, size_t smem);
+int eval_blocks_per_sm_f64(int T, size_t smem);
+
+cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s);
+cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
+                           LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
+                           uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
+                           int64_t leaf_cap, int grid, cudaStream_t s);
+
+}  // namespace slr

@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports what include/slrcount.h declares (CPU only, no compute)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from .conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "slrcount.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_05890_gb300 as pkg
+    return pkg.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(slr_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_binding_names():
+    import paper_2312_05890_gb300 as pkg
+    assert declared_functions() == sorted(pkg.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = os.path.join(ROOT, "paper_2312_05890_gb300", "libslrcount.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_default_options(lib):
+    import paper_2312_05890_gb300 as pkg
+    o = pkg.slr_default_options()
+    assert o.precision == pkg.PREC_FP32 and o.relax_mode == pkg.RELAX_NEURIFY
+    assert o.fp64_recheck == 1 and o.record_leaves == 0
+    assert o.frontier_cap == 1 << 24
+
+
+def test_null_context_is_rejected_without_a_gpu(lib):
+    import paper_2312_05890_gb300 as pkg
+    assert lib.slr_load_network(None, 1, None, None, None) == -1
+    assert lib.slr_set_box(None, 1, None, None) == -1
+    assert lib.slr_count(None, 3, None) == -1
+    assert lib.slr_destroy(None) == 0
+    assert b"null context" in lib.slr_last_error(None)
+    out = ctypes.c_void_p()
+    rc = lib.slr_create(ctypes.byref(out), -1, None)
+    assert rc in (-1, -3) and not out.value   # no device here, or device -1 out of range
+    _ = pkg
+
+
+def test_result_struct_matches_header_size(lib):
+    import paper_2312_05890_gb300 as pkg
+    # 5 u64 + 2 i32 + 4 * 64 u64 + double
+    assert ctypes.sizeof(pkg.slr_result) == 5 * 8 + 2 * 4 + 4 * 64 * 8 + 8
+    assert ctypes.sizeof(pkg.slr_options) == 4 * 4 + 2 * 8
