@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact #DNN-Verification counter (SLR + bisection) on GB300.
+
+One step is one whole count, Alg. 1 level by level (Sec. 3), of the
+ACAS-shaped workload: a 5 -> 6x50 -> 5 ReLU network, a random sub-box of
+[-0.5, 0.5]^5, the unsafe set "output 0 is not minimal", depth 20 (a frontier of
+up to 2^20 boxes).  The metric is SLR subdomain bounds per second: boxes bounded
+over all levels divided by the device time of the count; the time-to-count is
+ms_per_step.
+
+Prints one JSON line.  Besides the contract keys it carries
+  roofline      the FP32 evaluation kernel's algorithmic FLOP rate (centre/radius
+                form: 4 n_{k+1} n_k (d+1) per box and affine layer) against the
+                FP32 CUDA-core peak 152 SMs x 128 lanes x 2 x the sampled SM clock,
+  cpu_baseline  the FP64 oracle on the host cores over a bounded sample of the
+                same count (one process per core, levels in order, ~15 s),
+  e2e           the same metric through the C ABI with host buffers: network,
+                box and property uploaded and the result read back every step,
+  clocks        nvidia-smi samples taken during the timed region.
+`--impl reference` times the oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SMS = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20          # written between timed steps (> 129 MB L2)
+
+# DRAM bytes per box of the FP32 evaluation kernel from one ncu capture of the
+# kernel source hashed below (profiles/slr_eval_f32_acas.md); reported as
+# roofline.traffic only while the kernel source is unchanged.
+TRAFFIC = {"source_sha": "533f19481a9bfa0a", "bytes_per_box": 8.4}
+KERNEL_SOURCES = ["paper_2312_05890_gb300/csrc/slr_eval.cuh", "paper_2312_05890_gb300/csrc/slr_eval_f32.cu",
+                  "paper_2312_05890_gb300/csrc/slr_device.cuh"]
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_flops_per_box(widths, R):
+    """4 n_{k+1} n_k (d+1) per affine layer after the first (W C and |W| R), last layer with R rows."""
+    d = widths[0]
+    n = list(widths[:-1]) + [R]
+    return sum(4 * n[k + 1] * n[k] * (d + 1) for k in range(1, len(n) - 1))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def _worker_init(name, seed, D):
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    global _W
+    import oracle
+    from workloads import generators as gen
+    p = gen.make(name, seed)
+    _W = (oracle, p, oracle.split_schedule(p.lo, p.hi, D), D)
+
+
+def _worker_level(args):
+    codes, t = args
+    import numpy as np
+    oracle, p, sched, D = _W
+    codes = np.asarray(codes, dtype=np.int64)
+    lo, hi = oracle.decode(codes, t, sched, p.lo, p.hi)
+    rlo, rhi, _ = oracle.slr_forward(p.net, lo, hi, p.prop)
+    cls = oracle.classify(rlo, rhi, p.prop)
+    return codes[cls == oracle.UNDECIDED], int((cls == oracle.UNSAFE).sum())
+
+
+def oracle_sample(name, seed, D, budget_s, procs):
+    """The oracle's level-by-level count, its levels split over `procs` processes, stopped at a
+    level boundary after `budget_s` seconds.  Returns (boxes, seconds, levels)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_worker_init, initargs=(name, seed, D)) as pool:
+        pool.map(_worker_level, [(np.zeros(1, np.int64), 0)] * procs)      # warm the workers
+        frontier = np.zeros(1, dtype=np.int64)
+        boxes, levels = 0, 0
+        t0 = time.perf_counter()
+        for t in range(D + 1):
+            if frontier.shape[0] == 0:
+                break
+            chunks = [c for c in np.array_split(frontier, max(1, min(procs * 4, frontier.shape[0]))) if c.size]
+            res = pool.map(_worker_level, [(c, t) for c in chunks])
+            boxes += int(frontier.shape[0])
+            levels = t + 1
+            und = np.concatenate([r[0] for r in res]) if res else np.zeros(0, np.int64)
+            frontier = np.concatenate([2 * und, 2 * und + 1]) if t < D else und
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+    return boxes, dt, levels
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="acas")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
+                    help="L2 flush buffer written between timed steps (MB)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    procs = os.cpu_count() or 1
+
+    from workloads import generators as gen
+    # weak scaling: rank r counts its own problem of the same shape (seed + r)
+    p = gen.make(args.workload, args.seed + rank)
+    D = p.depth
+    workload = f"{p.name} D={D} seed={args.seed}"
+    config = {"workload": workload, "widths": p.net.widths, "depth": D, "rows": p.prop.R,
+              "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            oracle_sample(args.workload, args.seed, D, budget, procs)
+        tot_boxes, tot_s, lv = 0, 0.0, 0
+        for _ in range(args.steps):
+            b, s, lv = oracle_sample(args.workload, args.seed, D, budget, procs)
+            tot_boxes += b
+            tot_s += s
+        v = tot_boxes / tot_s
+        sample = f"levels 0..{lv - 1} of the count ({tot_boxes // max(1, args.steps)} boxes per step)"
+        print(json.dumps({
+            "impl": "reference", "metric": "slr_subdomain_bounds_per_sec", "value": v, "unit": "boxes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": v, "unit": "boxes/s", "cores": procs, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    import paper_2312_05890_gb300 as pkg
+    pkg.load_library()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device="cuda")
+    c = pkg.Counter(local_rank)
+    c.set_problem(p)
+    c.set_options(profile=1)
+    for _ in range(args.warmup):
+        c.count(D)
+
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t_wall = time.perf_counter()
+    dev_ms, boxes, kern = [], 0, [0.0, 0.0, 0.0]
+    launches = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        r = c.count(D)
+        dev_ms.append(r["device_ms"])
+        boxes += r["boxes"]
+        launches += r["launches"]
+        for i in range(3):
+            kern[i] += r["kernel_ms"][i]
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    last = r
+
+    tot_ms = sum(dev_ms)
+    stats = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+    tot_boxes = torch.tensor([boxes], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(stats, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot_boxes, op=dist.ReduceOp.SUM)
+    max_ms = float(stats.item())
+    value = float(tot_boxes.item()) / (max_ms / 1e3)
+
+    # ---- e2e: upload network, box and property from host memory every step ------
+    e2e_s = []
+    h2d = d2h = 0
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.set_problem(p)
+        r = c.count(D)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e_s.append(dt)
+            h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
+    e2e_value = last["boxes"] / statistics.mean(e2e_s)
+
+    # ---- roofline of the FP32 evaluation kernel ---------------------------------
+    fpb = algorithmic_flops_per_box(p.net.widths, p.prop.R)
+    eval_s = kern[0] / 1e3
+    achieved = fpb * boxes / eval_s / 1e12
+    clk = clocks.get("sm_mhz") or 2070.0
+    peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    eval_launches = args.steps * (D + 1)
+    traffic = None
+    if TRAFFIC["source_sha"] == kernel_sha() and TRAFFIC["bytes_per_box"]:
+        traffic = TRAFFIC["bytes_per_box"] * boxes / eval_launches
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "slr_eval_kernel<float>",
+                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk:.0f} MHz (sampled median)",
+                "flop_per_box": fpb, "kernel_share": kern[0] / max(1e-9, sum(dev_ms)),
+                "avg_launch_ms": kern[0] / eval_launches}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, cs, lv = oracle_sample(args.workload, args.seed, D, args.cpu_budget, procs)
+        cpu = {"value": cb / cs, "unit": "boxes/s", "cores": procs, "kind": "oracle",
+               "sample": f"levels 0..{lv - 1} of the same count, {cb} boxes, {cs:.1f} s, one process per core"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config,
+            "count": {"unsafe_lo": last["unsafe_lo"], "unsafe_hi": last["unsafe_hi"], "boxes": last["boxes"],
+                      "rechecked": last["rechecked"], "tie_leaves": last["tie_leaves"]},
+            "kernel_ms_per_step": {"eval_f32": kern[0] / args.steps, "recheck_f64": kern[1] / args.steps,
+                                   "compact": kern[2] / args.steps},
+            "wall_s": wall,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks,
+        }))
+    c.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,8 @@ typedef struct {
     int32_t fp64_recheck;   /* 1: re-bound in FP64 the undecided boxes that the FP32
                                bounds would decide without their widening; default 1 */
     int32_t record_leaves;  /* 1: keep the leaves of the last count for slr_leaves(); default 0 */
+    int32_t profile;        /* 1: time each kernel of a count with CUDA events (kernel_ms); default 0 */
+    int32_t reserved;       /* must be 0 */
     int64_t frontier_cap;   /* most boxes one level may hold; default 1<<24 */
     int64_t leaf_cap;       /* most leaves recorded when record_leaves; default 1<<22 */
 } slr_options;
@@ -86,6 +88,11 @@ typedef struct {
     uint64_t level_unsafe[SLR_MAX_LEVELS + 1];
     uint64_t level_undecided[SLR_MAX_LEVELS + 1];
     double device_ms;       /* device time of the count (CUDA events on the context stream) */
+    double kernel_ms[3];    /* with profile: summed device time of the FP32 evaluation,
+                               the FP64 re-check and the compaction kernels */
+    int64_t launches;       /* kernels launched by the count */
+    int64_t h2d_bytes;      /* host-to-device bytes copied by the count (inputs, schedule) */
+    int64_t d2h_bytes;      /* device-to-host bytes copied by the count (counters, status) */
 } slr_result;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to

@@ -39,6 +39,7 @@ class SlrError(RuntimeError):
 class slr_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
                 ("fp64_recheck", ctypes.c_int32), ("record_leaves", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("frontier_cap", ctypes.c_int64), ("leaf_cap", ctypes.c_int64)]
 
 
@@ -49,13 +50,17 @@ class slr_result(ctypes.Structure):
     _fields_ = [("unsafe_lo", ctypes.c_uint64), ("unsafe_hi", ctypes.c_uint64), ("boxes", ctypes.c_uint64),
                 ("rechecked", ctypes.c_uint64), ("tie_leaves", ctypes.c_uint64), ("depth", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("level_boxes", _U64A), ("level_safe", _U64A),
-                ("level_unsafe", _U64A), ("level_undecided", _U64A), ("device_ms", ctypes.c_double)]
+                ("level_unsafe", _U64A), ("level_undecided", _U64A), ("device_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double * 3), ("launches", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
     def to_dict(self):
         n = self.depth + 1
         return dict(unsafe_lo=int(self.unsafe_lo), unsafe_hi=int(self.unsafe_hi), boxes=int(self.boxes),
                     rechecked=int(self.rechecked), tie_leaves=int(self.tie_leaves), depth=int(self.depth),
                     levels=int(self.levels), device_ms=float(self.device_ms),
+                    kernel_ms=[float(x) for x in self.kernel_ms], launches=int(self.launches),
+                    h2d_bytes=int(self.h2d_bytes), d2h_bytes=int(self.d2h_bytes),
                     level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 

@@ -81,9 +81,12 @@ struct slr_ctx {
     size_t scratch_bytes = 0;
     int sm_count = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> prof_ev;   // profile: one event before and after each launch
     slr::LevelCounters *h_ctr = nullptr;
     unsigned int *h_status = nullptr;
-    std::vector<unsigned char> h_stage;
+    unsigned char *h_stage = nullptr;     // pinned staging for host-to-device copies
+    size_t h_stage_bytes = 0;
+    int64_t h2d_pending = 0;              // bytes uploaded since the last count returned
 };
 
 namespace {
@@ -248,6 +251,16 @@ int choose_tile(const slr::NetParams<Real> &p, size_t &smem, int &blocks_per_sm)
     return bestT;
 }
 
+int ensure_stage(slr_ctx *ctx, size_t bytes) {
+    if (ctx->h_stage_bytes >= bytes) return SLR_OK;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    CK(ctx, cudaMallocHost(&ctx->h_stage, bytes));
+    ctx->h_stage_bytes = bytes;
+    return SLR_OK;
+}
+
 int prepare_device(slr_ctx *ctx) {
     if (!ctx->dev_dirty) return SLR_OK;
     if (ctx->widths.back() != (int)(ctx->C.size() / std::max<size_t>(1, ctx->e.size())))
@@ -263,14 +276,19 @@ int prepare_device(slr_ctx *ctx) {
         ctx->net_buf = nullptr;
     }
     CK(ctx, cudaMalloc(&ctx->net_buf, bytes));
-    std::vector<unsigned char> host(bytes, 0);
-    size_t off = 0;
-    layout_params(ctx, Lf, (unsigned char *)ctx->net_buf, host.data(), off, ctx->nf);
-    layout_params(ctx, Ld, (unsigned char *)ctx->net_buf, host.data(), off, ctx->nd);
-    CK(ctx, cudaMemcpyAsync(ctx->net_buf, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    int rc = ensure_stage(ctx, bytes);
+    if (rc) return rc;
+    std::memset(ctx->h_stage, 0, bytes);
+    size_t off = 0;
+    layout_params(ctx, Lf, (unsigned char *)ctx->net_buf, ctx->h_stage, off, ctx->nf);
+    layout_params(ctx, Ld, (unsigned char *)ctx->net_buf, ctx->h_stage, off, ctx->nd);
+    CK(ctx, cudaMemcpyAsync(ctx->net_buf, ctx->h_stage, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->h2d_pending += (int64_t)bytes;
     int bps = 0;
     ctx->T32 = choose_tile(ctx->nf, ctx->smem32, bps);
+    (void)rc;
     if (ctx->T32 == 0)
         return fail(ctx, SLR_EUNSUPPORTED, "network too large for the fused FP32 kernel (d=%d, widest=%d)",
                     ctx->nf.d, ctx->nf.n_max_pad);
@@ -365,6 +383,8 @@ void slr_default_options(slr_options *opt) {
     opt->relax_mode = SLR_RELAX_NEURIFY;
     opt->fp64_recheck = 1;
     opt->record_leaves = 0;
+    opt->profile = 0;
+    opt->reserved = 0;
     opt->frontier_cap = (int64_t)1 << 24;
     opt->leaf_cap = (int64_t)1 << 22;
 }
@@ -415,8 +435,10 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->scratch);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return SLR_OK;
@@ -429,6 +451,7 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
         return fail(ctx, SLR_EINVAL, "relax_mode %d unknown", opt->relax_mode);
     if (opt->frontier_cap < 2 || opt->frontier_cap > ((int64_t)1 << 34))
         return fail(ctx, SLR_EINVAL, "frontier_cap %lld out of range", (long long)opt->frontier_cap);
+    if (opt->reserved != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
     if (opt->record_leaves && (opt->leaf_cap < 1 || opt->leaf_cap > ((int64_t)1 << 34)))
         return fail(ctx, SLR_EINVAL, "leaf_cap %lld out of range", (long long)opt->leaf_cap);
     if (opt->relax_mode != ctx->opt.relax_mode) ctx->dev_dirty = true;
@@ -534,12 +557,15 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         cnt[best] += 1;
         masks[best] |= 1ull << (D - 1 - t);
     }
-    ctx->h_stage.resize(root.size() * sizeof(double) + masks.size() * sizeof(unsigned long long));
-    std::memcpy(ctx->h_stage.data(), root.data(), root.size() * sizeof(double));
-    std::memcpy(ctx->h_stage.data() + root.size() * sizeof(double), masks.data(), masks.size() * sizeof(unsigned long long));
-    CK(ctx, cudaMemcpyAsync(ctx->root, ctx->h_stage.data(), root.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->masks, ctx->h_stage.data() + root.size() * sizeof(double),
-                            masks.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t root_bytes = root.size() * sizeof(double);
+    const size_t mask_bytes = masks.size() * sizeof(unsigned long long);
+    if ((rc = ensure_stage(ctx, root_bytes + mask_bytes))) return rc;
+    std::memcpy(ctx->h_stage, root.data(), root_bytes);
+    std::memcpy(ctx->h_stage + root_bytes, masks.data(), mask_bytes);
+    CK(ctx, cudaMemcpyAsync(ctx->root, ctx->h_stage, root_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->masks, ctx->h_stage + root_bytes, mask_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    const int64_t h2d = ctx->h2d_pending + (int64_t)(root_bytes + mask_bytes);
+    ctx->h2d_pending = 0;
     CK(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(slr::LevelCounters), ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
     CK(ctx, slr::launch_init_count(ctx->codes[0], ctx->ctr, ctx->stream));
@@ -547,6 +573,17 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     const bool leaves = ctx->opt.record_leaves != 0;
     const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0;
     const int compact_grid = std::max(1, ctx->sm_count * 4);
+    const bool prof = ctx->opt.profile != 0;
+    const size_t n_prof = prof ? (size_t)(D + 1) * 6 : 0;
+    while (ctx->prof_ev.size() < n_prof) {
+        cudaEvent_t e;
+        CK(ctx, cudaEventCreate(&e));
+        ctx->prof_ev.push_back(e);
+    }
+    auto mark = [&](int t, int slot) -> cudaError_t {
+        return prof ? cudaEventRecord(ctx->prof_ev[(size_t)t * 6 + slot], ctx->stream) : cudaSuccess;
+    };
+    int64_t launches = 1;
     CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
     for (int t = 0; t <= D; ++t) {
         slr::BoxSource src{};
@@ -566,7 +603,10 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         o.near_cap = ctx->near_cap;
         o.tie_count = &ctx->ctr->ties;
         o.status = ctx->status;
+        CK(ctx, mark(t, 0));
         CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->grid32, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+        CK(ctx, mark(t, 1));
+        ++launches;
         if (recheck) {
             slr::BoxSource s2 = src;
             s2.index = ctx->near_list;
@@ -577,10 +617,15 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
             o2.tie_count = &ctx->ctr->ties;
             o2.status = ctx->status;
             CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->sm_count, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
+            ++launches;
         }
+        CK(ctx, mark(t, 2));
+        CK(ctx, mark(t, 4));
         CK(ctx, slr::launch_compact(ctx->codes[t & 1], ctx->cls, ctx->codes[(t + 1) & 1], ctx->ctr, ctx->status,
                                     ctx->cap, t, D, leaves ? ctx->leaf_codes : nullptr, ctx->leaf_depth,
                                     ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream));
+        CK(ctx, mark(t, 5));
+        ++launches;
     }
     CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost, ctx->stream));
@@ -609,6 +654,20 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     out->rechecked = recheck ? rech : 0;
     out->levels = levels;
     out->device_ms = ms;
+    out->launches = launches;
+    out->h2d_bytes = h2d;
+    out->d2h_bytes = (int64_t)(sizeof(slr::LevelCounters) + sizeof(unsigned int));
+    if (prof) {
+        for (int t = 0; t <= D; ++t) {
+            float a = 0.f, b = 0.f, c2 = 0.f;
+            cudaEventElapsedTime(&a, ctx->prof_ev[(size_t)t * 6 + 0], ctx->prof_ev[(size_t)t * 6 + 1]);
+            cudaEventElapsedTime(&b, ctx->prof_ev[(size_t)t * 6 + 1], ctx->prof_ev[(size_t)t * 6 + 2]);
+            cudaEventElapsedTime(&c2, ctx->prof_ev[(size_t)t * 6 + 4], ctx->prof_ev[(size_t)t * 6 + 5]);
+            out->kernel_ms[0] += a;
+            out->kernel_ms[1] += b;
+            out->kernel_ms[2] += c2;
+        }
+    }
     ctx->n_leaves = leaves ? (int64_t)c.leaves : 0;
     ctx->leaves_valid = leaves;
     const unsigned st = *ctx->h_status;

@@ -64,6 +64,18 @@ def test_null_context_is_rejected_without_a_gpu(lib):
 
 def test_result_struct_matches_header_size(lib):
     import paper_2312_05890_gb300 as pkg
-    # 5 u64 + 2 i32 + 4 * 64 u64 + double
-    assert ctypes.sizeof(pkg.slr_result) == 5 * 8 + 2 * 4 + 4 * 64 * 8 + 8
-    assert ctypes.sizeof(pkg.slr_options) == 4 * 4 + 2 * 8
+    src = (
+        '#include <stdio.h>\n#include <stddef.h>\n#include "slrcount.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu", sizeof(slr_result), sizeof(slr_options),'
+        ' offsetof(slr_result, device_ms), offsetof(slr_options, frontier_cap)); return 0;}\n')
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "t.c")
+        exe = os.path.join(td, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert sizes[0] == ctypes.sizeof(pkg.slr_result)
+    assert sizes[1] == ctypes.sizeof(pkg.slr_options)
+    assert sizes[2] == pkg.slr_result.device_ms.offset
+    assert sizes[3] == pkg.slr_options.frontier_cap.offset
