@@ -160,6 +160,30 @@ int slr_leaves(slr_ctx *ctx, int64_t cap, uint64_t *codes, uint8_t *depth,
  * widest-side schedule), D entries. */
 int slr_schedule(slr_ctx *ctx, int D, int32_t *dims);
 
+/* slr_count for callers that cannot allocate GPU memory.  The paper has no
+ * counterpart: this entry exists for programs that set the library up once
+ * and then count from code where cudaMalloc/cudaFree are not allowed (while a
+ * framework's caching allocator holds the device memory, inside a real-time
+ * loop that must not stall on allocation, or while capturing a CUDA graph).
+ *
+ * Same arguments, result and classification as slr_count, but every scratch
+ * buffer (two frontiers of path codes, class bytes, the FP64 re-check list,
+ * level counters, root box and split masks) lives in one fixed device array
+ * of about 4.8 MB that the library defines at file scope: each GPU that loads
+ * the library holds it until the process exits.  Limits: at most 262144
+ * boxes per level and 65536 re-checked boxes per level; a count that needs
+ * more returns SLR_EOVERFLOW (its result is then incomplete).  Leaves are not
+ * recorded, slr_schedule is not updated and profile timing is not taken.
+ *
+ * The network and property must already be on the device: call slr_count (or
+ * slr_bounds with n >= 1) once after setting them, else SLR_ESTATE.  The
+ * first call on a device looks up the array's device address (a CUDA runtime
+ * query, no allocation); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (two contexts
+ * or streams at once on one device) race and give wrong counts; run them one
+ * after another.  Each call clears the counters it needs before use. */
+int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out);
+
 /* Message of the last failed call on this context ("" if none).  With a NULL
  * context, the message of the last failed slr_create on this thread. */
 const char *slr_last_error(const slr_ctx *ctx);

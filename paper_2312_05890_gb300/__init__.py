@@ -27,7 +27,7 @@ MAX_LEVELS = 63
 # Names the header declares (checked by the CPU test that loads the library).
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
-           "slr_last_error")
+           "slr_count_noalloc", "slr_last_error")
 
 
 class SlrError(RuntimeError):
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "slr_bounds": (ctypes.c_int, [P, i64, P, P, P, P, P, P, ctypes.c_int]),
         "slr_leaves": (ctypes.c_int, [P, i64, P, P, P, ctypes.POINTER(i64)]),
         "slr_schedule": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "slr_count_noalloc": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
         "slr_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -220,6 +221,14 @@ def slr_schedule(ctx, D: int):
     return out
 
 
+def slr_count_noalloc(ctx, D: int) -> dict:
+    """slr_count without any GPU allocation (fixed scratch inside the library; see the header)."""
+    lib = load_library()
+    res = slr_result()
+    _check(lib, ctx, lib.slr_count_noalloc(ctx, int(D), ctypes.byref(res)))
+    return res.to_dict()
+
+
 def slr_last_error(ctx) -> str:
     return load_library().slr_last_error(ctx).decode()
 
@@ -277,6 +286,9 @@ class Counter:
 
     def count(self, D: int) -> dict:
         return slr_count(self.ctx, D)
+
+    def count_noalloc(self, D: int) -> dict:
+        return slr_count_noalloc(self.ctx, D)
 
     def bounds(self, lo, hi, want_rows=True, want_cls=True, want_err=False):
         return slr_bounds(self.ctx, lo, hi, self.R, want_rows, want_cls, want_err)

@@ -9,6 +9,7 @@
 
 #include "slrcount.h"
 #include "slr_kernels.h"
+#include "slr_noalloc.h"
 
 namespace {
 
@@ -374,6 +375,38 @@ int check_ready(slr_ctx *ctx) {
 }
 
 }  // namespace
+
+int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!ctx->has_net || !ctx->has_box || !ctx->has_prop)
+        return fail(ctx, SLR_ESTATE, "network, box and property must be set before counting");
+    if ((int)ctx->lo.size() != ctx->widths[0])
+        return fail(ctx, SLR_EINVAL, "box has %zu dimensions but the network has %d inputs", ctx->lo.size(),
+                    ctx->widths[0]);
+    if (ctx->dev_dirty || !ctx->net_buf)
+        return fail(ctx, SLR_ESTATE,
+                    "slr_count_noalloc needs the network and property on the device: call slr_count (or "
+                    "slr_bounds with n >= 1) once after setting them");
+    v->device = ctx->device;
+    v->stream = ctx->stream;
+    v->d = ctx->widths[0];
+    v->T32 = ctx->T32;
+    v->grid32 = ctx->grid32;
+    v->T64 = ctx->T64;
+    v->sm_count = ctx->sm_count;
+    v->smem32 = ctx->smem32;
+    v->smem64 = ctx->smem64;
+    v->nf = &ctx->nf;
+    v->nd = &ctx->nd;
+    v->lo = ctx->lo.data();
+    v->hi = ctx->hi.data();
+    v->fp64_recheck = ctx->opt.fp64_recheck;
+    v->ev0 = ctx->ev0;
+    v->ev1 = ctx->ev1;
+    return SLR_OK;
+}
+
+int slr_internal_fail(slr_ctx *ctx, int code, const char *msg) { return fail(ctx, code, "%s", msg); }
 
 extern "C" {
 
