@@ -315,7 +315,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
             "count": {"unsafe_lo": last["unsafe_lo"], "unsafe_hi": last["unsafe_hi"], "boxes": last["boxes"],
-                      "rechecked": last["rechecked"], "tie_leaves": last["tie_leaves"]},
+                      "rechecked": last["rechecked"], "tie_leaves": last["tie_leaves"],
+                      "tile_boxes_threads": last["tile"]},
             "kernel_ms_per_step": {"eval_f32": kern[0] / args.steps, "recheck_f64": kern[1] / args.steps,
                                    "compact": kern[2] / args.steps},
             "wall_s": wall,

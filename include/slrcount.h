@@ -56,8 +56,13 @@ enum { SLR_RELAX_NEURIFY = 0, SLR_RELAX_PAPER_LITERAL = 1 };
 /* Arithmetic of the symbolic contraction U' = W+ U + W- L + b, L' = W+ L + W- U + b.
  * FP32: IEEE FP32 FMA on the CUDA cores (the constant terms as float-float
  *   pairs); every rounding is bounded a priori and the bounds are widened
- *   outward by that amount, so every bound stays sound. */
-enum { SLR_PREC_FP32 = 0 };
+ *   outward by that amount, so every bound stays sound.
+ * TC_TF32: the contraction on the tensor cores (tcgen05) with operands split
+ *   into two TF32 pieces (three products, FP32 accumulation), widened by its
+ *   own a-priori bound; boxes whose class depends on that widening are
+ *   re-bounded by the FP32 path (and, if still needed, in FP64).  Needs every
+ *   layer and the property at most 64 wide (SLR_EUNSUPPORTED otherwise). */
+enum { SLR_PREC_FP32 = 0, SLR_PREC_TC_TF32 = 1 };
 
 typedef struct {
     int32_t precision;      /* SLR_PREC_*; default SLR_PREC_FP32 */
@@ -93,6 +98,9 @@ typedef struct {
     int64_t launches;       /* kernels launched by the count */
     int64_t h2d_bytes;      /* host-to-device bytes copied by the count (inputs, schedule) */
     int64_t d2h_bytes;      /* device-to-host bytes copied by the count (counters, status) */
+    int32_t tile_boxes;     /* boxes per CTA of the FP32 evaluation kernel (chosen by timing) */
+    int32_t tile_threads;   /* threads per CTA of the FP32 evaluation kernel */
+    uint64_t rechecked_fp32; /* TC_TF32: boxes re-bounded by the FP32 path */
 } slr_result;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to

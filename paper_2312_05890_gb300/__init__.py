@@ -22,6 +22,7 @@ STATUS = {0: "SLR_OK", -1: "SLR_EINVAL", -2: "SLR_ENOMEM", -3: "SLR_ECUDA", -4: 
 SAFE, UNSAFE, UNDECIDED = 0, 1, 2
 RELAX_NEURIFY, RELAX_PAPER_LITERAL = 0, 1
 PREC_FP32 = 0
+PREC_TC_TF32 = 1
 MAX_LEVELS = 63
 
 # Names the header declares (checked by the CPU test that loads the library).
@@ -52,7 +53,9 @@ class slr_result(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("level_boxes", _U64A), ("level_safe", _U64A),
                 ("level_unsafe", _U64A), ("level_undecided", _U64A), ("device_ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double * 3), ("launches", ctypes.c_int64),
-                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
+                ("rechecked_fp32", ctypes.c_uint64)]
 
     def to_dict(self):
         n = self.depth + 1
@@ -61,6 +64,8 @@ class slr_result(ctypes.Structure):
                     levels=int(self.levels), device_ms=float(self.device_ms),
                     kernel_ms=[float(x) for x in self.kernel_ms], launches=int(self.launches),
                     h2d_bytes=int(self.h2d_bytes), d2h_bytes=int(self.d2h_bytes),
+                    tile=(int(self.tile_boxes), int(self.tile_threads)),
+                    rechecked_fp32=int(self.rechecked_fp32),
                     level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 

@@ -57,9 +57,17 @@ struct slr_ctx {
     void *net_buf = nullptr;
     slr::NetParams<float> nf{};
     slr::NetParams<double> nd{};
-    int T32 = 0, T64 = 0;
+    int T32 = 0, T64 = 0, NT32 = 0, NT64 = 0;
     size_t smem32 = 0, smem64 = 0;
     int grid32 = 0, grid64 = 0;
+    void *tc_buf = nullptr;               // tensor-core weight images
+    slr::TcParams tcp{};
+    int T_tc = 0, grid_tc = 0;
+    size_t smem_tc = 0;
+    bool tc_ok = false;
+    int64_t *near_list2 = nullptr;
+    std::string tuned_key;                // network shape the FP32 tile choice was timed for
+    int tuned_T = 0, tuned_NT = 0;
 
     int64_t cap = 0, near_cap = 0;
     uint64_t *codes[2] = {nullptr, nullptr};
@@ -231,25 +239,30 @@ void layout_params(slr_ctx *ctx, const HostLayers<Real> &L, unsigned char *dev, 
     p.relax_mode = ctx->opt.relax_mode;
 }
 
-// Pick the tile size with the most boxes resident per SM that fits.
+struct TileChoice {
+    int T = 0, NT = 0, blocks = 0;
+    size_t smem = 0;
+};
+
+// Every (boxes per CTA, threads per CTA) the fused kernel can run this network with.
 template <typename Real>
-int choose_tile(const slr::NetParams<Real> &p, size_t &smem, int &blocks_per_sm) {
-    int bestT = 0;
-    long best = 0;
-    for (int T : slr::kTileSizes) {
-        const size_t s = slr::eval_smem_bytes<Real>(T, p.d, p.R, p.n_max_pad, p.n_in_max);
-        if (s > (size_t)kMaxSmem) continue;
-        const int nb = sizeof(Real) == 4 ? slr::eval_blocks_per_sm_f32(T, s) : slr::eval_blocks_per_sm_f64(T, s);
-        if (nb <= 0) continue;
-        const long boxes = (long)nb * T;
-        if (boxes > best) {
-            best = boxes;
-            bestT = T;
-            smem = s;
-            blocks_per_sm = nb;
+std::vector<TileChoice> tile_candidates(const slr::NetParams<Real> &p) {
+    std::vector<TileChoice> out;
+    for (int NT : slr::kThreadCounts) {
+        for (int T : slr::kTileSizes) {
+            TileChoice c;
+            c.T = T;
+            c.NT = NT;
+            c.smem = slr::eval_smem_bytes<Real>(T, p.d, p.R, p.n_max_pad, p.n_in_max);
+            if (c.smem > (size_t)kMaxSmem) continue;
+            if (slr::eval_gemm_items(T, p.d, p.n_max_pad) > 2 * NT) continue;
+            c.blocks = sizeof(Real) == 4 ? slr::eval_blocks_per_sm_f32(T, NT, c.smem)
+                                         : slr::eval_blocks_per_sm_f64(T, NT, c.smem);
+            if (c.blocks <= 0) continue;
+            out.push_back(c);
         }
     }
-    return bestT;
+    return out;
 }
 
 int ensure_stage(slr_ctx *ctx, size_t bytes) {
@@ -259,6 +272,183 @@ int ensure_stage(slr_ctx *ctx, size_t bytes) {
     ctx->h_stage_bytes = 0;
     CK(ctx, cudaMallocHost(&ctx->h_stage, bytes));
     ctx->h_stage_bytes = bytes;
+    return SLR_OK;
+}
+
+float tf32_host(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;
+    u = (u + 0x1000u) & 0xffffe000u;   // nearest, ties away from zero, 10 fraction bits
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Weight images of the tensor-core path (see slr_eval_tc.cu): for each layer
+// k >= 1, A = [W ; |W|] split into TF32 hi and lo in the K-major shared-memory
+// layout, then the float W^T used by the constant dot products.
+int build_tc(slr_ctx *ctx, const HostLayers<float> &L) {
+    ctx->tc_ok = false;
+    const slr::NetParams<float> &nf = ctx->nf;
+    const int K = nf.K;
+    if (K < 2) return fail(ctx, SLR_EUNSUPPORTED, "the tensor-core path needs at least one hidden layer");
+    int kmax = 8;
+    for (int k = 1; k < K; ++k) {
+        if (nf.n[k] > slr::kTcMaxWidth || nf.n[k + 1] > slr::kTcMaxWidth)
+            return fail(ctx, SLR_EUNSUPPORTED, "the tensor-core path needs layers and property at most %d wide",
+                        slr::kTcMaxWidth);
+        // B holds the inputs of layer k and, after the product, its outputs
+        kmax = std::max(kmax, std::max((nf.n[k] + 7) & ~7, (nf.n[k + 1] + 7) & ~7));
+    }
+    slr::TcParams &tp = ctx->tcp;
+    std::memset(&tp, 0, sizeof tp);
+    tp.sbo = (kmax / 4) * slr::kTcLbo;
+    tp.a_bytes = 16 * tp.sbo;
+    tp.NCg = 2 * nf.d + 3;
+    auto boff = [&](int r, int kk) { return (r / 8) * tp.sbo + (kk / 4) * slr::kTcLbo + (r % 8) * 16 + (kk % 4) * 4; };
+    std::vector<size_t> offs(K, 0);
+    size_t total = 0;
+    for (int k = 1; k < K; ++k) {
+        const int n_in = nf.n[k], n_out = nf.n[k + 1], Mpad = (n_out + 7) & ~7;
+        const size_t wb = ((size_t)n_in * Mpad * 4 + 15) & ~(size_t)15;
+        tp.img_bytes[k] = (int)(2 * (size_t)tp.a_bytes + wb);
+        tp.k_pad[k] = (n_in + 7) & ~7;
+        tp.img_max = std::max(tp.img_max, tp.img_bytes[k]);
+        offs[k] = total;
+        total += ((size_t)tp.img_bytes[k] + 255) & ~(size_t)255;
+    }
+    tp.k_pad[0] = (nf.n[0] + 7) & ~7;
+    std::vector<unsigned char> img(total, 0);
+    for (int k = 1; k < K; ++k) {
+        const int n_in = nf.n[k], n_out = nf.n[k + 1], Mpad = (n_out + 7) & ~7;
+        unsigned char *hi = img.data() + offs[k];
+        unsigned char *lo = hi + tp.a_bytes;
+        float *w = reinterpret_cast<float *>(hi + 2 * tp.a_bytes);
+        const std::vector<float> &Wt = L.W[k];   // transposed: [i * n_out + p]
+        for (int p = 0; p < n_out; ++p) {
+            for (int i = 0; i < n_in; ++i) {
+                const float v = Wt[(size_t)i * n_out + p];
+                const float h = tf32_host(v);
+                const float l = tf32_host(v - h);
+                const float ah = std::fabs(h);
+                const float al = v >= 0.f ? l : -l;
+                std::memcpy(hi + boff(p, i), &h, 4);
+                std::memcpy(lo + boff(p, i), &l, 4);
+                std::memcpy(hi + boff(64 + p, i), &ah, 4);
+                std::memcpy(lo + boff(64 + p, i), &al, 4);
+                w[(size_t)i * Mpad + p] = v;
+            }
+        }
+    }
+    if (ctx->tc_buf) {
+        cudaFree(ctx->tc_buf);
+        ctx->tc_buf = nullptr;
+    }
+    CK(ctx, cudaMalloc(&ctx->tc_buf, total));
+    CK(ctx, cudaMemcpy(ctx->tc_buf, img.data(), total, cudaMemcpyHostToDevice));
+    ctx->h2d_pending += (int64_t)total;
+    for (int k = 1; k < K; ++k) tp.img[k] = (const unsigned char *)ctx->tc_buf + offs[k];
+    // the most boxes per CTA whose B operand fits N <= 256 and shared memory
+    ctx->T_tc = 0;
+    for (int T : slr::kTileSizes) {
+        slr::TcParams t2 = tp;
+        t2.Npad = (tp.NCg * T + 15) & ~15;
+        if (t2.Npad > 256) continue;
+        t2.b_bytes = (t2.Npad / 8) * tp.sbo;
+        const size_t smem = slr::eval_tc_smem_bytes(T, nf, t2);
+        if (smem > (size_t)kMaxSmem) continue;
+        tp = t2;
+        ctx->T_tc = T;
+        ctx->smem_tc = smem;
+        break;
+    }
+    if (!ctx->T_tc) return fail(ctx, SLR_EUNSUPPORTED, "no tensor-core tile fits (d=%d)", nf.d);
+    tp.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(tp.Npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    ctx->grid_tc = ctx->sm_count * (ctx->smem_tc * 2 <= (size_t)kMaxSmem ? 2 : 1);
+    ctx->tc_ok = true;
+    return SLR_OK;
+}
+
+int ensure_scratch(slr_ctx *ctx, size_t bytes);
+
+// Time every tile choice of the FP32 kernel on a fixed set of boxes (sides 1/16
+// of the root box, or of [-0.05, 0.05]^d without one) and keep the fastest.
+// The result is kept per network shape, so new weights of the same shape reuse it.
+int autotune(slr_ctx *ctx, const std::vector<TileChoice> &cands, TileChoice &best) {
+    char key[256];
+    int kl = std::snprintf(key, sizeof key, "R%d r%d", (int)ctx->e.size(), ctx->opt.relax_mode);
+    for (int w : ctx->widths) kl += std::snprintf(key + kl, sizeof key - kl, " %d", w);
+    if (ctx->tuned_key == key) {
+        for (const TileChoice &c : cands)
+            if (c.T == ctx->tuned_T && c.NT == ctx->tuned_NT) {
+                best = c;
+                return SLR_OK;
+            }
+    }
+    const int d = ctx->widths[0];
+    int64_t n = 16384;
+    while (n > 1024 && (size_t)n * d * 8 > ((size_t)64 << 20)) n /= 2;
+    const size_t need = align_up((size_t)n * d * 2 * sizeof(float)) + align_up((size_t)n);
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    std::vector<float> h((size_t)n * d * 2);
+    uint64_t st = 0x9e3779b97f4a7c15ull;
+    auto rnd = [&]() {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        return (double)(st >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int64_t k = 0; k < n; ++k) {
+        for (int i = 0; i < d; ++i) {
+            double a = -0.05, w = 0.1;
+            if (ctx->has_box && (int)ctx->lo.size() == d) {
+                a = ctx->lo[i];
+                w = (double)ctx->hi[i] - ctx->lo[i];
+            }
+            const double side = w / 16.0;
+            const double lo = a + (w - side) * rnd();
+            h[(size_t)k * d + i] = (float)lo;
+            h[(size_t)n * d + (size_t)k * d + i] = (float)(lo + side);
+        }
+    }
+    float *dlo = (float *)ctx->scratch;
+    float *dhi = dlo + (size_t)n * d;
+    uint8_t *dcls = (uint8_t *)ctx->scratch + align_up((size_t)n * d * 2 * sizeof(float));
+    CK(ctx, cudaMemcpyAsync(dlo, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    slr::BoxSource src{};
+    src.mode = 1;
+    src.n_explicit = n;
+    src.lo = dlo;
+    src.hi = dhi;
+    src.cap = n;
+    slr::EvalOutputs o{};
+    o.cls = dcls;
+    if (!ctx->status) {
+        CK(ctx, cudaMalloc(&ctx->status, sizeof(unsigned int)));
+        CK(ctx, cudaMallocHost(&ctx->h_status, sizeof(unsigned int)));
+    }
+    o.status = ctx->status;
+    float best_ms = 1e30f;
+    for (const TileChoice &c : cands) {
+        const int grid = (int)std::min<int64_t>((n + c.T - 1) / c.T, (int64_t)c.blocks * ctx->sm_count);
+        float ms = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+            CK(ctx, slr::launch_eval_f32(c.T, c.NT, grid, c.smem, ctx->stream, ctx->nf, src, o, 0));
+            CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+            CK(ctx, cudaEventSynchronize(ctx->ev1));
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1);
+            if (rep > 0) ms += t;     // the first run warms the caches
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    ctx->tuned_key = key;
+    ctx->tuned_T = best.T;
+    ctx->tuned_NT = best.NT;
     return SLR_OK;
 }
 
@@ -287,15 +477,35 @@ int prepare_device(slr_ctx *ctx) {
     CK(ctx, cudaMemcpyAsync(ctx->net_buf, ctx->h_stage, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->h2d_pending += (int64_t)bytes;
-    int bps = 0;
-    ctx->T32 = choose_tile(ctx->nf, ctx->smem32, bps);
     (void)rc;
-    if (ctx->T32 == 0)
+    const std::vector<TileChoice> c32 = tile_candidates(ctx->nf);
+    if (c32.empty())
         return fail(ctx, SLR_EUNSUPPORTED, "network too large for the fused FP32 kernel (d=%d, widest=%d)",
                     ctx->nf.d, ctx->nf.n_max_pad);
-    ctx->grid32 = bps * ctx->sm_count;
-    ctx->T64 = choose_tile(ctx->nd, ctx->smem64, bps);
-    ctx->grid64 = ctx->T64 ? bps * ctx->sm_count : 0;
+    TileChoice best = c32[0];
+    if (c32.size() > 1) {
+        if ((rc = autotune(ctx, c32, best))) return rc;
+    }
+    ctx->T32 = best.T;
+    ctx->NT32 = best.NT;
+    ctx->smem32 = best.smem;
+    ctx->grid32 = best.blocks * ctx->sm_count;
+    // FP64 re-check: short lists, so the smallest tiles spread them over the most SMs
+    const std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
+    ctx->T64 = 0;
+    for (const TileChoice &c : c64) {
+        if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT < ctx->NT64)) {
+            ctx->T64 = c.T;
+            ctx->NT64 = c.NT;
+            ctx->smem64 = c.smem;
+            ctx->grid64 = c.blocks * ctx->sm_count;
+        }
+    }
+    if (ctx->opt.precision == SLR_PREC_TC_TF32) {
+        if ((rc = build_tc(ctx, Lf))) return rc;
+    } else {
+        ctx->tc_ok = false;
+    }
     ctx->dev_dirty = false;
     return SLR_OK;
 }
@@ -315,9 +525,11 @@ void free_count_buffers(slr_ctx *ctx) {
     cudaFree(ctx->codes[1]);
     cudaFree(ctx->cls);
     cudaFree(ctx->near_list);
+    cudaFree(ctx->near_list2);
     ctx->codes[0] = ctx->codes[1] = nullptr;
     ctx->cls = nullptr;
     ctx->near_list = nullptr;
+    ctx->near_list2 = nullptr;
     ctx->cap = 0;
 }
 
@@ -330,6 +542,7 @@ int ensure_count_buffers(slr_ctx *ctx) {
         CK(ctx, cudaMalloc(&ctx->cls, (size_t)cap));
         ctx->near_cap = std::max<int64_t>(1024, cap / 4);
         CK(ctx, cudaMalloc(&ctx->near_list, (size_t)ctx->near_cap * sizeof(int64_t)));
+        CK(ctx, cudaMalloc(&ctx->near_list2, (size_t)ctx->near_cap * sizeof(int64_t)));
         ctx->cap = cap;
     }
     if (!ctx->ctr) {
@@ -391,8 +604,11 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
     v->stream = ctx->stream;
     v->d = ctx->widths[0];
     v->T32 = ctx->T32;
+    v->NT32 = ctx->NT32;
     v->grid32 = ctx->grid32;
     v->T64 = ctx->T64;
+    v->NT64 = ctx->NT64;
+    v->grid64 = ctx->grid64;
     v->sm_count = ctx->sm_count;
     v->smem32 = ctx->smem32;
     v->smem64 = ctx->smem64;
@@ -458,6 +674,7 @@ int slr_destroy(slr_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_count_buffers(ctx);
     cudaFree(ctx->net_buf);
+    cudaFree(ctx->tc_buf);
     cudaFree(ctx->ctr);
     cudaFree(ctx->status);
     cudaFree(ctx->root);
@@ -479,7 +696,8 @@ int slr_destroy(slr_ctx *ctx) {
 
 int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
     if (!ctx || !opt) return fail(ctx, SLR_EINVAL, "null argument");
-    if (opt->precision != SLR_PREC_FP32) return fail(ctx, SLR_EUNSUPPORTED, "precision %d not built", opt->precision);
+    if (opt->precision != SLR_PREC_FP32 && opt->precision != SLR_PREC_TC_TF32)
+        return fail(ctx, SLR_EINVAL, "precision %d unknown", opt->precision);
     if (opt->relax_mode != SLR_RELAX_NEURIFY && opt->relax_mode != SLR_RELAX_PAPER_LITERAL)
         return fail(ctx, SLR_EINVAL, "relax_mode %d unknown", opt->relax_mode);
     if (opt->frontier_cap < 2 || opt->frontier_cap > ((int64_t)1 << 34))
@@ -487,7 +705,7 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
     if (opt->reserved != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
     if (opt->record_leaves && (opt->leaf_cap < 1 || opt->leaf_cap > ((int64_t)1 << 34)))
         return fail(ctx, SLR_EINVAL, "leaf_cap %lld out of range", (long long)opt->leaf_cap);
-    if (opt->relax_mode != ctx->opt.relax_mode) ctx->dev_dirty = true;
+    if (opt->relax_mode != ctx->opt.relax_mode || opt->precision != ctx->opt.precision) ctx->dev_dirty = true;
     ctx->opt = *opt;
     return SLR_OK;
 }
@@ -605,6 +823,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
 
     const bool leaves = ctx->opt.record_leaves != 0;
     const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0;
+    const bool use_tc = ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok;
     const int compact_grid = std::max(1, ctx->sm_count * 4);
     const bool prof = ctx->opt.profile != 0;
     const size_t n_prof = prof ? (size_t)(D + 1) * 6 : 0;
@@ -637,7 +856,37 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         o.tie_count = &ctx->ctr->ties;
         o.status = ctx->status;
         CK(ctx, mark(t, 0));
-        CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->grid32, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+        if (use_tc) {
+            // tier 1 on the tensor cores; boxes whose class depends on its
+            // widening are re-bounded by the FP32 path (tier 2), and those whose
+            // class still depends on the FP32 widening in FP64 (tier 3)
+            o.near_list = ctx->near_list;
+            CK(ctx, slr::launch_eval_tc(ctx->T_tc, ctx->grid_tc, ctx->smem_tc, ctx->stream, ctx->nf, ctx->tcp, src, o, 0));
+            CK(ctx, mark(t, 1));
+            ++launches;
+            slr::BoxSource s1 = src;
+            s1.index = ctx->near_list;
+            s1.index_count = &ctx->ctr->near_n[t];
+            s1.cap = ctx->near_cap;
+            slr::EvalOutputs o1 = o;
+            o1.near_list = recheck ? ctx->near_list2 : nullptr;
+            o1.near_count = &ctx->ctr->near2_n[t];
+            CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->NT32, ctx->grid32, ctx->smem32, ctx->stream, ctx->nf, s1, o1, 0));
+            ++launches;
+            if (recheck) {
+                slr::BoxSource s2 = src;
+                s2.index = ctx->near_list2;
+                s2.index_count = &ctx->ctr->near2_n[t];
+                s2.cap = ctx->near_cap;
+                slr::EvalOutputs o2{};
+                o2.cls = ctx->cls;
+                o2.tie_count = &ctx->ctr->ties;
+                o2.status = ctx->status;
+                CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
+                ++launches;
+            }
+        } else {
+        CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->NT32, ctx->grid32, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
         CK(ctx, mark(t, 1));
         ++launches;
         if (recheck) {
@@ -649,8 +898,9 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
             o2.cls = ctx->cls;
             o2.tie_count = &ctx->ctr->ties;
             o2.status = ctx->status;
-            CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->sm_count, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
+            CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
             ++launches;
+        }
         }
         CK(ctx, mark(t, 2));
         CK(ctx, mark(t, 4));
@@ -675,8 +925,9 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     out->tie_leaves = c.ties;
     out->depth = D;
     int levels = 0;
-    unsigned long long rech = 0;
+    unsigned long long rech = 0, rech2 = 0;
     for (int t = 0; t <= D; ++t) {
+        rech2 += std::min<unsigned long long>(c.near2_n[t], (unsigned long long)ctx->near_cap);
         out->level_boxes[t] = c.level_boxes[t];
         out->level_safe[t] = c.level_safe[t];
         out->level_unsafe[t] = c.level_unsafe[t];
@@ -684,11 +935,14 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         rech += std::min<unsigned long long>(c.near_n[t], (unsigned long long)ctx->near_cap);
         if (c.level_boxes[t]) levels = t + 1;
     }
-    out->rechecked = recheck ? rech : 0;
+    out->rechecked = recheck ? (use_tc ? rech2 : rech) : 0;
+    out->rechecked_fp32 = use_tc ? rech : 0;
     out->levels = levels;
     out->device_ms = ms;
     out->launches = launches;
     out->h2d_bytes = h2d;
+    out->tile_boxes = ctx->T32;
+    out->tile_threads = ctx->NT32;
     out->d2h_bytes = (int64_t)(sizeof(slr::LevelCounters) + sizeof(unsigned int));
     if (prof) {
         for (int t = 0; t <= D; ++t) {
@@ -710,6 +964,8 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         return fail(ctx, SLR_EOVERFLOW, "FP64 re-check list exceeded %lld boxes", (long long)ctx->near_cap);
     if (st & slr::kStatusLeafOverflow)
         return fail(ctx, SLR_EOVERFLOW, "leaf recording exceeded leaf_cap=%lld", (long long)ctx->opt.leaf_cap);
+    if (st & slr::kStatusTimeout)
+        return fail(ctx, SLR_ETIMEOUT, "a bounded wait on the tensor core gave up; the result is incomplete");
     return SLR_OK;
 }
 
@@ -766,9 +1022,16 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
         CK(ctx, cudaMallocHost(&ctx->h_status, sizeof(unsigned int)));
     }
     o.status = ctx->status;
-    const int64_t tiles = (n + ctx->T32 - 1) / ctx->T32;
-    const int grid = (int)std::min<int64_t>(tiles, ctx->grid32);
-    CK(ctx, slr::launch_eval_f32(ctx->T32, grid, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+    CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
+    if (ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok) {
+        const int64_t tiles = (n + ctx->T_tc - 1) / ctx->T_tc;
+        const int grid = (int)std::min<int64_t>(tiles, ctx->grid_tc);
+        CK(ctx, slr::launch_eval_tc(ctx->T_tc, grid, ctx->smem_tc, ctx->stream, ctx->nf, ctx->tcp, src, o, 0));
+    } else {
+        const int64_t tiles = (n + ctx->T32 - 1) / ctx->T32;
+        const int grid = (int)std::min<int64_t>(tiles, ctx->grid32);
+        CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->NT32, grid, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+    }
     if (!on_device) {
         if (row_lo) {
             CK(ctx, cudaMemcpyAsync(row_lo, drl, (size_t)n * R * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -778,7 +1041,10 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
             CK(ctx, cudaMemcpyAsync(row_err, dre, (size_t)n * R * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
         if (cls) CK(ctx, cudaMemcpyAsync(cls, dcls, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
     }
+    CK(ctx, cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*ctx->h_status & slr::kStatusTimeout)
+        return fail(ctx, SLR_ETIMEOUT, "a bounded wait on the tensor core gave up; the bounds are incomplete");
     return SLR_OK;
 }
 

@@ -39,7 +39,33 @@ enum : uint32_t {
     kStatusOverflow = 1u,      // a level exceeded the frontier capacity
     kStatusNearOverflow = 2u,  // the FP64 re-check list overflowed
     kStatusLeafOverflow = 4u,  // leaf recording overflowed
+    kStatusTimeout = 8u,       // a bounded wait on the tensor core gave up
 };
+
+// Tensor-core path: operand layout constants and per-layer weight images.
+constexpr int kTcLbo = 144;       // bytes between core matrices along K (128 + 16 pad)
+constexpr int kTcTmemCols = 256;  // accumulator columns allocated per CTA
+constexpr int kTcMaxWidth = 64;   // widest layer the [W ; |W|] stacking in M = 128 allows
+
+struct TcParams {
+    const unsigned char *img[kMaxLayers];  // layer k >= 1: [A hi | A lo | W^T float], shared-memory image
+    int img_bytes[kMaxLayers];
+    int k_pad[kMaxLayers];                 // K of layer k's product: n[k] rounded up to 8
+    int a_bytes;                           // bytes of one A image (128 rows)
+    int img_max;                           // largest image, bytes
+    int b_bytes;                           // bytes of one B image (Npad rows)
+    int sbo;                               // bytes between 8-row groups of A and B
+    int NCg;                               // GEMM columns per box: 2d + 3
+    int Npad;                              // NCg * T rounded up to 16
+    uint32_t idesc;                        // tcgen05 instruction descriptor (tf32, M = 128, N = Npad)
+};
+
+// Relative rounding bound of one output of the split-TF32 product:
+// dropped lo*lo and TF32 rounding of the lo pieces (3 2^-22) plus FP32
+// accumulation, modelled as one 2^-23 rounding per product of the K terms.
+__host__ __device__ inline float tc_gamma(int k_pad) {
+    return (float)(k_pad + 8) * 0x1p-23f + 3.0f * 0x1p-22f;
+}
 
 // Directed-rounding arithmetic, one specialisation per working precision.
 template <typename Real> struct Arith;
@@ -139,20 +165,27 @@ struct LevelCounters {
     unsigned long long level_undecided[kMaxDepth + 2];
     unsigned long long frontier_n[kMaxDepth + 2];   // boxes at each level
     unsigned long long near_n[kMaxDepth + 2];       // re-check list length at each level
+    unsigned long long near2_n[kMaxDepth + 2];      // second re-check list (tensor-core path)
 };
 
 // Columns of one row of the state (see slr_eval.cuh): C coefficients, C
 // constant (hi), R coefficients, R constant, N, E, C constant (lo).
 __host__ __device__ inline int state_cols(int d) { return 2 * d + 5; }
 
+// Contraction tiles (8 rows x 4 columns) per CTA of the fused kernel; each of
+// its threads holds at most two in registers, so this must not exceed 2 x 256.
+__host__ __device__ inline int eval_gemm_items(int T, int d, int n_max_pad) {
+    return (n_max_pad / 8) * ((2 * d + 3) * T / 4);
+}
+
 // Shared-memory footprint of the fused evaluation kernel for a tile of T boxes.
 template <typename Real>
 __host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max_pad, int n_in_max) {
     const int NS = T * state_cols(d);
     size_t s = 0;
-    s += 2 * (size_t)n_max_pad * NS * sizeof(Real);        // two state buffers
+    s += (size_t)n_max_pad * NS * sizeof(Real);            // state, updated in place
+    s += 3 * (size_t)n_max_pad * T * sizeof(Real);         // next layer's constants (hi, lo, error)
     s += (size_t)n_in_max * n_max_pad * sizeof(Real);      // staged weights (transposed)
-    s += (size_t)n_max_pad * sizeof(Real);                 // staged bias
     s += 3 * (size_t)T * d * sizeof(Real);                 // box centres (hi, lo) and radii
     s += 3 * (size_t)T * R * sizeof(Real);                 // row lo / hi / E
     s += (size_t)T * sizeof(int64_t);                      // box indices

@@ -123,28 +123,45 @@ __device__ __forceinline__ Real uerr(Real x) {
     return Arith<Real>::mul_up(x, (Real)0.50001 * Arith<Real>::ulp2);
 }
 
+// Row accessors.  A row view R maps a column of one row (SIMT numbering: C
+// coefficients 0..d-1, C constant hi d, R coefficients d+1..2d, R constant
+// 2d+1, N 2d+2, E 2d+3, C constant lo 2d+4) to a Real& in shared memory.
+template <typename Real, int T>
+struct SimtLayout {
+    Real *S;
+    int NS;
+    struct Row {
+        Real *p;
+        __device__ __forceinline__ Real &operator()(int c) const { return p[c * T]; }
+    };
+    __device__ __forceinline__ Row row(int p, int b) const { return Row{S + p * NS + b}; }
+    // upper bound of |value| of a column (exact here)
+    __device__ __forceinline__ Real mag(int p, int b, int c) const { return Arith<Real>::abs(S[p * NS + c * T + b]); }
+    __device__ __forceinline__ void finish_row(int, int) const {}
+};
+
 // Concrete bounds of the raw equations U = C + R, L = C - R of one row over
 // the box (Sec. 2.2: const +- sum_j |coeff_j| in the normalised input), with
 // outward rounding so that they bound the stored equations exactly.
-template <typename Real, int T>
+template <typename Real>
 struct RowBounds {
     Real uu, lu, ul, ll;   // max U, min U, max L, min L
     Real NC, NR;           // sum |C_j| over coefficients, sum |R_j| incl. its constant
-    __device__ __forceinline__ void compute(const Real *row, int d, Real chi, Real clo) {
+    template <class Row>
+    __device__ __forceinline__ void compute(const Row &R, int d, Real chi, Real clo) {
         using A = Arith<Real>;
         Real SU = 0, SL = 0;
         NC = 0;
         NR = 0;
-        const Real *rr = row + (d + 1) * T;
         for (int j = 0; j < d; ++j) {
-            const Real c = row[j * T];
-            const Real r = rr[j * T];
+            const Real c = R(j);
+            const Real r = R(d + 1 + j);
             SU = A::add_up(SU, A::abs(c + r));
             SL = A::add_up(SL, A::abs(c - r));
             NC = A::add_up(NC, A::abs(c));
             NR = A::add_up(NR, A::abs(r));
         }
-        const Real rd = rr[d * T];
+        const Real rd = R(2 * d + 1);
         NR = A::add_up(NR, A::abs(rd));
         // |c +- r| <= |fl(c +- r)| (1 + u): cover the round-to-nearest of each term
         SU = A::mul_up(SU, (Real)1 + A::ulp2);
@@ -159,6 +176,9 @@ struct RowBounds {
 template <typename Real, int T, int NT>
 struct EvalTile {
     using A = Arith<Real>;
+    // FP32 carries the constants as compensated pairs; FP64 is precise enough
+    // with a plain FMA chain (its gamma_n error bound is ~1e-14 relative).
+    static constexpr bool kCompensated = sizeof(Real) == 4;
 
     // Column offsets of one row (times T in memory): C coefficients [0, d),
     // C constant hi (d), R coefficients [d+1, 2d+1), R constant (2d+1),
@@ -194,21 +214,22 @@ struct EvalTile {
     }
 
     // ---- layer 1: C = [W_1 diag(r) | W_1 m + b_1], R = 0 ------------------------
-    static __device__ void init_layer(Real *S, const NetParams<Real> &net, const Real *sMh,
-                                      const Real *sMl, const Real *sR, int NS) {
+    template <class L>
+    static __device__ void init_layer(const L &lay, const NetParams<Real> &net, const Real *sMh, const Real *sMl,
+                                      const Real *sR) {
         const int d = net.d;
         const int n1 = net.n[1];
         for (int item = threadIdx.x; item < n1 * T; item += NT) {
             const int p = item / T;
             const int b = item - p * T;
-            Real *row = S + p * NS + b;
+            const auto R = lay.row(p, b);
             const Real *w = net.W0 + (size_t)p * d;
             const Real bp = net.b[0][p];
             Real S1 = 0, s = bp, e = 0, sabs = A::abs(bp);
             for (int j = 0; j < d; ++j) {
                 const Real wj = w[j];
                 const Real c = A::mul_rn(wj, sR[b * d + j]);
-                row[j * T] = c;
+                R(j) = c;
                 S1 = A::add_up(S1, A::abs(c));
                 Real p1, pe, t, se;
                 two_prod<Real>(wj, sMh[b * d + j], p1, pe);
@@ -219,8 +240,8 @@ struct EvalTile {
             }
             Real chi, clo;
             two_sum<Real>(s, e, chi, clo);
-            row[cCh(d) * T] = chi;
-            row[cCl(d) * T] = clo;
+            R(cCh(d)) = chi;
+            R(cCl(d)) = clo;
             const Real g = gam<Real>(d + 2);
             Real E = A::add_up(uerr<Real>(S1),
                                A::mul_up(A::mul_up((Real)2 * g, g), A::mul_up(sabs, (Real)1 + gam<Real>(d))));
@@ -234,68 +255,148 @@ struct EvalTile {
                 }
                 E = A::add_up(E, fe);
             }
-            Real *rr = row + cR(d) * T;
-            for (int j = 0; j <= d; ++j) rr[j * T] = 0;
-            row[cN(d) * T] = S1;
-            row[cE(d) * T] = E;
+            for (int j = 0; j <= d; ++j) R(cR(d) + j) = 0;
+            R(cN(d)) = S1;
+            R(cE(d)) = E;
+        }
+    }
+
+    // ---- constants of the next layer, before the contraction overwrites the state --
+    // For output rows p0 = 2q and p0 + 1 and box b: the error-free constant dot
+    // product over the input rows, its error bound, and (last layer only) the
+    // rounding of the folded property weights, sum_i delta_pi |z_i| with
+    // |z_i| <= N_i + |C_i const| + E_i.  Written to sConst = [hi | lo | err].
+    // sW holds the layer's float weights transposed (row i, column p, stride Mpad).
+    template <class L>
+    static __device__ void const_phase(const L &lay, Real *sConst, const Real *sW, int Mpad,
+                                       const NetParams<Real> &net, int layer) {
+        const int d = net.d;
+        const int n_in = net.n[layer];
+        const int n_out = net.n[layer + 1];
+        const bool last = layer + 1 == net.K;
+        const Real *bias = net.b[layer];
+        const int nmp = net.n_max_pad;
+        const int pairs = (n_out + 1) / 2;
+        for (int item = threadIdx.x; item < pairs * T; item += NT) {
+            const int q = item / T;
+            const int b = item - q * T;
+            const int p0 = 2 * q;
+            const bool two = p0 + 1 < n_out;
+            Real s0 = bias[p0], e0 = 0, a0 = A::abs(s0);
+            Real s1 = two ? bias[p0 + 1] : (Real)0, e1 = 0, a1 = A::abs(s1);
+            Real f0 = 0, f1 = 0;
+            for (int i = 0; i < n_in; ++i) {
+                const auto Ri = lay.row(i, b);
+                const Real h = Ri(cCh(d));
+                const Real l = Ri(cCl(d));
+                const Real w0 = sW[i * Mpad + p0];
+                const Real w1 = sW[i * Mpad + p0 + 1];
+                if (kCompensated) {
+                    Real p1, pe, t, se;
+                    two_prod<Real>(w0, h, p1, pe);
+                    two_sum<Real>(s0, p1, t, se);
+                    s0 = t;
+                    e0 = A::fma_rn(w0, l, e0 + (pe + se));
+                    a0 = a0 + A::abs(p1);
+                    two_prod<Real>(w1, h, p1, pe);
+                    two_sum<Real>(s1, p1, t, se);
+                    s1 = t;
+                    e1 = A::fma_rn(w1, l, e1 + (pe + se));
+                    a1 = a1 + A::abs(p1);
+                } else {
+                    // float64: a plain FMA chain, |error| <= gamma_2n sum |w| (|h| + |l|)
+                    s0 = A::fma_rn(w0, h, A::fma_rn(w0, l, s0));
+                    s1 = A::fma_rn(w1, h, A::fma_rn(w1, l, s1));
+                    a0 = A::fma_rn(A::abs(w0), A::abs(h) + A::abs(l), a0);
+                    a1 = A::fma_rn(A::abs(w1), A::abs(h) + A::abs(l), a1);
+                }
+                if (last) {
+                    const Real z = A::add_up(A::add_up(lay.mag(i, b, cN(d)), A::abs(h)),
+                                             A::add_up(A::abs(l), lay.mag(i, b, cE(d))));
+                    f0 = A::add_up(f0, A::mul_up(net.fold_err[p0 * n_in + i], z));
+                    if (two) f1 = A::add_up(f1, A::mul_up(net.fold_err[(p0 + 1) * n_in + i], z));
+                }
+            }
+            const Real g = gam<Real>(kCompensated ? n_in + 2 : 2 * n_in + 2);
+            const Real g2 = kCompensated ? A::mul_up((Real)2 * g, g) : (Real)2 * g;
+            const Real ga = (Real)1 + gam<Real>(n_in);
+            Real hi, lo;
+            two_sum<Real>(s0, e0, hi, lo);
+            sConst[p0 * T + b] = hi;
+            sConst[(nmp + p0) * T + b] = lo;
+            Real err = A::mul_up(g2, A::mul_up(a0, ga));
+            if (last) err = A::add_up(err, A::add_up(f0, net.fold_berr[p0]));
+            sConst[(2 * nmp + p0) * T + b] = err;
+            if (two) {
+                two_sum<Real>(s1, e1, hi, lo);
+                sConst[(p0 + 1) * T + b] = hi;
+                sConst[(nmp + p0 + 1) * T + b] = lo;
+                err = A::mul_up(g2, A::mul_up(a1, ga));
+                if (last) err = A::add_up(err, A::add_up(f1, net.fold_berr[p0 + 1]));
+                sConst[(2 * nmp + p0 + 1) * T + b] = err;
+            }
         }
     }
 
     // ---- add the contraction's constant and error; returns (chi, clo, E) -------
-    static __device__ __forceinline__ void finish_contraction(Real *row, const Real *Sprev, const Real *sW, int Mpad,
-                                                              int p, int b, int d, int n_in, int NS, Real bias,
-                                                              Real &chi, Real &clo, Real &E) {
-        Real cerr;
-        const_dot(sW, Mpad, p, Sprev + cCh(d) * T + b, Sprev + cCl(d) * T + b, n_in, NS, bias, chi, clo, cerr);
-        // coefficients: a-priori gamma_n (sum_i |W_pi| N_i) from the |W| N column
-        const Real wN = row[cN(d) * T];
-        const Real g = gam<Real>(n_in);
-        Real eps = A::mul_up(g, A::mul_up(wN, (Real)1 + g));
+    // gcoef bounds the relative rounding of the contraction's coefficient
+    // columns (gamma_n * sum_i |W_pi| N_i, from the |W| N column).
+    template <class Row>
+    static __device__ __forceinline__ void finish_contraction(const Row &R, const Real *sConst, int nmp, int p, int b,
+                                                              int d, int n_in, Real gcoef, Real &chi, Real &clo,
+                                                              Real &E) {
+        chi = sConst[p * T + b];
+        clo = sConst[(nmp + p) * T + b];
+        const Real cerr = sConst[(2 * nmp + p) * T + b];
+        const Real wN = R(cN(d));
+        Real eps = A::mul_up(gcoef, A::mul_up(wN, (Real)1 + gcoef));
         eps = A::add_up(A::add_up(eps, cerr), (Real)(n_in + 4) * A::tiny);
-        // |W| E was summed in round-to-nearest from non-negative terms
-        E = A::add_up(A::mul_up(row[cE(d) * T], (Real)1 + (Real)2 * g), eps);
+        // |W| E was summed from non-negative terms with the same relative rounding
+        E = A::add_up(A::mul_up(R(cE(d)), (Real)1 + (Real)2 * gcoef), eps);
     }
 
     // ---- one hidden layer: constant, error, concrete bounds, ReLU relaxation ----
-    static __device__ void hidden_epilogue(Real *S, const Real *Sprev, const Real *sW, int Mpad,
-                                           const NetParams<Real> &net, int layer, int NS) {
+    template <class L>
+    static __device__ void hidden_epilogue(const L &lay, const Real *sConst, const NetParams<Real> &net, int layer,
+                                           Real gcoef) {
         const int d = net.d;
         const int nrows = net.n[layer];
         const int n_in = net.n[layer - 1];
-        const Real *bias = net.b[layer - 1];
         for (int item = threadIdx.x; item < nrows * T; item += NT) {
             const int p = item / T;
             const int b = item - p * T;
-            Real *row = S + p * NS + b;
-            Real *rr = row + cR(d) * T;
+            const auto R = lay.row(p, b);
+            const int cr = cR(d);
             Real chi, clo, E;
             if (layer > 1) {
-                finish_contraction(row, Sprev, sW, Mpad, p, b, d, n_in, NS, bias[p], chi, clo, E);
+                finish_contraction(R, sConst, net.n_max_pad, p, b, d, n_in, gcoef, chi, clo, E);
             } else {
-                chi = row[cCh(d) * T];
-                clo = row[cCl(d) * T];
-                E = row[cE(d) * T];
+                chi = R(cCh(d));
+                clo = R(cCl(d));
+                E = R(cE(d));
             }
-            RowBounds<Real, T> bd;
-            bd.compute(row, d, chi, clo);
+            RowBounds<Real> bd;
+            bd.compute(R, d, chi, clo);
             if (bd.ll >= (Real)0) {
                 // stable active: relu is the identity on [L - E, U + E] up to
                 // U + E >= lu + E >= 0, so the equations and E carry over
-                row[cCh(d) * T] = chi;
-                row[cCl(d) * T] = clo;
-                row[cN(d) * T] = A::add_up(bd.NC, bd.NR);
-                row[cE(d) * T] = E;
+                R(cCh(d)) = chi;
+                R(cCl(d)) = clo;
+                R(cN(d)) = A::add_up(bd.NC, bd.NR);
+                R(cE(d)) = E;
+                lay.finish_row(p, b);
                 continue;
             }
             if (bd.uu <= (Real)0) {
                 // stable inactive: relu(z) lies in [0, max(0, uu + E)]
-                for (int j = 0; j < d; ++j) row[j * T] = 0;
-                for (int j = 0; j <= d; ++j) rr[j * T] = 0;
-                row[cCh(d) * T] = 0;
-                row[cCl(d) * T] = 0;
-                row[cN(d) * T] = 0;
+                for (int j = 0; j < d; ++j) R(j) = 0;
+                for (int j = 0; j <= d; ++j) R(cr + j) = 0;
+                R(cCh(d)) = 0;
+                R(cCl(d)) = 0;
+                R(cN(d)) = 0;
                 const Real top = A::add_up(bd.uu, E);
-                row[cE(d) * T] = top > (Real)0 ? top : (Real)0;
+                R(cE(d)) = top > (Real)0 ? top : (Real)0;
+                lay.finish_row(p, b);
                 continue;
             }
             // unstable: U' = sig_u (U - l) and L' = sig_l L (Eq. 1).  Applied to
@@ -323,86 +424,106 @@ struct EvalTile {
             const Real pp = (sig_u + sig_l) * (Real)0.5;
             const Real qq = (sig_u - sig_l) * (Real)0.5;
             for (int j = 0; j < d; ++j) {
-                const Real c = row[j * T];
-                const Real r = rr[j * T];
-                row[j * T] = A::fma_rn(pp, c, qq * r);
-                rr[j * T] = A::fma_rn(qq, c, pp * r);
+                const Real c = R(j);
+                const Real r = R(cr + j);
+                R(j) = A::fma_rn(pp, c, qq * r);
+                R(cr + j) = A::fma_rn(qq, c, pp * r);
             }
-            const Real rd = rr[d * T];
+            const Real rd = R(cr + d);
             const Real hh = h * (Real)0.5;
             Real ph, pe, nh, nl;
             two_prod<Real>(pp, chi, ph, pe);
             const Real rest = pe + A::fma_rn(pp, clo, A::fma_rn(qq, rd, hh));
             two_sum<Real>(ph, rest, nh, nl);
-            row[cCh(d) * T] = nh;
-            row[cCl(d) * T] = nl;
-            rr[d * T] = A::fma_rn(qq, chi, A::fma_rn(qq, clo, A::fma_rn(pp, rd, hh)));
+            R(cCh(d)) = nh;
+            R(cCl(d)) = nl;
+            R(cr + d) = A::fma_rn(qq, chi, A::fma_rn(qq, clo, A::fma_rn(pp, rd, hh)));
             const Real sig_max = sig_u > sig_l ? sig_u : sig_l;
             const Real tot = A::add_up(A::add_up(bd.NC, bd.NR), A::add_up(A::abs(chi), A::abs(clo)));
             const Real mag = A::add_up(A::mul_up(sig_max, tot), h);
             const Real err = A::add_up(A::mul_up((Real)8 * A::ulp2, mag), (Real)(2 * d + 8) * A::tiny);
-            row[cE(d) * T] = A::add_up(E, err);
-            row[cN(d) * T] = A::mul_up(A::add_up(mag, A::add_up(err, err)), (Real)1 + (Real)4 * A::ulp2);
+            R(cE(d)) = A::add_up(E, err);
+            R(cN(d)) = A::mul_up(A::add_up(mag, A::add_up(err, err)), (Real)1 + (Real)4 * A::ulp2);
+            lay.finish_row(p, b);
         }
     }
 
     // ---- C' = W C, R' = |W| R over the coefficient, N and E columns ---------------
-    // The constant of C is not part of this product: the epilogue computes it
-    // with error-free transformations (const_dot).
-    static __device__ void contract(const Real *__restrict__ sIn, Real *__restrict__ sOut,
-                                    const Real *sW, int n_in, int Mpad, int d, int NS) {
-        const int QW = d * T / 4;             // quads of C coefficient columns
-        const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
-        const int Q = QW + QA;
-        const int G = Mpad / 8;
-        for (int item = threadIdx.x; item < G * Q; item += NT) {
-            const int g = item / Q;
-            const int q = item - g * Q;
-            const int p0 = g * 8;
-            const bool is_abs = q >= QW;
-            const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-            Real acc[8][4];
+    // The constant of C is not part of this product: const_phase computes it
+    // with error-free transformations.  The state is updated in place: every
+    // thread first accumulates its (at most kItems) 8 x 4 tiles in registers,
+    // then, after a barrier, overwrites the rows.
+    static constexpr int kItems = 2;
+
+    static __device__ __forceinline__ void tile_mac(const Real *wp, const Real *xp, int n_in, int Mpad, int NS,
+                                                    bool is_abs, Real (&acc)[8][4]) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = 0;
-            const Real *wp = sW + p0;
-            const Real *xp = sIn + j0;
-            if (is_abs) {
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+        if (is_abs) {
 #pragma unroll 2
-                for (int i = 0; i < n_in; ++i) {
-                    Real a0[4], a1[4], x[4];
-                    V4<Real>::ld(wp + i * Mpad, a0);
-                    V4<Real>::ld(wp + i * Mpad + 4, a1);
-                    V4<Real>::ld(xp + i * NS, x);
+            for (int i = 0; i < n_in; ++i) {
+                Real a0[4], a1[4], x[4];
+                V4<Real>::ld(wp + i * Mpad, a0);
+                V4<Real>::ld(wp + i * Mpad + 4, a1);
+                V4<Real>::ld(xp + i * NS, x);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < 4; ++c) {
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            acc[r][c] = A::fma_rn(A::abs(a0[r]), x[c], acc[r][c]);
-                            acc[r + 4][c] = A::fma_rn(A::abs(a1[r]), x[c], acc[r + 4][c]);
-                        }
-                    }
-                }
-            } else {
-#pragma unroll 2
-                for (int i = 0; i < n_in; ++i) {
-                    Real a0[4], a1[4], x[4];
-                    V4<Real>::ld(wp + i * Mpad, a0);
-                    V4<Real>::ld(wp + i * Mpad + 4, a1);
-                    V4<Real>::ld(xp + i * NS, x);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            acc[r][c] = A::fma_rn(a0[r], x[c], acc[r][c]);
-                            acc[r + 4][c] = A::fma_rn(a1[r], x[c], acc[r + 4][c]);
-                        }
+                    for (int r = 0; r < 4; ++r) {
+                        acc[r][c] = A::fma_rn(A::abs(a0[r]), x[c], acc[r][c]);
+                        acc[r + 4][c] = A::fma_rn(A::abs(a1[r]), x[c], acc[r + 4][c]);
                     }
                 }
             }
+        } else {
+#pragma unroll 2
+            for (int i = 0; i < n_in; ++i) {
+                Real a0[4], a1[4], x[4];
+                V4<Real>::ld(wp + i * Mpad, a0);
+                V4<Real>::ld(wp + i * Mpad + 4, a1);
+                V4<Real>::ld(xp + i * NS, x);
 #pragma unroll
-            for (int r = 0; r < 8; ++r) V4<Real>::st(sOut + (p0 + r) * NS + j0, acc[r]);
+                for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        acc[r][c] = A::fma_rn(a0[r], x[c], acc[r][c]);
+                        acc[r + 4][c] = A::fma_rn(a1[r], x[c], acc[r + 4][c]);
+                    }
+                }
+            }
+        }
+    }
+
+    static __device__ void contract(Real *S, const Real *sW, int n_in, int Mpad, int d, int NS) {
+        const int QW = d * T / 4;             // quads of C coefficient columns
+        const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
+        const int Q = QW + QA;
+        const int total = (Mpad / 8) * Q;
+        Real acc[kItems][8][4];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const int item = threadIdx.x + it * NT;
+            if (item < total) {
+                const int g = item / Q;
+                const int q = item - g * Q;
+                const bool is_abs = q >= QW;
+                const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
+                tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const int item = threadIdx.x + it * NT;
+            if (item < total) {
+                const int g = item / Q;
+                const int q = item - g * Q;
+                const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) V4<Real>::st(S + (g * 8 + r) * NS + j0, acc[it][r]);
+            }
         }
     }
 
@@ -415,37 +536,27 @@ struct EvalTile {
     }
 
     // ---- property rows: constant, error (incl. the fold), sound bounds ----------
-    static __device__ void final_rows(Real *S, const Real *Sprev, const Real *sW, int Mpad,
-                                      const NetParams<Real> &net, int NS, Real *sLo, Real *sHi, Real *sErr) {
+    template <class L>
+    static __device__ void final_rows(const L &lay, const Real *sConst, const NetParams<Real> &net, Real gcoef,
+                                      Real *sLo, Real *sHi, Real *sErr) {
         const int d = net.d;
         const int R = net.R;
         const int K = net.K;
         const int n_in = net.n[K - 1];
-        const Real *bias = net.b[K - 1];
         for (int item = threadIdx.x; item < R * T; item += NT) {
             const int r = item / T;
             const int b = item - r * T;
-            Real *row = S + r * NS + b;
+            const auto Rw = lay.row(r, b);
             Real chi, clo, E;
             if (K > 1) {
-                finish_contraction(row, Sprev, sW, Mpad, r, b, d, n_in, NS, bias[r], chi, clo, E);
-                // rounding of the folded property layer: |z_i| <= N_i + |C_i const| + E_i
-                Real fe = net.fold_berr[r];
-                const Real *pv = Sprev + b;
-                for (int i = 0; i < n_in; ++i) {
-                    const Real *q = pv + i * NS;
-                    Real z = A::add_up(A::add_up(q[cN(d) * T], A::abs(q[cCh(d) * T])),
-                                       A::add_up(A::abs(q[cCl(d) * T]), q[cE(d) * T]));
-                    fe = A::add_up(fe, A::mul_up(net.fold_err[r * n_in + i], z));
-                }
-                E = A::add_up(E, fe);
+                finish_contraction(Rw, sConst, net.n_max_pad, r, b, d, n_in, gcoef, chi, clo, E);
             } else {
-                chi = row[cCh(d) * T];
-                clo = row[cCl(d) * T];
-                E = row[cE(d) * T];
+                chi = Rw(cCh(d));
+                clo = Rw(cCl(d));
+                E = Rw(cE(d));
             }
-            RowBounds<Real, T> bd;
-            bd.compute(row, d, chi, clo);
+            RowBounds<Real> bd;
+            bd.compute(Rw, d, chi, clo);
             sLo[r * T + b] = A::add_dn(bd.ll, -E);
             sHi[r * T + b] = A::add_up(bd.uu, E);
             sErr[r * T + b] = E;
@@ -487,7 +598,7 @@ __device__ __forceinline__ uint8_t classify_rows(const NetParams<Real> &net, con
 //         counts the boxes still depending on E as ties).
 // ---------------------------------------------------------------------------
 template <typename Real, int T, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? 2 : 1)
 slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutputs out, const int pass) {
     using A = Arith<Real>;
     using Tile = EvalTile<Real, T, NT>;
@@ -498,13 +609,12 @@ slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutput
     const int nmp = net.n_max_pad;
 
     unsigned char *sp = smem_raw;
-    Real *sA = reinterpret_cast<Real *>(sp);
+    Real *sS = reinterpret_cast<Real *>(sp);
     sp += (size_t)nmp * NS * sizeof(Real);
-    Real *sB = reinterpret_cast<Real *>(sp);
-    sp += (size_t)nmp * NS * sizeof(Real);
+    Real *sConst = reinterpret_cast<Real *>(sp);
+    sp += 3 * (size_t)nmp * T * sizeof(Real);
     Real *sW = reinterpret_cast<Real *>(sp);
     sp += (size_t)net.n_in_max * nmp * sizeof(Real);
-    sp += (size_t)nmp * sizeof(Real);   // (bias slot, unused: biases enter the constant)
     Real *sMh = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * d * sizeof(Real);
     Real *sMl = reinterpret_cast<Real *>(sp);
@@ -569,27 +679,21 @@ slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutput
         }
         __syncthreads();
 
-        Tile::init_layer(sA, net, sMh, sMl, sR, NS);
+        const SimtLayout<Real, T> lay{sS, NS};
+        Tile::init_layer(lay, net, sMh, sMl, sR);
         __syncthreads();
 
-        Real *cur = sA;
-        Real *nxt = sB;
-        int Mpad_prev = 0;
         for (int k = 1; k < net.K; ++k) {
-            Tile::hidden_epilogue(cur, nxt, sW, Mpad_prev, net, k, NS);
-            __syncthreads();
+            Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]));
             const int n_out = net.n[k + 1];
             const int Mpad = (n_out + 7) & ~7;
             Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
             __syncthreads();
-            Tile::contract(cur, nxt, sW, net.n[k], Mpad, d, NS);
+            Tile::const_phase(lay, sConst, sW, Mpad, net, k);
+            Tile::contract(sS, sW, net.n[k], Mpad, d, NS);   // barrier inside, then in-place store
             __syncthreads();
-            Real *t = cur;
-            cur = nxt;
-            nxt = t;
-            Mpad_prev = Mpad;
         }
-        Tile::final_rows(cur, nxt, sW, Mpad_prev, net, NS, sLo, sHi, sErr);
+        Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
         __syncthreads();
 
         // ---- classify (Sec. 3) and write ------------------------------------

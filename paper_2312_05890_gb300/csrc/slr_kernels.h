@@ -10,17 +10,22 @@ namespace slr {
 
 // Tile sizes (boxes per CTA) the evaluation kernel is built for.
 constexpr int kTileSizes[] = {64, 32, 16, 8, 4};
-constexpr int kEvalThreads = 256;
+constexpr int kThreadCounts[] = {256, 128};
 
 // Fused evaluation (kernel (b) plus its contraction); one instantiation per
-// working precision.  `T` must be one of kTileSizes.
-cudaError_t launch_eval_f32(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
+// working precision.  `T` must be one of kTileSizes and `NT` of kThreadCounts.
+cudaError_t launch_eval_f32(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass);
-cudaError_t launch_eval_f64(int T, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
+cudaError_t launch_eval_f64(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass);
-// Resident CTAs per SM of the evaluation kernel at tile size T and this smem.
-int eval_blocks_per_sm_f32(int T, size_t smem);
-int eval_blocks_per_sm_f64(int T, size_t smem);
+// Resident CTAs per SM of the evaluation kernel at tile size T, NT threads and this smem.
+int eval_blocks_per_sm_f32(int T, int NT, size_t smem);
+int eval_blocks_per_sm_f64(int T, int NT, size_t smem);
+
+// Tensor-core evaluation (FP32 state, split-TF32 contraction on tcgen05).
+size_t eval_tc_smem_bytes(int T, const NetParams<float> &net, const TcParams &tc);
+cudaError_t launch_eval_tc(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
+                           const TcParams &tc, const BoxSource &src, const EvalOutputs &out, int pass);
 
 cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s);
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,

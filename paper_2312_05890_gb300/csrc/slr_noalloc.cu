@@ -140,7 +140,7 @@ extern "C" int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out) {
         o.near_cap = kNearCap;
         o.tie_count = &ctr->ties;
         o.status = status;
-        NA_CK(slr::launch_eval_f32(v.T32, v.grid32, v.smem32, s, *v.nf, src, o, 0));
+        NA_CK(slr::launch_eval_f32(v.T32, v.NT32, v.grid32, v.smem32, s, *v.nf, src, o, 0));
         ++launches;
         if (recheck) {
             slr::BoxSource s2 = src;
@@ -151,7 +151,7 @@ extern "C" int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out) {
             o2.cls = cls;
             o2.tie_count = &ctr->ties;
             o2.status = status;
-            NA_CK(slr::launch_eval_f64(v.T64, v.sm_count, v.smem64, s, *v.nd, s2, o2, 1));
+            NA_CK(slr::launch_eval_f64(v.T64, v.NT64, v.grid64, v.smem64, s, *v.nd, s2, o2, 1));
             ++launches;
         }
         NA_CK(slr::launch_compact(codes[t & 1], cls, codes[(t + 1) & 1], ctr, status, kFrontierCap, t, D, nullptr,
@@ -187,6 +187,8 @@ extern "C" int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out) {
     out->launches = launches;
     out->h2d_bytes = (int64_t)(2 * d * sizeof(double) + d * sizeof(unsigned long long));
     out->d2h_bytes = (int64_t)(sizeof c + sizeof st);
+    out->tile_boxes = v.T32;
+    out->tile_threads = v.NT32;
     if (st & slr::kStatusOverflow)
         return slr_internal_fail(ctx, SLR_EOVERFLOW,
                                  "slr_count_noalloc: a level exceeded the 262144-box frontier of its fixed scratch");

@@ -10,7 +10,7 @@ struct slr_noalloc_view {
     int device;
     cudaStream_t stream;
     int d;
-    int T32, grid32, T64, sm_count;
+    int T32, NT32, grid32, T64, NT64, grid64, sm_count;
     size_t smem32, smem64;
     const slr::NetParams<float> *nf;
     const slr::NetParams<double> *nd;
