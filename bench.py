@@ -191,6 +191,8 @@ def main():
     procs = os.cpu_count() or 1
 
     from workloads import generators as gen
+    if args.workload == "batch":
+        return bench_batch(args, world, rank, local_rank)
     # weak scaling: rank r counts its own problem of the same shape (seed + r)
     p = gen.make(args.workload, args.seed + rank)
     D = p.depth
@@ -327,6 +329,53 @@ def main():
     c.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_batch(args, world, rank, local_rank):
+    """The batched workload: 256 (network, property) problems counted together per step."""
+    import torch
+
+    import paper_2312_05890_gb300 as pkg
+    from workloads import generators as gen
+    torch.cuda.set_device(local_rank)
+    probs = gen.batched_uneven(args.seed + rank)
+    flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device="cuda")
+    c = pkg.Counter(local_rank)
+    for _ in range(args.warmup):
+        c.count_batch(probs)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, boxes, e2e = [], 0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = c.count_batch(probs)          # uploads every problem from host memory, reads back all counts
+        e2e.append(time.perf_counter() - t0)
+        ms.append(res[0]["device_ms"])
+        boxes += sum(r["boxes"] for r in res)
+    clocks = sampler.stop()
+    per_boxes = sorted(r["boxes"] for r in res)
+    levels = sorted(r["levels"] for r in res)
+    tot_s = sum(ms) / 1e3
+    value = boxes / tot_s
+    if rank == 0:
+        print(json.dumps({
+            "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched: {len(probs)} problems over 16 networks (d 5-32, widths 32-128, "
+                                   f"2-8 hidden layers), depth caps 12-22, seed {args.seed}",
+                       "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}",
+                       "tile_boxes": res[0]["tile"][0], "launches_per_step": res[0]["launches"]},
+            "per_problem": {"boxes_min_median_max": [per_boxes[0], per_boxes[len(per_boxes) // 2], per_boxes[-1]],
+                            "levels_min_max": [levels[0], levels[-1]]},
+            "e2e": {"value": boxes / sum(e2e), "unit": "boxes/s", "h2d_bytes_per_step": res[0]["h2d_bytes"],
+                    "d2h_bytes_per_step": res[0]["d2h_bytes"]},
+            "gpu_launches": res[0]["launches"] * args.steps, "clocks": clocks,
+        }))
+    c.close()
 
 
 if __name__ == "__main__":

@@ -168,6 +168,36 @@ int slr_leaves(slr_ctx *ctx, int64_t cap, uint64_t *codes, uint8_t *depth,
  * widest-side schedule), D entries. */
 int slr_schedule(slr_ctx *ctx, int D, int32_t *dims);
 
+/* One problem of a batch: a network, an input box, a property (as in
+ * slr_load_network, slr_set_box and slr_set_property) and its depth cap. */
+typedef struct {
+    int32_t K;                        /* affine layers */
+    const int32_t *widths;            /* widths[0..K] */
+    const float *const *W;            /* W[k]: widths[k+1] x widths[k], row-major */
+    const float *const *b;            /* b[k]: widths[k+1] */
+    const float *lo;                  /* box: widths[0] endpoints, lo <= hi */
+    const float *hi;
+    int32_t n_clauses;                /* property: OR over clauses of AND over rows */
+    const int32_t *rows_per_clause;
+    const float *C;                   /* R x widths[K], row-major */
+    const float *e;                   /* R */
+    const uint8_t *strict;            /* R */
+    int32_t depth;                    /* D of this problem, 0..62 */
+} slr_problem;
+
+/* Count n problems of uneven size together (Alg. 1 for each, Sec. 3 level
+ * evaluation across all of them): every level step bounds the current level
+ * of every unfinished problem in one persistent launch, tiles never mixing
+ * problems; problems with smaller depth caps simply finish earlier.  The step
+ * loop is captured once as a CUDA graph and replayed while later calls keep
+ * the batch's shape (same widths, rows, clauses and depths; weights, boxes
+ * and properties may change).  results[i] receives problem i's count as
+ * slr_count would return it (device_ms is the time of the whole batch).
+ * Inputs are copied.  Each problem's frontier holds up to min(2^depth,
+ * frontier_cap) boxes (SLR_EOVERFLOW beyond).  Uses the context's options
+ * (relax_mode, fp64_recheck, frontier_cap) and stream; FP32 arithmetic. */
+int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results);
+
 /* slr_count for callers that cannot allocate GPU memory.  The paper has no
  * counterpart: this entry exists for programs that set the library up once
  * and then count from code where cudaMalloc/cudaFree are not allowed (while a

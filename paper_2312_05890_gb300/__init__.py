@@ -28,7 +28,7 @@ MAX_LEVELS = 63
 # Names the header declares (checked by the CPU test that loads the library).
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
-           "slr_count_noalloc", "slr_last_error")
+           "slr_count_noalloc", "slr_count_batch", "slr_last_error")
 
 
 class SlrError(RuntimeError):
@@ -70,6 +70,13 @@ class slr_result(ctypes.Structure):
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 
 
+class slr_problem(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("widths", ctypes.c_void_p), ("W", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("n_clauses", ctypes.c_int32),
+                ("rows_per_clause", ctypes.c_void_p), ("C", ctypes.c_void_p), ("e", ctypes.c_void_p),
+                ("strict", ctypes.c_void_p), ("depth", ctypes.c_int32)]
+
+
 _lib_handle = None
 
 
@@ -96,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "slr_leaves": (ctypes.c_int, [P, i64, P, P, P, ctypes.POINTER(i64)]),
         "slr_schedule": (ctypes.c_int, [P, ctypes.c_int, P]),
         "slr_count_noalloc": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
+        "slr_count_batch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_problem), ctypes.POINTER(slr_result)]),
         "slr_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -234,6 +242,33 @@ def slr_count_noalloc(ctx, D: int) -> dict:
     return res.to_dict()
 
 
+def slr_count_batch(ctx, problems, depths=None):
+    """Count many workloads.Problem-like objects together; returns one result dict per problem."""
+    lib = load_library()
+    keep = []
+    arr = (slr_problem * len(problems))()
+    for i, p in enumerate(problems):
+        Ws = [np.ascontiguousarray(w, dtype=np.float32) for w in p.net.W]
+        bs = [np.ascontiguousarray(x, dtype=np.float32).reshape(-1) for x in p.net.b]
+        widths = np.array([Ws[0].shape[1]] + [w.shape[0] for w in Ws], dtype=np.int32)
+        wp = (ctypes.c_void_p * len(Ws))(*[w.ctypes.data for w in Ws])
+        bp = (ctypes.c_void_p * len(bs))(*[x.ctypes.data for x in bs])
+        lo = np.ascontiguousarray(p.lo, dtype=np.float32)
+        hi = np.ascontiguousarray(p.hi, dtype=np.float32)
+        rpc = np.ascontiguousarray(p.prop.rows_per_clause, dtype=np.int32)
+        C = np.ascontiguousarray(p.prop.C, dtype=np.float32)
+        e = np.ascontiguousarray(p.prop.e, dtype=np.float32)
+        st = np.ascontiguousarray(p.prop.strict, dtype=np.uint8)
+        keep += [Ws, bs, widths, wp, bp, lo, hi, rpc, C, e, st]
+        D = p.depth if depths is None else depths[i]
+        arr[i] = slr_problem(len(Ws), widths.ctypes.data, ctypes.cast(wp, ctypes.c_void_p),
+                             ctypes.cast(bp, ctypes.c_void_p), lo.ctypes.data, hi.ctypes.data, int(rpc.shape[0]),
+                             rpc.ctypes.data, C.ctypes.data, e.ctypes.data, st.ctypes.data, int(D))
+    res = (slr_result * len(problems))()
+    _check(lib, ctx, lib.slr_count_batch(ctx, len(problems), arr, res))
+    return [r.to_dict() for r in res]
+
+
 def slr_last_error(ctx) -> str:
     return load_library().slr_last_error(ctx).decode()
 
@@ -291,6 +326,9 @@ class Counter:
 
     def count(self, D: int) -> dict:
         return slr_count(self.ctx, D)
+
+    def count_batch(self, problems, depths=None):
+        return slr_count_batch(self.ctx, problems, depths)
 
     def count_noalloc(self, D: int) -> dict:
         return slr_count_noalloc(self.ctx, D)

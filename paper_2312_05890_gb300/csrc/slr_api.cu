@@ -36,6 +36,22 @@ struct HostLayers {
 
 }  // namespace
 
+// Device state of the last batched count, reused while the batch keeps its shape.
+struct BatchState {
+    std::string key;
+    void *arena = nullptr;
+    size_t upload_bytes = 0;             // weights, network params, roots and masks (re-uploaded per call)
+    unsigned char *h_upload = nullptr;   // pinned staging of the upload region
+    cudaGraphExec_t graph = nullptr;
+    int P = 0, Dmax = 0;
+    slr::LevelCounters *ctrs = nullptr;  // P counters
+    unsigned int *status = nullptr;
+    slr::LevelCounters *h_ctrs = nullptr;
+    std::vector<int64_t> near_cap;
+    int64_t launches = 0;
+    int T32 = 0, T64 = 0;
+};
+
 struct slr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -66,6 +82,7 @@ struct slr_ctx {
     size_t smem_tc = 0;
     bool tc_ok = false;
     int64_t *near_list2 = nullptr;
+    BatchState *batch = nullptr;
     std::string tuned_key;                // network shape the FP32 tile choice was timed for
     int tuned_T = 0, tuned_NT = 0;
 
@@ -131,8 +148,8 @@ bool finite_all(const float *p, size_t n) {
 // Fold the property rows into the last layer in float64 (Sec. 3 check on the
 // rows C y + e): W' = C W_K, b' = C b_K + e, with a bound on the float64
 // rounding error, then round to the working precision and add that rounding.
-template <typename Real>
-void build_layers(const slr_ctx *ctx, HostLayers<Real> &L) {
+template <typename Real, typename Src>
+void build_layers(const Src *ctx, HostLayers<Real> &L) {
     const int K = ctx->K;
     const int R = (int)ctx->e.size();
     const int n_out = ctx->widths[K];
@@ -203,8 +220,8 @@ size_t layers_bytes(const HostLayers<Real> &L) {
     return s;
 }
 
-template <typename Real>
-void layout_params(slr_ctx *ctx, const HostLayers<Real> &L, unsigned char *dev, unsigned char *host,
+template <typename Real, typename Src>
+void layout_params(const Src *ctx, const HostLayers<Real> &L, unsigned char *dev, unsigned char *host,
                    size_t &off, slr::NetParams<Real> &p) {
     auto put = [&](const std::vector<Real> &v) -> const Real * {
         const Real *dp = reinterpret_cast<const Real *>(dev + off);
@@ -689,6 +706,13 @@ int slr_destroy(slr_ctx *ctx) {
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    if (ctx->batch) {
+        if (ctx->batch->graph) cudaGraphExecDestroy(ctx->batch->graph);
+        cudaFree(ctx->batch->arena);
+        if (ctx->batch->h_upload) cudaFreeHost(ctx->batch->h_upload);
+        if (ctx->batch->h_ctrs) cudaFreeHost(ctx->batch->h_ctrs);
+        delete ctx->batch;
+    }
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return SLR_OK;
@@ -1079,3 +1103,410 @@ const char *slr_last_error(const slr_ctx *ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched count: many (network, box, property, depth) problems, one persistent
+// kernel launch per level step for all of them, the whole step loop captured
+// in one CUDA graph and replayed while the batch keeps its shape.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ProblemHost {
+    struct {
+        int relax_mode;
+    } opt;
+    int K = 0;
+    std::vector<int> widths;
+    std::vector<std::vector<float>> W, b;
+    std::vector<float> lo, hi;
+    int n_clauses = 0;
+    std::vector<int> rpc;
+    std::vector<float> C, e;
+    std::vector<uint8_t> strict;
+    int depth = 0;
+};
+
+int read_problem(slr_ctx *ctx, int idx, const slr_problem &q, int relax_mode, ProblemHost &h) {
+    if (q.K < 1 || q.K > slr::kMaxLayers || !q.widths || !q.W || !q.b)
+        return fail(ctx, SLR_EINVAL, "problem %d: bad network", idx);
+    for (int k = 0; k <= q.K; ++k)
+        if (q.widths[k] < 1 || q.widths[k] > slr::kMaxWidth)
+            return fail(ctx, SLR_EINVAL, "problem %d: widths[%d]=%d out of range", idx, k, q.widths[k]);
+    h.opt.relax_mode = relax_mode;
+    h.K = q.K;
+    h.widths.assign(q.widths, q.widths + q.K + 1);
+    h.W.resize(q.K);
+    h.b.resize(q.K);
+    for (int k = 0; k < q.K; ++k) {
+        const size_t nw = (size_t)q.widths[k + 1] * q.widths[k];
+        if (!q.W[k] || !q.b[k] || !finite_all(q.W[k], nw) || !finite_all(q.b[k], q.widths[k + 1]))
+            return fail(ctx, SLR_EINVAL, "problem %d: bad or non-finite layer %d", idx, k);
+        h.W[k].assign(q.W[k], q.W[k] + nw);
+        h.b[k].assign(q.b[k], q.b[k] + q.widths[k + 1]);
+    }
+    const int d = q.widths[0];
+    if (!q.lo || !q.hi) return fail(ctx, SLR_EINVAL, "problem %d: no box", idx);
+    for (int i = 0; i < d; ++i)
+        if (!std::isfinite(q.lo[i]) || !std::isfinite(q.hi[i]) || q.lo[i] > q.hi[i])
+            return fail(ctx, SLR_EINVAL, "problem %d: bad box in dimension %d", idx, i);
+    h.lo.assign(q.lo, q.lo + d);
+    h.hi.assign(q.hi, q.hi + d);
+    if (q.n_clauses < 1 || !q.rows_per_clause || !q.C || !q.e || !q.strict)
+        return fail(ctx, SLR_EINVAL, "problem %d: bad property", idx);
+    int R = 0;
+    for (int c = 0; c < q.n_clauses; ++c) {
+        if (q.rows_per_clause[c] < 1) return fail(ctx, SLR_EINVAL, "problem %d: empty clause", idx);
+        R += q.rows_per_clause[c];
+    }
+    if (R > slr::kMaxRows) return fail(ctx, SLR_EINVAL, "problem %d: more than %d rows", idx, slr::kMaxRows);
+    const int n_out = q.widths[q.K];
+    if (!finite_all(q.C, (size_t)R * n_out) || !finite_all(q.e, R))
+        return fail(ctx, SLR_EINVAL, "problem %d: non-finite property", idx);
+    h.n_clauses = q.n_clauses;
+    h.rpc.assign(q.rows_per_clause, q.rows_per_clause + q.n_clauses);
+    h.C.assign(q.C, q.C + (size_t)R * n_out);
+    h.e.assign(q.e, q.e + R);
+    h.strict.assign(q.strict, q.strict + R);
+    if (q.depth < 0 || q.depth > slr::kMaxDepth) return fail(ctx, SLR_EINVAL, "problem %d: depth out of range", idx);
+    h.depth = q.depth;
+    return SLR_OK;
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (n < 1 || n > 65535 || !problems || !results) return fail(ctx, SLR_EINVAL, "bad batch arguments");
+    CK(ctx, cudaSetDevice(ctx->device));
+    const int P = n;
+    std::vector<ProblemHost> ph(P);
+    int rc;
+    for (int i = 0; i < P; ++i)
+        if ((rc = read_problem(ctx, i, problems[i], ctx->opt.relax_mode, ph[i]))) return rc;
+
+    // host images of every problem's layers (property folded into the last)
+    std::vector<HostLayers<float>> Lf(P);
+    std::vector<HostLayers<double>> Ld(P);
+    size_t wbytes = 0;
+    for (int i = 0; i < P; ++i) {
+        build_layers(&ph[i], Lf[i]);
+        build_layers(&ph[i], Ld[i]);
+        wbytes += layers_bytes(Lf[i]) + layers_bytes(Ld[i]);
+    }
+    int Dmax = 0;
+    std::string key = "B" + std::to_string(ctx->opt.relax_mode) + ":" + std::to_string(ctx->opt.fp64_recheck);
+    for (const ProblemHost &h : ph) {
+        Dmax = std::max(Dmax, h.depth);
+        key += "|" + std::to_string(h.depth) + "," + std::to_string(h.e.size()) + "," + std::to_string(h.n_clauses);
+        for (int w : h.widths) key += "," + std::to_string(w);
+        for (int r : h.rpc) key += "c" + std::to_string(r);
+    }
+    const bool recheck = ctx->opt.fp64_recheck != 0;
+    BatchState *bs = ctx->batch;
+    if (!bs || bs->key != key) {
+        if (bs) {
+            if (bs->graph) cudaGraphExecDestroy(bs->graph);
+            cudaFree(bs->arena);
+            if (bs->h_upload) cudaFreeHost(bs->h_upload);
+            if (bs->h_ctrs) cudaFreeHost(bs->h_ctrs);
+            delete bs;
+            ctx->batch = nullptr;
+        }
+        bs = new BatchState();
+        ctx->batch = bs;
+        bs->key = key;
+        bs->P = P;
+        bs->Dmax = Dmax;
+        // ---- arena layout: [upload: weights | nets32 | nets64 | roots+masks] [per problem] [step tables]
+        size_t off = 0;
+        const size_t o_w = off;
+        off += al(wbytes);
+        const size_t o_n32 = off;
+        off += al((size_t)P * sizeof(slr::NetParams<float>));
+        const size_t o_n64 = off;
+        off += al((size_t)P * sizeof(slr::NetParams<double>));
+        std::vector<size_t> o_root(P), o_masks(P), o_c0(P), o_c1(P), o_cls(P), o_near(P);
+        std::vector<int64_t> cap(P);
+        bs->near_cap.assign(P, 0);
+        for (int i = 0; i < P; ++i) {
+            const int d = ph[i].widths[0];
+            o_root[i] = off;
+            off += al(2 * (size_t)d * sizeof(double));
+            o_masks[i] = off;
+            off += al((size_t)d * sizeof(unsigned long long));
+        }
+        bs->upload_bytes = off;
+        const size_t o_ctr = off;
+        off += al((size_t)P * sizeof(slr::LevelCounters));
+        const size_t o_status = off;
+        off += al(sizeof(unsigned int) + sizeof(unsigned long long));
+        for (int i = 0; i < P; ++i) {
+            cap[i] = std::min<int64_t>((int64_t)1 << std::max(1, ph[i].depth), ctx->opt.frontier_cap);
+            bs->near_cap[i] = std::max<int64_t>(1024, cap[i] / 4);
+            o_c0[i] = off;
+            off += al((size_t)cap[i] * 8);
+            o_c1[i] = off;
+            off += al((size_t)cap[i] * 8);
+            o_cls[i] = off;
+            off += al((size_t)cap[i]);
+            o_near[i] = off;
+            off += al((size_t)bs->near_cap[i] * 8);
+        }
+        const size_t nsteps = (size_t)Dmax + 1;
+        const size_t o_sm = off;
+        off += al(nsteps * P * sizeof(slr::BoxSource));
+        const size_t o_sr = off;
+        off += al(nsteps * P * sizeof(slr::BoxSource));
+        const size_t o_om = off;
+        off += al(nsteps * P * sizeof(slr::EvalOutputs));
+        const size_t o_or = off;
+        off += al(nsteps * P * sizeof(slr::EvalOutputs));
+        const size_t o_ca = off;
+        off += al(2 * (size_t)P * sizeof(slr::CompactArgs));
+        const size_t o_pm = off;
+        off += al(((size_t)P + 1) * sizeof(long long));
+        const size_t o_pr = off;
+        off += al(((size_t)P + 1) * sizeof(long long));
+        CK(ctx, cudaMalloc(&bs->arena, off));
+        CK(ctx, cudaMallocHost(&bs->h_upload, bs->upload_bytes));
+        CK(ctx, cudaMallocHost(&bs->h_ctrs, (size_t)P * sizeof(slr::LevelCounters)));
+        unsigned char *A = (unsigned char *)bs->arena;
+        bs->ctrs = (slr::LevelCounters *)(A + o_ctr);
+        bs->status = (unsigned int *)(A + o_status);
+        const unsigned long long *zero = (const unsigned long long *)(A + o_status + 8);
+
+        // ---- network params (device pointers into the weights region) ------
+        std::memset(bs->h_upload, 0, bs->upload_bytes);
+        size_t woff = o_w;
+        std::vector<slr::NetParams<float>> n32(P);
+        std::vector<slr::NetParams<double>> n64(P);
+        slr::BatchShape sh32{0, 0, 0, 0}, sh64{0, 0, 0, 0};
+        for (int i = 0; i < P; ++i) {
+            layout_params(&ph[i], Lf[i], A, bs->h_upload, woff, n32[i]);
+            layout_params(&ph[i], Ld[i], A, bs->h_upload, woff, n64[i]);
+            for (slr::BatchShape *sh : {&sh32, &sh64}) {
+                sh->nmp = std::max(sh->nmp, n32[i].n_max_pad);
+                sh->d = std::max(sh->d, n32[i].d);
+                sh->n_in_max = std::max(sh->n_in_max, n32[i].n_in_max);
+                sh->R = std::max(sh->R, n32[i].R);
+            }
+        }
+        std::memcpy(bs->h_upload + o_n32, n32.data(), (size_t)P * sizeof(slr::NetParams<float>));
+        std::memcpy(bs->h_upload + o_n64, n64.data(), (size_t)P * sizeof(slr::NetParams<double>));
+
+        // ---- tiles: the most boxes in flight that the largest problem allows ----
+        const size_t kStatic = 4096;   // shared copies of one problem's params, source and outputs
+        auto pick = [&](bool f64, int &T, size_t &smem, int &grid) {
+            T = 0;
+            long best = 0;
+            for (int t : slr::kTileSizes) {
+                const size_t sm = f64 ? slr::eval_smem_bytes<double>(t, sh64.d, sh64.R, sh64.nmp, sh64.n_in_max)
+                                      : slr::eval_smem_bytes<float>(t, sh32.d, sh32.R, sh32.nmp, sh32.n_in_max);
+                if (sm + kStatic > (size_t)kMaxSmem) continue;
+                bool fits = true;   // each problem's contraction tiles must fit two per thread
+                for (int i = 0; i < P && fits; ++i)
+                    fits = slr::eval_gemm_items(t, n32[i].d, n32[i].n_max_pad) <= 2 * 256;
+                if (!fits) continue;
+                const int nb = f64 ? slr::eval_batch_blocks_per_sm_f64(t, sm) : slr::eval_batch_blocks_per_sm_f32(t, sm);
+                if (nb <= 0) continue;
+                const long score = f64 ? (long)(1000 - t) : (long)nb * t;   // FP64: short lists, small tiles
+                if (score > best) {
+                    best = score;
+                    T = t;
+                    smem = sm;
+                    grid = nb * ctx->sm_count;
+                }
+            }
+        };
+        int T32 = 0, T64 = 0, g32 = 0, g64 = 0;
+        size_t sm32 = 0, sm64 = 0;
+        pick(false, T32, sm32, g32);
+        pick(true, T64, sm64, g64);
+        if (!T32) return fail(ctx, SLR_EUNSUPPORTED, "a problem of the batch is too large for the fused kernel");
+        bs->T32 = T32;
+        bs->T64 = T64;
+        const bool rch = recheck && T64 > 0;
+
+        // ---- per-step sources, outputs and compaction arguments ------------
+        std::vector<slr::BoxSource> sm(nsteps * P), sr(nsteps * P);
+        std::vector<slr::EvalOutputs> om(nsteps * P), orr(nsteps * P);
+        std::vector<slr::CompactArgs> ca(2 * (size_t)P);
+        for (int i = 0; i < P; ++i) {
+            slr::LevelCounters *ctr = bs->ctrs + i;
+            const int d = ph[i].widths[0];
+            for (int par = 0; par < 2; ++par) {
+                slr::CompactArgs &c = ca[(size_t)par * P + i];
+                c.codes_in = (uint64_t *)(A + (par ? o_c1[i] : o_c0[i]));
+                c.codes_out = (uint64_t *)(A + (par ? o_c0[i] : o_c1[i]));
+                c.cls = A + o_cls[i];
+                c.ctr = ctr;
+                c.cap = cap[i];
+                c.D = ph[i].depth;
+            }
+            for (size_t t = 0; t < nsteps; ++t) {
+                slr::BoxSource &b = sm[t * P + i];
+                b = slr::BoxSource{};
+                b.mode = 0;
+                b.codes = (uint64_t *)(A + ((t & 1) ? o_c1[i] : o_c0[i]));
+                b.count = (int)t <= ph[i].depth ? &ctr->frontier_n[t] : zero;
+                b.t = (int)t;
+                b.D = std::max(ph[i].depth, (int)t);
+                b.dim_mask = (unsigned long long *)(A + o_masks[i]);
+                b.root_lo = (double *)(A + o_root[i]);
+                b.root_w = (double *)(A + o_root[i]) + d;
+                b.cap = cap[i];
+                slr::BoxSource &b2 = sr[t * P + i];
+                b2 = b;
+                b2.index = (int64_t *)(A + o_near[i]);
+                b2.index_count = (int)t <= ph[i].depth ? &ctr->near_n[t] : zero;
+                b2.cap = bs->near_cap[i];
+                slr::EvalOutputs &o = om[t * P + i];
+                o = slr::EvalOutputs{};
+                o.cls = A + o_cls[i];
+                o.near_list = rch ? (int64_t *)(A + o_near[i]) : nullptr;
+                o.near_count = &ctr->near_n[t];
+                o.near_cap = bs->near_cap[i];
+                o.tie_count = &ctr->ties;
+                o.status = bs->status;
+                slr::EvalOutputs &o2 = orr[t * P + i];
+                o2 = slr::EvalOutputs{};
+                o2.cls = A + o_cls[i];
+                o2.tie_count = &ctr->ties;
+                o2.status = bs->status;
+            }
+        }
+        CK(ctx, cudaMemcpy(A + o_sm, sm.data(), sm.size() * sizeof(slr::BoxSource), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(A + o_sr, sr.data(), sr.size() * sizeof(slr::BoxSource), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(A + o_om, om.data(), om.size() * sizeof(slr::EvalOutputs), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(A + o_or, orr.data(), orr.size() * sizeof(slr::EvalOutputs), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(A + o_ca, ca.data(), ca.size() * sizeof(slr::CompactArgs), cudaMemcpyHostToDevice));
+
+        // ---- capture the step loop ----------------------------------------
+        int64_t maxcap = 1;
+        for (int i = 0; i < P; ++i) maxcap = std::max(maxcap, cap[i]);
+        const int bpp = (int)std::max<int64_t>(1, std::min<int64_t>(128, maxcap / 32768));
+        const slr::NetParams<float> *dn32 = (const slr::NetParams<float> *)(A + o_n32);
+        const slr::NetParams<double> *dn64 = (const slr::NetParams<double> *)(A + o_n64);
+        long long *pm = (long long *)(A + o_pm);
+        long long *pr = (long long *)(A + o_pr);
+        cudaGraph_t g;
+        CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        int64_t L = 0;
+        cudaError_t ce = cudaMemsetAsync(bs->ctrs, 0, (size_t)P * sizeof(slr::LevelCounters), ctx->stream);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(bs->status, 0, 16, ctx->stream);
+        if (ce == cudaSuccess) ce = slr::launch_init_batch((const slr::CompactArgs *)(A + o_ca), P, ctx->stream), ++L;
+        for (size_t t = 0; t < nsteps && ce == cudaSuccess; ++t) {
+            const slr::BoxSource *s_m = (const slr::BoxSource *)(A + o_sm) + t * P;
+            const slr::BoxSource *s_r = (const slr::BoxSource *)(A + o_sr) + t * P;
+            const slr::EvalOutputs *o_m = (const slr::EvalOutputs *)(A + o_om) + t * P;
+            const slr::EvalOutputs *o_r = (const slr::EvalOutputs *)(A + o_or) + t * P;
+            ce = slr::launch_tile_prefix(s_m, P, T32, pm, ctx->stream);
+            if (ce == cudaSuccess)
+                ce = slr::launch_eval_batch_f32(T32, g32, sm32, ctx->stream, dn32, s_m, o_m, P, pm, sh32, 0);
+            L += 2;
+            if (rch && ce == cudaSuccess) {
+                ce = slr::launch_tile_prefix(s_r, P, T64, pr, ctx->stream);
+                if (ce == cudaSuccess)
+                    ce = slr::launch_eval_batch_f64(T64, g64, sm64, ctx->stream, dn64, s_r, o_r, P, pr, sh64, 1);
+                L += 2;
+            }
+            if (ce == cudaSuccess)
+                ce = slr::launch_compact_batch((const slr::CompactArgs *)(A + o_ca) + (t & 1) * P, P, (int)t, bs->status,
+                                               bpp, ctx->stream);
+            ++L;
+        }
+        const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "capturing the batched count");
+        if (ee != cudaSuccess) return cuda_fail(ctx, ee, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&bs->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+        bs->launches = L;
+    }
+
+    // ---- data of this call: weights, params, roots and split masks ----------
+    unsigned char *A = (unsigned char *)bs->arena;
+    {
+        size_t woff = 0;
+        std::vector<slr::NetParams<float>> n32(P);
+        std::vector<slr::NetParams<double>> n64(P);
+        for (int i = 0; i < P; ++i) {
+            layout_params(&ph[i], Lf[i], A, bs->h_upload, woff, n32[i]);
+            layout_params(&ph[i], Ld[i], A, bs->h_upload, woff, n64[i]);
+        }
+        const size_t o_n32 = al(wbytes);
+        const size_t o_n64 = o_n32 + al((size_t)P * sizeof(slr::NetParams<float>));
+        std::memcpy(bs->h_upload + o_n32, n32.data(), (size_t)P * sizeof(slr::NetParams<float>));
+        std::memcpy(bs->h_upload + o_n64, n64.data(), (size_t)P * sizeof(slr::NetParams<double>));
+        size_t off = o_n64 + al((size_t)P * sizeof(slr::NetParams<double>));
+        for (int i = 0; i < P; ++i) {
+            const int d = ph[i].widths[0];
+            const int D = ph[i].depth;
+            double *root = (double *)(bs->h_upload + off);
+            unsigned long long *masks = (unsigned long long *)(bs->h_upload + off + al(2 * (size_t)d * sizeof(double)));
+            std::vector<int> cnt(d, 0);
+            for (int k = 0; k < d; ++k) {
+                root[k] = (double)ph[i].lo[k];
+                root[d + k] = (double)ph[i].hi[k] - (double)ph[i].lo[k];
+                masks[k] = 0ull;
+            }
+            for (int t = 0; t < D; ++t) {   // widest side first, ties to the lowest index
+                int best = 0;
+                double bw = -1.0;
+                for (int k = 0; k < d; ++k) {
+                    const double w = std::ldexp(root[d + k], -cnt[k]);
+                    if (w > bw) {
+                        bw = w;
+                        best = k;
+                    }
+                }
+                cnt[best] += 1;
+                masks[best] |= 1ull << (D - 1 - t);
+            }
+            off += al(2 * (size_t)d * sizeof(double)) + al((size_t)d * sizeof(unsigned long long));
+        }
+    }
+    CK(ctx, cudaMemcpyAsync(A, bs->h_upload, bs->upload_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+    CK(ctx, cudaGraphLaunch(bs->graph, ctx->stream));
+    CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+    unsigned int st = 0;
+    CK(ctx, cudaMemcpyAsync(bs->h_ctrs, bs->ctrs, (size_t)P * sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaMemcpyAsync(&st, bs->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    for (int i = 0; i < P; ++i) {
+        const slr::LevelCounters &c = bs->h_ctrs[i];
+        slr_result &out = results[i];
+        std::memset(&out, 0, sizeof out);
+        const int D = ph[i].depth;
+        out.unsafe_lo = c.unsafe_lo;
+        out.unsafe_hi = c.unsafe_lo + c.undecided_at_D;
+        out.boxes = c.boxes;
+        out.tie_leaves = c.ties;
+        out.depth = D;
+        unsigned long long rech = 0;
+        for (int t = 0; t <= D; ++t) {
+            out.level_boxes[t] = c.level_boxes[t];
+            out.level_safe[t] = c.level_safe[t];
+            out.level_unsafe[t] = c.level_unsafe[t];
+            out.level_undecided[t] = c.level_undecided[t];
+            rech += std::min<unsigned long long>(c.near_n[t], (unsigned long long)bs->near_cap[i]);
+            if (c.level_boxes[t]) out.levels = t + 1;
+        }
+        out.rechecked = recheck ? rech : 0;
+        out.device_ms = ms;              // the whole batch
+        out.launches = bs->launches;
+        out.h2d_bytes = (int64_t)bs->upload_bytes;
+        out.d2h_bytes = (int64_t)((size_t)P * sizeof(slr::LevelCounters) + sizeof st);
+        out.tile_boxes = bs->T32;
+        out.tile_threads = 256;
+    }
+    if (st & slr::kStatusOverflow) return fail(ctx, SLR_EOVERFLOW, "a problem's level exceeded its frontier capacity");
+    if (st & slr::kStatusNearOverflow) return fail(ctx, SLR_EOVERFLOW, "an FP64 re-check list overflowed");
+    return SLR_OK;
+}

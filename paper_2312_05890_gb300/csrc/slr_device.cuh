@@ -168,6 +168,11 @@ struct LevelCounters {
     unsigned long long near2_n[kMaxDepth + 2];      // second re-check list (tensor-core path)
 };
 
+// Largest shapes of the problems of one batched launch (shared-memory carve).
+struct BatchShape {
+    int nmp, d, n_in_max, R;
+};
+
 // Columns of one row of the state (see slr_eval.cuh): C coefficients, C
 // constant (hi), R coefficients, R constant, N, E, C constant (lo).
 __host__ __device__ inline int state_cols(int d) { return 2 * d + 5; }

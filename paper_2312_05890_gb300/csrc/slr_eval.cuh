@@ -591,44 +591,42 @@ __device__ __forceinline__ uint8_t classify_rows(const NetParams<Real> &net, con
 }
 
 // ---------------------------------------------------------------------------
-// The kernel: persistent over tiles of the level's boxes.
-// pass 0: working precision; writes the sound class and lists the undecided
-//         boxes whose class depends on E (their optimistic class differs);
-// pass 1: re-check of such a list in the higher precision (writes the class,
-//         counts the boxes still depending on E as ties).
+// Shared-memory views of one tile, carved from the dynamic allocation for the
+// largest shapes the launch serves.
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? 2 : 1)
-slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutputs out, const int pass) {
-    using A = Arith<Real>;
-    using Tile = EvalTile<Real, T, NT>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int d = net.d;
-    const int R = net.R;
+template <typename Real>
+struct TileSmem {
+    Real *sS, *sConst, *sW, *sMh, *sMl, *sR, *sLo, *sHi, *sErr;
+    int64_t *sIdx;
+};
+
+template <typename Real, int T>
+__device__ __forceinline__ TileSmem<Real> carve_smem(unsigned char *sp, int nmp, int d, int n_in_max, int R) {
+    TileSmem<Real> m;
     const int NS = T * state_cols(d);
-    const int nmp = net.n_max_pad;
-
-    unsigned char *sp = smem_raw;
-    Real *sS = reinterpret_cast<Real *>(sp);
+    m.sS = reinterpret_cast<Real *>(sp);
     sp += (size_t)nmp * NS * sizeof(Real);
-    Real *sConst = reinterpret_cast<Real *>(sp);
+    m.sConst = reinterpret_cast<Real *>(sp);
     sp += 3 * (size_t)nmp * T * sizeof(Real);
-    Real *sW = reinterpret_cast<Real *>(sp);
-    sp += (size_t)net.n_in_max * nmp * sizeof(Real);
-    Real *sMh = reinterpret_cast<Real *>(sp);
+    m.sW = reinterpret_cast<Real *>(sp);
+    sp += (size_t)n_in_max * nmp * sizeof(Real);
+    m.sMh = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * d * sizeof(Real);
-    Real *sMl = reinterpret_cast<Real *>(sp);
+    m.sMl = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * d * sizeof(Real);
-    Real *sR = reinterpret_cast<Real *>(sp);
+    m.sR = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * d * sizeof(Real);
-    Real *sLo = reinterpret_cast<Real *>(sp);
+    m.sLo = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * R * sizeof(Real);
-    Real *sHi = reinterpret_cast<Real *>(sp);
+    m.sHi = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * R * sizeof(Real);
-    Real *sErr = reinterpret_cast<Real *>(sp);
+    m.sErr = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * R * sizeof(Real);
-    int64_t *sIdx = reinterpret_cast<int64_t *>(sp);
+    m.sIdx = reinterpret_cast<int64_t *>(sp);
+    return m;
+}
 
+__device__ __forceinline__ int64_t source_count(const BoxSource &src) {
     int64_t n;
     if (src.index != nullptr) {
         n = (int64_t)*src.index_count;
@@ -637,97 +635,175 @@ slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutput
     } else {
         n = src.n_explicit;
     }
-    if (n > src.cap) n = src.cap;
+    return n > src.cap ? src.cap : n;
+}
 
-    for (int64_t base = (int64_t)blockIdx.x * T; base < n; base += (int64_t)gridDim.x * T) {
-        const int nb = (int)((n - base) < T ? (n - base) : T);
-        if (threadIdx.x < T) {
-            const int64_t k = base + (threadIdx.x < nb ? threadIdx.x : 0);
-            sIdx[threadIdx.x] = src.index != nullptr ? src.index[k] : k;
+// ---------------------------------------------------------------------------
+// One tile: boxes base .. base + T - 1 of the source (n boxes in all).
+// pass 0: working precision; writes the sound class and lists the undecided
+//         boxes whose class depends on E (their optimistic class differs);
+// pass 1: re-check of such a list in the higher precision (writes the class,
+//         counts the boxes still depending on E as ties).
+// ---------------------------------------------------------------------------
+template <typename Real, int T, int NT>
+__device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, const EvalOutputs &out, const int pass,
+                          const TileSmem<Real> &sm, const int64_t base, const int64_t n) {
+    using A = Arith<Real>;
+    using Tile = EvalTile<Real, T, NT>;
+    const int d = net.d;
+    const int R = net.R;
+    const int NS = T * state_cols(d);
+    Real *sS = sm.sS, *sConst = sm.sConst, *sW = sm.sW, *sMh = sm.sMh, *sMl = sm.sMl, *sR = sm.sR;
+    Real *sLo = sm.sLo, *sHi = sm.sHi, *sErr = sm.sErr;
+    int64_t *sIdx = sm.sIdx;
+    const int nb = (int)((n - base) < T ? (n - base) : T);
+    if (threadIdx.x < T) {
+        const int64_t k = base + (threadIdx.x < nb ? threadIdx.x : 0);
+        sIdx[threadIdx.x] = src.index != nullptr ? src.index[k] : k;
+    }
+    __syncthreads();
+
+    // ---- boxes: centre (hi + lo) and radius, outward ----------------------
+    for (int item = threadIdx.x; item < T * d; item += NT) {
+        const int b = item / d;
+        const int i = item - b * d;
+        const int64_t idx = sIdx[b];
+        double m64, r64, pad;
+        if (src.mode == 0) {
+            // Sec. 2.2 bisection: dimension i split c times, half index k
+            const unsigned long long code = src.codes[idx];
+            const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
+            const unsigned long long k = pext64(code, mask);
+            const int c = __popcll(mask);
+            const double w = src.root_w[i];
+            const double a = src.root_lo[i];
+            r64 = ldexp(w, -(c + 1));
+            m64 = a + w * ldexp((double)(2 * k + 1), -(c + 1));
+            pad = ldexp(fabs(m64) + fabs(a) + w, -50);
+        } else {
+            const double lo = (double)src.lo[idx * d + i];
+            const double hi = (double)src.hi[idx * d + i];
+            m64 = 0.5 * (lo + hi);
+            r64 = 0.5 * (hi - lo);
+            pad = ldexp(fabs(m64) + fabs(r64), -52);
         }
-        __syncthreads();
+        Real mh, ml, r;
+        split_centre<Real>(m64, r64, pad, mh, ml, r);
+        sMh[b * d + i] = mh;
+        sMl[b * d + i] = ml;
+        sR[b * d + i] = r;
+    }
+    __syncthreads();
 
-        // ---- boxes: centre (hi + lo) and radius, outward ----------------------
-        for (int item = threadIdx.x; item < T * d; item += NT) {
-            const int b = item / d;
-            const int i = item - b * d;
-            const int64_t idx = sIdx[b];
-            double m64, r64, pad;
-            if (src.mode == 0) {
-                // Sec. 2.2 bisection: dimension i split c times, half index k
-                const unsigned long long code = src.codes[idx];
-                const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
-                const unsigned long long k = pext64(code, mask);
-                const int c = __popcll(mask);
-                const double w = src.root_w[i];
-                const double a = src.root_lo[i];
-                r64 = ldexp(w, -(c + 1));
-                m64 = a + w * ldexp((double)(2 * k + 1), -(c + 1));
-                pad = ldexp(fabs(m64) + fabs(a) + w, -50);
-            } else {
-                const double lo = (double)src.lo[idx * d + i];
-                const double hi = (double)src.hi[idx * d + i];
-                m64 = 0.5 * (lo + hi);
-                r64 = 0.5 * (hi - lo);
-                pad = ldexp(fabs(m64) + fabs(r64), -52);
+    const SimtLayout<Real, T> lay{sS, NS};
+    Tile::init_layer(lay, net, sMh, sMl, sR);
+    __syncthreads();
+
+    for (int k = 1; k < net.K; ++k) {
+        Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]));
+        const int n_out = net.n[k + 1];
+        const int Mpad = (n_out + 7) & ~7;
+        Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
+        __syncthreads();
+        Tile::const_phase(lay, sConst, sW, Mpad, net, k);
+        Tile::contract(sS, sW, net.n[k], Mpad, d, NS);   // barrier inside, then in-place store
+        __syncthreads();
+    }
+    Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
+    __syncthreads();
+
+    // ---- classify (Sec. 3) and write ------------------------------------
+    if (threadIdx.x < nb) {
+        const int b = threadIdx.x;
+        const uint8_t cls = classify_rows<Real, T>(net, sLo, sHi, sErr, b, (Real)0);
+        // optimistic bounds (raw +- E inward): the class the exact SLR could have
+        const uint8_t opt = classify_rows<Real, T>(net, sLo, sHi, sErr, b, (Real)2);
+        const bool near = (cls == kUndecided) && (opt != kUndecided);
+        const int64_t idx = sIdx[b];
+        if (out.cls != nullptr) out.cls[idx] = cls;
+        if (out.row_lo != nullptr) {
+            for (int r = 0; r < R; ++r) {
+                out.row_lo[idx * R + r] = to_lo<Real>(sLo[r * T + b]);
+                out.row_hi[idx * R + r] = to_hi<Real>(sHi[r * T + b]);
             }
-            Real mh, ml, r;
-            split_centre<Real>(m64, r64, pad, mh, ml, r);
-            sMh[b * d + i] = mh;
-            sMl[b * d + i] = ml;
-            sR[b * d + i] = r;
         }
-        __syncthreads();
-
-        const SimtLayout<Real, T> lay{sS, NS};
-        Tile::init_layer(lay, net, sMh, sMl, sR);
-        __syncthreads();
-
-        for (int k = 1; k < net.K; ++k) {
-            Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]));
-            const int n_out = net.n[k + 1];
-            const int Mpad = (n_out + 7) & ~7;
-            Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
-            __syncthreads();
-            Tile::const_phase(lay, sConst, sW, Mpad, net, k);
-            Tile::contract(sS, sW, net.n[k], Mpad, d, NS);   // barrier inside, then in-place store
-            __syncthreads();
+        if (out.row_err != nullptr) {
+            for (int r = 0; r < R; ++r) out.row_err[idx * R + r] = to_hi<Real>(sErr[r * T + b]);
         }
-        Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
-        __syncthreads();
-
-        // ---- classify (Sec. 3) and write ------------------------------------
-        if (threadIdx.x < nb) {
-            const int b = threadIdx.x;
-            const uint8_t cls = classify_rows<Real, T>(net, sLo, sHi, sErr, b, (Real)0);
-            // optimistic bounds (raw +- E inward): the class the exact SLR could have
-            const uint8_t opt = classify_rows<Real, T>(net, sLo, sHi, sErr, b, (Real)2);
-            const bool near = (cls == kUndecided) && (opt != kUndecided);
-            const int64_t idx = sIdx[b];
-            if (out.cls != nullptr) out.cls[idx] = cls;
-            if (out.row_lo != nullptr) {
-                for (int r = 0; r < R; ++r) {
-                    out.row_lo[idx * R + r] = to_lo<Real>(sLo[r * T + b]);
-                    out.row_hi[idx * R + r] = to_hi<Real>(sHi[r * T + b]);
+        if (near) {
+            if (pass == 0 && out.near_list != nullptr) {
+                const unsigned long long pos = atomicAdd(out.near_count, 1ull);
+                if ((int64_t)pos < out.near_cap) {
+                    out.near_list[pos] = idx;
+                } else {
+                    atomicOr(out.status, kStatusNearOverflow);
                 }
-            }
-            if (out.row_err != nullptr) {
-                for (int r = 0; r < R; ++r) out.row_err[idx * R + r] = to_hi<Real>(sErr[r * T + b]);
-            }
-            if (near) {
-                if (pass == 0 && out.near_list != nullptr) {
-                    const unsigned long long pos = atomicAdd(out.near_count, 1ull);
-                    if ((int64_t)pos < out.near_cap) {
-                        out.near_list[pos] = idx;
-                    } else {
-                        atomicOr(out.status, kStatusNearOverflow);
-                    }
-                } else if (pass == 1 && out.tie_count != nullptr) {
-                    atomicAdd(out.tie_count, 1ull);
-                }
+            } else if (pass == 1 && out.tie_count != nullptr) {
+                atomicAdd(out.tie_count, 1ull);
             }
         }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// The kernel: persistent over tiles of one problem's boxes.
+// ---------------------------------------------------------------------------
+template <typename Real, int T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? 2 : 1)
+slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutputs out, const int pass) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileSmem<Real> sm = carve_smem<Real, T>(smem_raw, net.n_max_pad, net.d, net.n_in_max, net.R);
+    const int64_t n = source_count(src);
+    for (int64_t base = (int64_t)blockIdx.x * T; base < n; base += (int64_t)gridDim.x * T)
+        eval_tile<Real, T, NT>(net, src, out, pass, sm, base, n);
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernel: tiles of many problems in one persistent launch.  Tile g
+// belongs to the problem p with tile_prefix[p] <= g < tile_prefix[p + 1]
+// (tiles never mix problems); its network, source and outputs are copied to
+// shared memory when the problem changes.
+// ---------------------------------------------------------------------------
+template <typename Real, int T, int NT>
+__global__ void __launch_bounds__(NT, 1)
+slr_eval_batch_kernel(const NetParams<Real> *__restrict__ nets, const BoxSource *__restrict__ srcs,
+                      const EvalOutputs *__restrict__ outs, const int P, const long long *__restrict__ tile_prefix,
+                      const BatchShape shape, const int pass) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ NetParams<Real> snet;
+    __shared__ BoxSource ssrc;
+    __shared__ EvalOutputs sout;
+    __shared__ int s_p;
+    __shared__ long long s_base;
+    const TileSmem<Real> sm = carve_smem<Real, T>(smem_raw, shape.nmp, shape.d, shape.n_in_max, shape.R);
+    const long long total = tile_prefix[P];
+    int cur = -1;
+    for (long long g = blockIdx.x; g < total; g += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = P;   // largest p with tile_prefix[p] <= g
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (tile_prefix[mid] <= g) lo = mid;
+                else hi = mid;
+            }
+            s_p = lo;
+            s_base = (g - tile_prefix[lo]) * T;
+        }
         __syncthreads();
+        const int p = s_p;
+        if (p != cur) {
+            const int *from = reinterpret_cast<const int *>(&nets[p]);
+            int *to = reinterpret_cast<int *>(&snet);
+            for (int i = threadIdx.x; i < (int)(sizeof(NetParams<Real>) / 4); i += NT) to[i] = from[i];
+            if (threadIdx.x == 0) {
+                ssrc = srcs[p];
+                sout = outs[p];
+            }
+            cur = p;
+            __syncthreads();
+        }
+        eval_tile<Real, T, NT>(snet, ssrc, sout, pass, sm, s_base, source_count(ssrc));
     }
 }
 

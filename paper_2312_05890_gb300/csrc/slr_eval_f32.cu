@@ -59,4 +59,49 @@ int eval_blocks_per_sm_f32(int T, int NT, size_t smem) {
     }
 }
 
+
+template <int T>
+static cudaError_t launch_batch_t(int grid, size_t smem, cudaStream_t s, const NetParams<float> *nets,
+                                  const BoxSource *srcs, const EvalOutputs *outs, int P, const long long *prefix,
+                                  const BatchShape &shape, int pass) {
+    auto k = slr_eval_batch_kernel<float, T, 256>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(nets, srcs, outs, P, prefix, shape, pass);
+    return cudaGetLastError();
+}
+
+template <int T>
+static int occ_batch_t(size_t smem) {
+    auto k = slr_eval_batch_kernel<float, T, 256>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 256, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_eval_batch_f32(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> *nets,
+                                  const BoxSource *srcs, const EvalOutputs *outs, int P, const long long *prefix,
+                                  const BatchShape &shape, int pass) {
+    switch (T) {
+        case 64: return launch_batch_t<64>(grid, smem, s, nets, srcs, outs, P, prefix, shape, pass);
+        case 32: return launch_batch_t<32>(grid, smem, s, nets, srcs, outs, P, prefix, shape, pass);
+        case 16: return launch_batch_t<16>(grid, smem, s, nets, srcs, outs, P, prefix, shape, pass);
+        case 8: return launch_batch_t<8>(grid, smem, s, nets, srcs, outs, P, prefix, shape, pass);
+        case 4: return launch_batch_t<4>(grid, smem, s, nets, srcs, outs, P, prefix, shape, pass);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int eval_batch_blocks_per_sm_f32(int T, size_t smem) {
+    switch (T) {
+        case 64: return occ_batch_t<64>(smem);
+        case 32: return occ_batch_t<32>(smem);
+        case 16: return occ_batch_t<16>(smem);
+        case 8: return occ_batch_t<8>(smem);
+        case 4: return occ_batch_t<4>(smem);
+        default: return 0;
+    }
+}
+
 }  // namespace slr

@@ -8,7 +8,7 @@
 //              t < D, or adds one unit to the undecided volume when t = D.
 // Each warp aggregates its counts and its output slots with one atomic per
 // warp (ballot + popc); integer sums make the result independent of order.
-#include "slr_device.cuh"
+#include "slr_eval.cuh"
 #include "slr_kernels.h"
 
 namespace slr {
@@ -20,18 +20,18 @@ __global__ void init_count_kernel(uint64_t *codes0, LevelCounters *ctr) {
     }
 }
 
-__global__ void __launch_bounds__(256)
-compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
-               uint64_t *__restrict__ codes_out, LevelCounters *ctr, unsigned int *status,
-               int64_t cap, int t, int D, uint64_t *leaf_codes, uint8_t *leaf_depth,
-               uint8_t *leaf_cls, int64_t leaf_cap) {
+__device__ __forceinline__ void compact_body(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
+                                             uint64_t *__restrict__ codes_out, LevelCounters *ctr,
+                                             unsigned int *status, int64_t cap, int t, int D, uint64_t *leaf_codes,
+                                             uint8_t *leaf_depth, uint8_t *leaf_cls, int64_t leaf_cap, int block,
+                                             int nblocks) {
     const unsigned long long n_raw = ctr->frontier_n[t];
     const int64_t n = (int64_t)n_raw < cap ? (int64_t)n_raw : cap;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t warp_global = ((int64_t)block * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)nblocks * blockDim.x) >> 5;
+    if (block == 0 && threadIdx.x == 0) {
         ctr->level_boxes[t] = (unsigned long long)n;
         atomicAdd(&ctr->boxes, (unsigned long long)n);
     }
@@ -93,6 +93,80 @@ compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict_
             if (t == D) atomicAdd(&ctr->undecided_at_D, n_und);
         }
     }
+}
+
+__global__ void __launch_bounds__(256)
+compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
+               uint64_t *__restrict__ codes_out, LevelCounters *ctr, unsigned int *status,
+               int64_t cap, int t, int D, uint64_t *leaf_codes, uint8_t *leaf_depth,
+               uint8_t *leaf_cls, int64_t leaf_cap) {
+    compact_body(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes, leaf_depth, leaf_cls, leaf_cap,
+                 blockIdx.x, gridDim.x);
+}
+
+// ---- batched counting: many problems advance one level per step ------------
+
+// Exclusive prefix of the tiles of each problem's source at this step
+// (tile_prefix[P] = total).  One block; problems in chunks of its width.
+__global__ void __launch_bounds__(1024) tile_prefix_kernel(const BoxSource *srcs, int P, int T, long long *prefix) {
+    __shared__ long long buf[1024];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < P; c0 += 1024) {
+        const int p = c0 + threadIdx.x;
+        long long v = 0;
+        if (p < P) {
+            const int64_t n = source_count(srcs[p]);
+            v = (n + T - 1) / T;
+        }
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {   // inclusive Hillis-Steele scan
+            const long long add = threadIdx.x >= off ? buf[threadIdx.x - off] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (p < P) prefix[p] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) prefix[P] = carry;
+}
+
+// Compaction of every active problem: block (x, p) works on problem p.
+__global__ void __launch_bounds__(256) compact_batch_kernel(const CompactArgs *args, int t, unsigned int *status) {
+    const CompactArgs a = args[blockIdx.y];
+    if (t > a.D) return;
+    compact_body(a.codes_in, a.cls, a.codes_out, a.ctr, status, a.cap, t, a.D, nullptr, nullptr, nullptr, 0,
+                 blockIdx.x, gridDim.x);
+}
+
+// Start of a batched count: every problem's level 0 is its root box.
+__global__ void init_batch_kernel(const CompactArgs *args, int P) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) {
+        const_cast<uint64_t *>(args[p].codes_in)[0] = 0ull;
+        args[p].ctr->frontier_n[0] = 1ull;
+    }
+}
+
+cudaError_t launch_tile_prefix(const BoxSource *srcs, int P, int T, long long *prefix, cudaStream_t s) {
+    tile_prefix_kernel<<<1, 1024, 0, s>>>(srcs, P, T, prefix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_batch(const CompactArgs *args, int P, int t, unsigned int *status, int blocks_per_problem,
+                                 cudaStream_t s) {
+    compact_batch_kernel<<<dim3(blocks_per_problem, P), 256, 0, s>>>(args, t, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_batch(const CompactArgs *args, int P, cudaStream_t s) {
+    init_batch_kernel<<<(P + 127) / 128, 128, 0, s>>>(args, P);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s) {

@@ -27,6 +27,28 @@ size_t eval_tc_smem_bytes(int T, const NetParams<float> &net, const TcParams &tc
 cudaError_t launch_eval_tc(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                            const TcParams &tc, const BoxSource &src, const EvalOutputs &out, int pass);
 
+// Batched count (many problems, one persistent launch per step).
+struct CompactArgs {
+    const uint64_t *codes_in;
+    const uint8_t *cls;
+    uint64_t *codes_out;
+    LevelCounters *ctr;
+    int64_t cap;
+    int D;
+};
+cudaError_t launch_eval_batch_f32(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> *nets,
+                                  const BoxSource *srcs, const EvalOutputs *outs, int P, const long long *prefix,
+                                  const BatchShape &shape, int pass);
+cudaError_t launch_eval_batch_f64(int T, int grid, size_t smem, cudaStream_t s, const NetParams<double> *nets,
+                                  const BoxSource *srcs, const EvalOutputs *outs, int P, const long long *prefix,
+                                  const BatchShape &shape, int pass);
+int eval_batch_blocks_per_sm_f32(int T, size_t smem);
+int eval_batch_blocks_per_sm_f64(int T, size_t smem);
+cudaError_t launch_tile_prefix(const BoxSource *srcs, int P, int T, long long *prefix, cudaStream_t s);
+cudaError_t launch_compact_batch(const CompactArgs *args, int P, int t, unsigned int *status, int blocks_per_problem,
+                                 cudaStream_t s);
+cudaError_t launch_init_batch(const CompactArgs *args, int P, cudaStream_t s);
+
 cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s);
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,

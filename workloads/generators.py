@@ -234,6 +234,56 @@ def rare_violation(seed: int = 0, depth: int = 18, target_margin: float = 2e-3) 
     return Problem("rare_3-32-32-1", net, lo, hi, prop, depth, seed)
 
 
+def _batch_member(rng, d, width, hidden, n_props, depth_range, seed):
+    net = _mlp(rng, [d] + [width] * hidden + [int(rng.integers(2, 9))])
+    n_out = net.widths[-1]
+    out = []
+    tries = 0
+    while len(out) < n_props and tries < 50 * n_props:
+        tries += 1
+        side = rng.uniform(0.02, 0.2, size=d)
+        a = rng.uniform(-0.5, 0.5 - side)
+        lo = a.astype(np.float32)
+        hi = (a + side).astype(np.float32)
+        rows = []
+        for _ in range(int(rng.integers(1, 3))):
+            i, j = rng.choice(n_out, size=2, replace=False)
+            c = np.zeros(n_out, dtype=np.float32)
+            c[i] = rng.uniform(0.5, 2.0)
+            c[j] = -rng.uniform(0.5, 2.0)
+            rows.append((c, float(rng.normal(0.0, np.sqrt(0.1))), False))
+        D = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        p = Problem(f"batch_d{d}_w{width}_h{hidden}", net, lo, hi, _prop([rows]), D, seed)
+        vr = mc_violation_rate(p, 1 << 12, seed=seed + tries)
+        if 0.01 <= vr <= 0.99:
+            out.append(p)
+    return out
+
+
+def batched_uneven(seed: int = 0, n_nets: int = 16, props_per_net: int = 16, depth_range=(12, 22),
+                   widths=(32, 64, 128)):
+    """Many (network, property) problems of uneven size (the batched workload).
+
+    16 seeded networks with inputs d in {5, 8, 16, 32}, hidden widths from
+    `widths` and 2-8 hidden layers, each carrying 16 random boxes (sides
+    U(0.02, 0.2) inside [-0.5, 0.5]^d) with a one-clause property of 1-2 rows
+    a y_i - a' y_j + e >= 0 (a, a' ~ U(0.5, 2), e ~ N(0, 0.1)), redrawn until
+    the Monte-Carlo violation rate lies in [1 %, 99 %], and a depth cap
+    D ~ U{12..22}.  A width is kept only when its contraction tiles fit the
+    fused kernel: (2d + 3) * width / 8 <= 512.
+    """
+    rng = np.random.default_rng(seed)
+    probs = []
+    ds = [5, 8, 16, 32]
+    for k in range(n_nets):
+        d = ds[k % len(ds)]
+        ok_w = [w for w in widths if (2 * d + 3) * ((w + 7) // 8) <= 512]
+        width = int(rng.choice(ok_w))
+        hidden = int(rng.integers(2, 9))
+        probs += _batch_member(rng, d, width, hidden, props_per_net, depth_range, seed * 1000 + k)
+    return probs
+
+
 CONFIGS = {
     "tiny": tiny,
     "acas": acas_shaped,
