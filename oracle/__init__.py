@@ -12,6 +12,8 @@ Modules
            property fold and classification (Sec. 3 containment check).
   counter  split schedule, path-code decoding and the level-by-level exact
            count (Alg. 1 with a depth cap; Sec. 3 level-parallel BaB).
+  grad     central finite differences of the row bounds with respect to the
+           lower ReLU slopes, the box, the weights and the biases.
 
 Every function here is pinned by tests that do not re-use its own formulas
 (brute force over box vertices, closed forms, hand-worked examples, sampling).
@@ -21,3 +23,4 @@ from .slr import (  # noqa: F401
     fold_property, classify, forward_points, unsafe_points, to_exact,
 )
 from .counter import split_schedule, decode, count, CountResult  # noqa: F401
+from .grad import objective, fd_gradients, default_alpha  # noqa: F401

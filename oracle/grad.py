@@ -1,0 +1,98 @@
+"""Central finite differences of the SLR row bounds (test infrastructure only).
+
+The objective is J = sum_r (w_hi[r] hi_r + w_lo[r] lo_r) over one box's SLR row
+bounds (Sec. 2.2, Eq. 1; Sec. 3).  Derivatives are taken by central
+differences in float64 with step h on the lower ReLU slopes alpha (any value
+in [0, 1] keeps the relaxation sound), the box endpoints, the weights and the
+biases.  A coordinate is reported as a kink (NaN) when the estimates with
+steps h and h/2 disagree, i.e. a ReLU case or a sign of a coefficient changes
+inside the stencil; the adjoint is compared only away from kinks.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .slr import slr_forward
+
+
+def objective(net, lo, hi, prop, alpha, w_hi, w_lo):
+    """J for one box (lo, hi: (d,)), alpha: list of (n_k,) arrays or None."""
+    a = None if alpha is None else [np.asarray(x, dtype=np.float64)[None] for x in alpha]
+    rlo, rhi, _ = slr_forward(net, np.asarray(lo, np.float64)[None], np.asarray(hi, np.float64)[None], prop, alpha=a)
+    return float(np.dot(w_hi, rhi[0]) + np.dot(w_lo, rlo[0]))
+
+
+def _central(f, x0, h):
+    g = np.empty_like(x0)
+    for i in range(x0.size):
+        e = np.zeros_like(x0)
+        e.flat[i] = h
+        g.flat[i] = (f(x0 + e) - f(x0 - e)) / (2 * h)
+    return g
+
+
+def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6):
+    """Central-difference gradients of J; entries at kinks are NaN.
+
+    Returns dict with 'alpha' (list per hidden layer), 'lo', 'hi', 'W', 'b'.
+    """
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    alpha = [np.asarray(a, np.float64) for a in alpha]
+    sizes = [a.size for a in alpha]
+
+    def split(v):
+        out, o = [], 0
+        for s in sizes:
+            out.append(v[o:o + s])
+            o += s
+        return out
+
+    def both(f, x0):
+        g1 = _central(f, x0, h)
+        g2 = _central(f, x0, h / 2)
+        scale = 1.0 + np.abs(g1)
+        return np.where(np.abs(g1 - g2) <= tol * scale + 1e-9, g1, np.nan)
+
+    out = {}
+    a0 = np.concatenate(alpha) if alpha else np.zeros(0)
+    out["alpha"] = split(both(lambda v: objective(net, lo, hi, prop, split(v), w_hi, w_lo), a0))
+    out["lo"] = both(lambda v: objective(net, v, hi, prop, alpha, w_hi, w_lo), lo)
+    out["hi"] = both(lambda v: objective(net, lo, v, prop, alpha, w_hi, w_lo), hi)
+
+    class _N:
+        pass
+    Ws, bs = [], []
+    for k in range(len(net.W)):
+        W0 = np.asarray(net.W[k], np.float64)
+        b0 = np.asarray(net.b[k], np.float64)
+
+        def fw(v, k=k, W0=W0):
+            n = _N()
+            n.W = [np.asarray(x, np.float64) for x in net.W]
+            n.b = [np.asarray(x, np.float64) for x in net.b]
+            n.W[k] = v.reshape(W0.shape)
+            return objective(n, lo, hi, prop, alpha, w_hi, w_lo)
+
+        def fb(v, k=k):
+            n = _N()
+            n.W = [np.asarray(x, np.float64) for x in net.W]
+            n.b = [np.asarray(x, np.float64) for x in net.b]
+            n.b[k] = v
+            return objective(n, lo, hi, prop, alpha, w_hi, w_lo)
+
+        Ws.append(both(fw, W0.ravel()).reshape(W0.shape))
+        bs.append(both(fb, b0))
+    out["W"] = Ws
+    out["b"] = bs
+    return out
+
+
+def default_alpha(net, lo, hi, prop=None):
+    """The default lower slopes u_l / (u_l - l_l) of each unstable neuron (0 elsewhere)."""
+    _, _, pre = slr_forward(net, np.asarray(lo, np.float64), np.asarray(hi, np.float64), prop)
+    out = []
+    for ll, ul, lu, uu in pre:
+        unst = (ll < 0) & (uu > 0) & (ul > 0)
+        out.append(np.where(unst, ul / np.where(unst, ul - ll, 1.0), 0.0))
+    return out

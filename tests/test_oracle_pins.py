@@ -179,3 +179,31 @@ def test_relaxation_lines_touch_relu_at_the_ends():
     assert abs(U2[0, 0, 0] * 0.0 + U2[0, 0, 1] - 0.0) < 1e-15      # chord at lu is 0
     assert abs(U2[0, 0, 0] * 1.0 + U2[0, 0, 1] - 1.0) < 1e-15      # chord at uu is uu
     assert abs(L2[0, 0, 0] * 0.75 + L2[0, 0, 1]) < 1e-15          # alpha L vanishes where L does
+
+
+def test_slope_gradient_hand_worked():
+    """abs_via_two_relus with slopes a1, a2: lo = min_x (a1 - a2) x on [-1, 1] = -|a1 - a2|."""
+    from workloads.generators import Network
+    net = Network([np.array([[1.0], [-1.0]], np.float32), np.array([[1.0, 1.0]], np.float32)],
+                  [np.zeros(2, np.float32), np.zeros(1, np.float32)])
+    alpha = [np.array([0.7, 0.2])]
+    J = oracle.objective(net, np.array([-1.0]), np.array([1.0]), None, alpha, np.array([0.0]), np.array([1.0]))
+    assert abs(J + 0.5) < 1e-12
+    g = oracle.fd_gradients(net, np.array([-1.0]), np.array([1.0]), None, alpha, np.array([0.0]), np.array([1.0]))
+    np.testing.assert_allclose(g["alpha"][0], [-1.0, 1.0], atol=1e-7)
+
+
+def test_box_gradient_of_an_affine_network_closed_form():
+    """One affine layer y = w.x + c: hi = w.m + c + |w|.r, so dhi/dlo_j = (w_j - |w_j|)/2, dhi/dhi_j = (w_j + |w_j|)/2."""
+    from workloads.generators import Network
+    rng = np.random.default_rng(4)
+    w = rng.normal(size=(1, 4)).astype(np.float32)
+    net = Network([w], [np.array([0.3], np.float32)])
+    lo = rng.uniform(-1, 0, 4)
+    hi = lo + rng.uniform(0.2, 1, 4)
+    g = oracle.fd_gradients(net, lo, hi, None, [], np.array([1.0]), np.array([0.0]))
+    wd = w[0].astype(np.float64)
+    np.testing.assert_allclose(g["lo"], (wd - np.abs(wd)) / 2, atol=1e-7)
+    np.testing.assert_allclose(g["hi"], (wd + np.abs(wd)) / 2, atol=1e-7)
+    # weight gradient: d hi / d w_j = m_j + sign(w_j) r_j
+    np.testing.assert_allclose(g["W"][0][0], (lo + hi) / 2 + np.sign(wd) * (hi - lo) / 2, atol=1e-7)
