@@ -74,6 +74,11 @@ typedef struct {
     int32_t reserved;       /* must be 0 */
     int64_t frontier_cap;   /* most boxes one level may hold; default 1<<24 */
     int64_t leaf_cap;       /* most leaves recorded when record_leaves; default 1<<22 */
+    int32_t alpha_steps;    /* slr_count: projected-Adam steps on the lower ReLU slopes of the
+                               boxes a level leaves UNDECIDED (0 = fixed slopes u/(u-l)); default 0 */
+    float alpha_lr;         /* Adam step size of those steps; default 0.1 */
+    int64_t alpha_cap;      /* most UNDECIDED boxes per level whose slopes are optimised
+                               (the rest keep fixed slopes); default 1<<16 */
 } slr_options;
 
 #define SLR_MAX_LEVELS 63
@@ -101,6 +106,9 @@ typedef struct {
     int32_t tile_boxes;     /* boxes per CTA of the FP32 evaluation kernel (chosen by timing) */
     int32_t tile_threads;   /* threads per CTA of the FP32 evaluation kernel */
     uint64_t rechecked_fp32; /* TC_TF32: boxes re-bounded by the FP32 path */
+    uint64_t alpha_boxes;   /* alpha_steps > 0: boxes whose slopes were optimised */
+    uint64_t alpha_decided; /* of those, boxes that the optimised slopes decided */
+    double alpha_ms;        /* with profile: device time of the slope optimisation */
 } slr_result;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
@@ -151,10 +159,59 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out);
  * means host memory.  row_lo/row_hi are sound for the float32 network: they
  * are the FP32 SLR bounds widened outward by E, so row_lo + row_err and
  * row_hi - row_err are the FP32 SLR bounds themselves.  No FP64 re-check is
- * applied here.  Needs network and property (SLR_ESTATE); with host pointers
- * lo > hi or non-finite endpoints give SLR_EINVAL. */
+ * applied here.  `alpha` (nullable, n x H with H from slr_alpha_width) gives
+ * the lower slope of every hidden neuron of every box, clamped to [0, 1]
+ * (relax mode NEURIFY, FP32 precision); NULL uses u_l / (u_l - l_l).  Needs
+ * network and property (SLR_ESTATE); with host pointers lo > hi or non-finite
+ * endpoints give SLR_EINVAL. */
 int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi,
-               float *row_lo, float *row_hi, float *row_err, uint8_t *cls, int on_device);
+               const float *alpha, float *row_lo, float *row_hi, float *row_err, uint8_t *cls,
+               int on_device);
+
+/* Hidden neurons of the loaded network, H = widths[1] + ... + widths[K-1]: the
+ * row length of every slope array below. */
+int slr_alpha_width(slr_ctx *ctx, int64_t *H);
+
+/* Reverse mode of the SLR pass (Sec. 2.2, Eq. 1; Sec. 3) for n boxes.  With
+ * lo, hi the float32 SLR row bounds of each box (round to nearest, not widened),
+ * the loss is J = sum over boxes b and rows r of g_lo[b,r] lo[b,r] + g_hi[b,r]
+ * hi[b,r] (g_lo, g_hi: n x R, required).  Writes, each output optional (NULL):
+ *   row_lo, row_hi  n x R: lo and hi;
+ *   d_alpha         n x H: dJ/d(slope) of every hidden neuron, the slopes
+ *                   being free variables; 0 for neurons whose lower line is
+ *                   not a slope line (stable, or u_l <= 0);
+ *   d_box_lo, d_box_hi  n x d: dJ/d(box endpoints);
+ *   d_W, d_b        K pointers each (NULL, or all K set): dJ/dW_k
+ *                   (widths[k+1] x widths[k], row-major) and dJ/db_k, summed
+ *                   over the boxes and overwritten.  The last layer's
+ *                   gradients are those of the network's own W_K, b_K (the
+ *                   property rows C are folded in as C W_K).
+ * `alpha` (n x H, nullable) gives the lower slopes; entries are clamped to
+ * [0, 1] (any slope in [0, 1] is sound: relu(z) >= a z >= a Eq_l).  NULL uses
+ * u_l / (u_l - l_l) and then the gradients also flow through that formula
+ * (d_alpha is then dJ/d(slope) at those slopes, holding the box fixed).
+ * Gradients are those of the piecewise-smooth bounds: at a kink (a ReLU case
+ * or a coefficient sign changing) they are one-sided.  Relax mode NEURIFY
+ * only (SLR_EUNSUPPORTED otherwise).  `on_device` as in slr_bounds, for every
+ * pointer; float32 atomics make d_W and d_b vary in the last bits run to run. */
+int slr_margin_backward(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi,
+                        const float *alpha, const float *g_lo, const float *g_hi,
+                        float *row_lo, float *row_hi, float *d_alpha,
+                        float *d_box_lo, float *d_box_hi, float *const *d_W,
+                        float *const *d_b, int on_device);
+
+/* Tighten the bounds of n boxes by `steps` projected-Adam steps on their lower
+ * ReLU slopes (lr = step size; betas 0.9, 0.999), starting from u_l/(u_l - l_l).
+ * Each step differentiates the nearer decision's loss (the SAFE loss
+ * sum_c max(0, min_{r in c} hi_r) or the UNSAFE loss min_c max(0, -min_{r in c}
+ * lo_r), chosen per box at the first step), moves the slopes and clips them
+ * to [0, 1]; then the sound FP32 bounds at the new slopes are intersected with
+ * the best so far.  Writes the intersected sound bounds (row_lo/row_hi, n x R,
+ * including the starting slopes), the class they give (cls), and the final
+ * slopes (alpha, n x H); each output optional.  on_device as in slr_bounds. */
+int slr_optimize_alpha(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi,
+                       int steps, float lr, float *alpha, float *row_lo, float *row_hi,
+                       uint8_t *cls, int on_device);
 
 /* Leaves of the last slr_count when record_leaves was set: for each leaf its
  * path code (bit t-1-j = half taken at split j, 1 = upper), depth and class.

@@ -31,15 +31,20 @@ def _central(f, x0, h):
     return g
 
 
-def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6):
+def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6, w_idx=None):
     """Central-difference gradients of J; entries at kinks are NaN.
 
+    alpha: list of per-layer slope arrays, or None for the slopes u/(u-l)
+    (then J is differentiated through that formula and 'alpha' is empty).
+    w_idx: optional dict layer -> flat indices of the weights to difference
+    (the others are NaN); all weights when None.
     Returns dict with 'alpha' (list per hidden layer), 'lo', 'hi', 'W', 'b'.
     """
     lo = np.asarray(lo, np.float64)
     hi = np.asarray(hi, np.float64)
-    alpha = [np.asarray(a, np.float64) for a in alpha]
-    sizes = [a.size for a in alpha]
+    free = alpha is not None
+    alpha = [np.asarray(a, np.float64) for a in alpha] if free else None
+    sizes = [a.size for a in alpha] if free else []
 
     def split(v):
         out, o = [], 0
@@ -48,15 +53,27 @@ def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6):
             o += s
         return out
 
-    def both(f, x0):
-        g1 = _central(f, x0, h)
-        g2 = _central(f, x0, h / 2)
+    def both(f, x0, idx=None):
+        if idx is None:
+            g1 = _central(f, x0, h)
+            g2 = _central(f, x0, h / 2)
+        else:
+            g1 = np.full_like(x0, np.nan)
+            g2 = np.full_like(x0, np.nan)
+            for i in idx:
+                e = np.zeros_like(x0)
+                e.flat[i] = 1.0
+                g1.flat[i] = (f(x0 + h * e) - f(x0 - h * e)) / (2 * h)
+                g2.flat[i] = (f(x0 + h / 2 * e) - f(x0 - h / 2 * e)) / h
         scale = 1.0 + np.abs(g1)
         return np.where(np.abs(g1 - g2) <= tol * scale + 1e-9, g1, np.nan)
 
     out = {}
-    a0 = np.concatenate(alpha) if alpha else np.zeros(0)
-    out["alpha"] = split(both(lambda v: objective(net, lo, hi, prop, split(v), w_hi, w_lo), a0))
+    if free:
+        a0 = np.concatenate(alpha) if alpha else np.zeros(0)
+        out["alpha"] = split(both(lambda v: objective(net, lo, hi, prop, split(v), w_hi, w_lo), a0))
+    else:
+        out["alpha"] = []
     out["lo"] = both(lambda v: objective(net, v, hi, prop, alpha, w_hi, w_lo), lo)
     out["hi"] = both(lambda v: objective(net, lo, v, prop, alpha, w_hi, w_lo), hi)
 
@@ -81,8 +98,9 @@ def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6):
             n.b[k] = v
             return objective(n, lo, hi, prop, alpha, w_hi, w_lo)
 
-        Ws.append(both(fw, W0.ravel()).reshape(W0.shape))
-        bs.append(both(fb, b0))
+        idx = None if w_idx is None else w_idx.get(k, [])
+        Ws.append(both(fw, W0.ravel(), idx).reshape(W0.shape))
+        bs.append(both(fb, b0, None if w_idx is None else list(range(b0.size)) if k in w_idx else []))
     out["W"] = Ws
     out["b"] = bs
     return out

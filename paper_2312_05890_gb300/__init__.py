@@ -28,7 +28,8 @@ MAX_LEVELS = 63
 # Names the header declares (checked by the CPU test that loads the library).
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
-           "slr_count_noalloc", "slr_count_batch", "slr_last_error")
+           "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
+           "slr_optimize_alpha", "slr_last_error")
 
 
 class SlrError(RuntimeError):
@@ -41,7 +42,8 @@ class slr_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
                 ("fp64_recheck", ctypes.c_int32), ("record_leaves", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("frontier_cap", ctypes.c_int64), ("leaf_cap", ctypes.c_int64)]
+                ("frontier_cap", ctypes.c_int64), ("leaf_cap", ctypes.c_int64),
+                ("alpha_steps", ctypes.c_int32), ("alpha_lr", ctypes.c_float), ("alpha_cap", ctypes.c_int64)]
 
 
 _U64A = ctypes.c_uint64 * (MAX_LEVELS + 1)
@@ -55,7 +57,8 @@ class slr_result(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * 3), ("launches", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
-                ("rechecked_fp32", ctypes.c_uint64)]
+                ("rechecked_fp32", ctypes.c_uint64), ("alpha_boxes", ctypes.c_uint64),
+                ("alpha_decided", ctypes.c_uint64), ("alpha_ms", ctypes.c_double)]
 
     def to_dict(self):
         n = self.depth + 1
@@ -65,7 +68,8 @@ class slr_result(ctypes.Structure):
                     kernel_ms=[float(x) for x in self.kernel_ms], launches=int(self.launches),
                     h2d_bytes=int(self.h2d_bytes), d2h_bytes=int(self.d2h_bytes),
                     tile=(int(self.tile_boxes), int(self.tile_threads)),
-                    rechecked_fp32=int(self.rechecked_fp32),
+                    rechecked_fp32=int(self.rechecked_fp32), alpha_boxes=int(self.alpha_boxes),
+                    alpha_decided=int(self.alpha_decided), alpha_ms=float(self.alpha_ms),
                     level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 
@@ -99,7 +103,11 @@ def load_library(path: str = LIB_PATH):
         "slr_set_box": (ctypes.c_int, [P, ctypes.c_int, P, P]),
         "slr_set_property": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, P, P, P]),
         "slr_count": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
-        "slr_bounds": (ctypes.c_int, [P, i64, P, P, P, P, P, P, ctypes.c_int]),
+        "slr_bounds": (ctypes.c_int, [P, i64, P, P, P, P, P, P, P, ctypes.c_int]),
+        "slr_alpha_width": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
+        "slr_margin_backward": (ctypes.c_int, [P, i64, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]),
+        "slr_optimize_alpha": (ctypes.c_int, [P, i64, P, P, ctypes.c_int, ctypes.c_float, P, P, P, P,
+                                              ctypes.c_int]),
         "slr_leaves": (ctypes.c_int, [P, i64, P, P, P, ctypes.POINTER(i64)]),
         "slr_schedule": (ctypes.c_int, [P, ctypes.c_int, P]),
         "slr_count_noalloc": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
@@ -186,34 +194,114 @@ def slr_count(ctx, D: int) -> dict:
     return res.to_dict()
 
 
-def slr_bounds(ctx, box_lo, box_hi, R: int, want_rows=True, want_cls=True, want_err=False):
+class _Buffers:
+    """Inputs and outputs of one call, all on the host (numpy) or all on the device (CUDA tensors)."""
+
+    def __init__(self, like):
+        self.device = hasattr(like, "data_ptr")
+        self.keep = []
+
+    def inp(self, a, dtype=np.float32):
+        if a is None:
+            return None
+        if self.device:
+            import torch
+            t = a.detach().to(dtype=torch.float32 if dtype == np.float32 else torch.uint8).contiguous()
+            self.keep.append(t)
+            return ctypes.c_void_p(t.data_ptr())
+        x = np.ascontiguousarray(a, dtype=dtype)
+        self.keep.append(x)
+        return _ptr(x)
+
+    def out(self, shape, dtype=np.float32, like=None):
+        if self.device:
+            import torch
+            return torch.empty(shape, dtype=torch.float32 if dtype == np.float32 else torch.uint8, device=like.device)
+        return np.empty(shape, dtype=dtype)
+
+    @staticmethod
+    def ptr(a):
+        if a is None:
+            return None
+        return ctypes.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else _ptr(a)
+
+
+def slr_bounds(ctx, box_lo, box_hi, R: int, want_rows=True, want_cls=True, want_err=False, alpha=None):
     """Bounds of n boxes: (row_lo, row_hi, cls) or, with want_err, (row_lo, row_hi, cls, row_err).
 
     numpy inputs use host memory; CUDA tensors (with .data_ptr) stay on the device.
+    alpha (n x H, optional) gives the lower ReLU slopes.
     """
     lib = load_library()
-    if hasattr(box_lo, "data_ptr"):
-        import torch
-        n = int(box_lo.shape[0])
-        dev = box_lo.device
-        rl = torch.empty((n, R), dtype=torch.float32, device=dev) if want_rows else None
-        rh = torch.empty((n, R), dtype=torch.float32, device=dev) if want_rows else None
-        re_ = torch.empty((n, R), dtype=torch.float32, device=dev) if want_err else None
-        cl = torch.empty((n,), dtype=torch.uint8, device=dev) if want_cls else None
-        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
-        _check(lib, ctx, lib.slr_bounds(ctx, n, p(box_lo.contiguous()), p(box_hi.contiguous()), p(rl), p(rh),
-                                        p(re_), p(cl), 1))
-        return (rl, rh, cl, re_) if want_err else (rl, rh, cl)
-    lo = np.ascontiguousarray(box_lo, dtype=np.float32)
-    hi = np.ascontiguousarray(box_hi, dtype=np.float32)
-    n = int(lo.shape[0])
-    rl = np.empty((n, R), dtype=np.float32) if want_rows else None
-    rh = np.empty((n, R), dtype=np.float32) if want_rows else None
-    re_ = np.empty((n, R), dtype=np.float32) if want_err else None
-    cl = np.empty((n,), dtype=np.uint8) if want_cls else None
-    q = lambda a: _ptr(a) if a is not None else None  # noqa: E731
-    _check(lib, ctx, lib.slr_bounds(ctx, n, _ptr(lo), _ptr(hi), q(rl), q(rh), q(re_), q(cl), 0))
+    io = _Buffers(box_lo)
+    n = int(box_lo.shape[0])
+    lo, hi, al = io.inp(box_lo), io.inp(box_hi), io.inp(alpha)
+    rl = io.out((n, R), like=box_lo) if want_rows else None
+    rh = io.out((n, R), like=box_lo) if want_rows else None
+    re_ = io.out((n, R), like=box_lo) if want_err else None
+    cl = io.out((n,), np.uint8, like=box_lo) if want_cls else None
+    q = io.ptr
+    _check(lib, ctx, lib.slr_bounds(ctx, n, lo, hi, al, q(rl), q(rh), q(re_), q(cl), 1 if io.device else 0))
     return (rl, rh, cl, re_) if want_err else (rl, rh, cl)
+
+
+def slr_alpha_width(ctx) -> int:
+    lib = load_library()
+    h = ctypes.c_int64()
+    _check(lib, ctx, lib.slr_alpha_width(ctx, ctypes.byref(h)))
+    return int(h.value)
+
+
+def slr_margin_backward(ctx, box_lo, box_hi, R: int, g_lo, g_hi, alpha=None, widths=None, want_rows=True,
+                        want_alpha=True, want_box=True):
+    """Gradients of J = sum(g_lo * lo + g_hi * hi) over the float32 SLR row bounds of n boxes.
+
+    Returns a dict with 'row_lo', 'row_hi' (n x R), 'd_alpha' (n x H), 'd_lo', 'd_hi' (n x d) and,
+    when `widths` (the network's widths[0..K]) is given, 'd_W' and 'd_b' (lists over layers).
+    """
+    lib = load_library()
+    io = _Buffers(box_lo)
+    n, d = int(box_lo.shape[0]), int(box_lo.shape[1])
+    H = slr_alpha_width(ctx)
+    lo, hi, al = io.inp(box_lo), io.inp(box_hi), io.inp(alpha)
+    gl, gh = io.inp(g_lo), io.inp(g_hi)
+    out = {}
+    out["row_lo"] = io.out((n, R), like=box_lo) if want_rows else None
+    out["row_hi"] = io.out((n, R), like=box_lo) if want_rows else None
+    out["d_alpha"] = io.out((n, H), like=box_lo) if want_alpha else None
+    out["d_lo"] = io.out((n, d), like=box_lo) if want_box else None
+    out["d_hi"] = io.out((n, d), like=box_lo) if want_box else None
+    wp = bp = None
+    if widths is not None:
+        K = len(widths) - 1
+        out["d_W"] = [io.out((int(widths[k + 1]), int(widths[k])), like=box_lo) for k in range(K)]
+        out["d_b"] = [io.out((int(widths[k + 1]),), like=box_lo) for k in range(K)]
+        wp = (ctypes.c_void_p * K)(*[io.ptr(x).value for x in out["d_W"]])
+        bp = (ctypes.c_void_p * K)(*[io.ptr(x).value for x in out["d_b"]])
+    q = io.ptr
+    _check(lib, ctx, lib.slr_margin_backward(ctx, n, lo, hi, al, gl, gh, q(out["row_lo"]), q(out["row_hi"]),
+                                             q(out["d_alpha"]), q(out["d_lo"]), q(out["d_hi"]),
+                                             ctypes.cast(wp, ctypes.c_void_p) if wp is not None else None,
+                                             ctypes.cast(bp, ctypes.c_void_p) if bp is not None else None,
+                                             1 if io.device else 0))
+    return out
+
+
+def slr_optimize_alpha(ctx, box_lo, box_hi, R: int, steps: int = 20, lr: float = 0.1, want_alpha=True):
+    """Projected-Adam steps on the lower slopes: (row_lo, row_hi, cls, alpha) with sound, intersected bounds."""
+    lib = load_library()
+    io = _Buffers(box_lo)
+    n = int(box_lo.shape[0])
+    H = slr_alpha_width(ctx)
+    lo, hi = io.inp(box_lo), io.inp(box_hi)
+    rl = io.out((n, R), like=box_lo)
+    rh = io.out((n, R), like=box_lo)
+    cl = io.out((n,), np.uint8, like=box_lo)
+    al = io.out((n, H), like=box_lo) if want_alpha else None
+    q = io.ptr
+    _check(lib, ctx, lib.slr_optimize_alpha(ctx, n, lo, hi, int(steps), float(lr), q(al), q(rl), q(rh), q(cl),
+                                            1 if io.device else 0))
+    return rl, rh, cl, al
 
 
 def slr_leaves(ctx, cap: int):
@@ -303,6 +391,7 @@ class Counter:
 
     def load_network(self, W, b):
         slr_load_network(self.ctx, W, b)
+        self.widths = [int(np.asarray(W[0]).shape[1])] + [int(np.asarray(w).shape[0]) for w in W]
 
     def set_box(self, lo, hi):
         slr_set_box(self.ctx, lo, hi)
@@ -333,8 +422,18 @@ class Counter:
     def count_noalloc(self, D: int) -> dict:
         return slr_count_noalloc(self.ctx, D)
 
-    def bounds(self, lo, hi, want_rows=True, want_cls=True, want_err=False):
-        return slr_bounds(self.ctx, lo, hi, self.R, want_rows, want_cls, want_err)
+    def bounds(self, lo, hi, want_rows=True, want_cls=True, want_err=False, alpha=None):
+        return slr_bounds(self.ctx, lo, hi, self.R, want_rows, want_cls, want_err, alpha)
+
+    def alpha_width(self) -> int:
+        return slr_alpha_width(self.ctx)
+
+    def margin_backward(self, lo, hi, g_lo, g_hi, alpha=None, weights=False, **kw):
+        return slr_margin_backward(self.ctx, lo, hi, self.R, g_lo, g_hi, alpha,
+                                   self.widths if weights else None, **kw)
+
+    def optimize_alpha(self, lo, hi, steps: int = 20, lr: float = 0.1, want_alpha=True):
+        return slr_optimize_alpha(self.ctx, lo, hi, self.R, steps, lr, want_alpha)
 
     def leaves(self, cap: int = 1 << 22):
         return slr_leaves(self.ctx, cap)

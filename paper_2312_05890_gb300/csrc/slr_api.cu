@@ -85,6 +85,13 @@ struct slr_ctx {
     BatchState *batch = nullptr;
     std::string tuned_key;                // network shape the FP32 tile choice was timed for
     int tuned_T = 0, tuned_NT = 0;
+    const float *dC = nullptr;            // property rows on the device (inside net_buf)
+    int64_t H = 0;                        // hidden neurons (slope row length)
+    int adj_nck = 0, adj_grid = 0, adj_nmax = 0;
+    size_t adj_smem = 0;
+    void *alpha_buf = nullptr;            // slope optimisation during a count
+    size_t alpha_buf_bytes = 0;
+    unsigned long long *alpha_ctr = nullptr;  // per level: undecided list length, then decided
 
     int64_t cap = 0, near_cap = 0;
     uint64_t *codes[2] = {nullptr, nullptr};
@@ -478,7 +485,8 @@ int prepare_device(slr_ctx *ctx) {
     HostLayers<double> Ld;
     build_layers(ctx, Lf);
     build_layers(ctx, Ld);
-    const size_t bytes = layers_bytes(Lf) + layers_bytes(Ld);
+    const size_t c_bytes = align_up(ctx->C.size() * sizeof(float));
+    const size_t bytes = layers_bytes(Lf) + layers_bytes(Ld) + c_bytes;
     if (ctx->net_buf) {
         cudaFree(ctx->net_buf);
         ctx->net_buf = nullptr;
@@ -491,6 +499,9 @@ int prepare_device(slr_ctx *ctx) {
     size_t off = 0;
     layout_params(ctx, Lf, (unsigned char *)ctx->net_buf, ctx->h_stage, off, ctx->nf);
     layout_params(ctx, Ld, (unsigned char *)ctx->net_buf, ctx->h_stage, off, ctx->nd);
+    std::memcpy(ctx->h_stage + off, ctx->C.data(), ctx->C.size() * sizeof(float));
+    ctx->dC = reinterpret_cast<const float *>((unsigned char *)ctx->net_buf + off);
+    off += c_bytes;
     CK(ctx, cudaMemcpyAsync(ctx->net_buf, ctx->h_stage, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->h2d_pending += (int64_t)bytes;
@@ -517,6 +528,30 @@ int prepare_device(slr_ctx *ctx) {
             ctx->smem64 = c.smem;
             ctx->grid64 = c.blocks * ctx->sm_count;
         }
+    }
+    // adjoint: keep as many hidden layers' equations in shared memory as fit in
+    // 96 KB, recompute the others
+    {
+        slr::AdjArgs a{};
+        a.net = ctx->nf;
+        a.H = 0;
+        for (int k = 1; k < ctx->K; ++k) a.H += ctx->widths[k];
+        a.n_max = 0;
+        for (int k = 1; k <= ctx->K; ++k) a.n_max = std::max(a.n_max, ctx->nf.n[k]);
+        a.nck = 0;
+        while (a.nck < ctx->K - 1) {
+            a.nck += 1;
+            if (slr::adjoint_smem_bytes(a) > 96 * 1024) {
+                a.nck -= 1;
+                break;
+            }
+        }
+        ctx->H = a.H;
+        ctx->adj_nmax = a.n_max;
+        ctx->adj_nck = a.nck;
+        ctx->adj_smem = slr::adjoint_smem_bytes(a);
+        const int nb = ctx->adj_smem <= (size_t)kMaxSmem ? slr::adjoint_blocks_per_sm(ctx->adj_smem) : 0;
+        ctx->adj_grid = nb * ctx->sm_count;
     }
     if (ctx->opt.precision == SLR_PREC_TC_TF32) {
         if ((rc = build_tc(ctx, Lf))) return rc;
@@ -594,6 +629,14 @@ int ensure_count_buffers(slr_ctx *ctx) {
     return SLR_OK;
 }
 
+int check_boxes(slr_ctx *ctx, int64_t n, int d, const float *box_lo, const float *box_hi) {
+    for (int64_t k = 0; k < n * d; ++k) {
+        if (!std::isfinite(box_lo[k]) || !std::isfinite(box_hi[k]) || box_lo[k] > box_hi[k])
+            return fail(ctx, SLR_EINVAL, "box %lld: bad endpoints in dimension %d", (long long)(k / d), (int)(k % d));
+    }
+    return SLR_OK;
+}
+
 int check_ready(slr_ctx *ctx) {
     if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
     if (!ctx->has_net || !ctx->has_box || !ctx->has_prop)
@@ -641,6 +684,11 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
 
 int slr_internal_fail(slr_ctx *ctx, int code, const char *msg) { return fail(ctx, code, "%s", msg); }
 
+int slr_internal_alpha_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t, int64_t *launches);
+namespace {
+int check_adjoint(slr_ctx *ctx);
+}
+
 extern "C" {
 
 void slr_default_options(slr_options *opt) {
@@ -653,6 +701,9 @@ void slr_default_options(slr_options *opt) {
     opt->reserved = 0;
     opt->frontier_cap = (int64_t)1 << 24;
     opt->leaf_cap = (int64_t)1 << 22;
+    opt->alpha_steps = 0;
+    opt->alpha_lr = 0.1f;
+    opt->alpha_cap = (int64_t)1 << 16;
 }
 
 int slr_create(slr_ctx **out, int device, void *cuda_stream) {
@@ -700,6 +751,8 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->leaf_depth);
     cudaFree(ctx->leaf_cls);
     cudaFree(ctx->scratch);
+    cudaFree(ctx->alpha_buf);
+    cudaFree(ctx->alpha_ctr);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -729,6 +782,16 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
     if (opt->reserved != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
     if (opt->record_leaves && (opt->leaf_cap < 1 || opt->leaf_cap > ((int64_t)1 << 34)))
         return fail(ctx, SLR_EINVAL, "leaf_cap %lld out of range", (long long)opt->leaf_cap);
+    if (opt->alpha_steps < 0 || opt->alpha_steps > 1000)
+        return fail(ctx, SLR_EINVAL, "alpha_steps %d out of range [0, 1000]", opt->alpha_steps);
+    if (opt->alpha_steps > 0) {
+        if (!(opt->alpha_lr > 0.f) || !std::isfinite(opt->alpha_lr))
+            return fail(ctx, SLR_EINVAL, "alpha_lr must be finite and positive");
+        if (opt->alpha_cap < 1 || opt->alpha_cap > ((int64_t)1 << 24))
+            return fail(ctx, SLR_EINVAL, "alpha_cap %lld out of range", (long long)opt->alpha_cap);
+        if (opt->relax_mode != SLR_RELAX_NEURIFY)
+            return fail(ctx, SLR_EUNSUPPORTED, "slope optimisation needs relax mode NEURIFY");
+    }
     if (opt->relax_mode != ctx->opt.relax_mode || opt->precision != ctx->opt.precision) ctx->dev_dirty = true;
     ctx->opt = *opt;
     return SLR_OK;
@@ -847,6 +910,13 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
 
     const bool leaves = ctx->opt.record_leaves != 0;
     const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0;
+    const bool slopes = ctx->opt.alpha_steps > 0;
+    if (slopes) {
+        if ((rc = check_adjoint(ctx))) return rc;
+        if (!ctx->alpha_ctr)
+            CK(ctx, cudaMalloc(&ctx->alpha_ctr, 2 * (slr::kMaxDepth + 2) * sizeof(unsigned long long)));
+        CK(ctx, cudaMemsetAsync(ctx->alpha_ctr, 0, 2 * (slr::kMaxDepth + 2) * sizeof(unsigned long long), ctx->stream));
+    }
     const bool use_tc = ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok;
     const int compact_grid = std::max(1, ctx->sm_count * 4);
     const bool prof = ctx->opt.profile != 0;
@@ -927,6 +997,12 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         }
         }
         CK(ctx, mark(t, 2));
+        if (slopes && t < D) {
+            // boxes at depth D are leaves either way; above it, optimised slopes
+            // may decide boxes that would otherwise be split
+            if ((rc = slr_internal_alpha_level(ctx, src, t, &launches))) return rc;
+        }
+        CK(ctx, mark(t, 3));
         CK(ctx, mark(t, 4));
         CK(ctx, slr::launch_compact(ctx->codes[t & 1], ctx->cls, ctx->codes[(t + 1) & 1], ctx->ctr, ctx->status,
                                     ctx->cap, t, D, leaves ? ctx->leaf_codes : nullptr, ctx->leaf_depth,
@@ -937,6 +1013,9 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long h_alpha[2 * (slr::kMaxDepth + 2)] = {};
+    if (slopes)
+        CK(ctx, cudaMemcpyAsync(h_alpha, ctx->alpha_ctr, sizeof h_alpha, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -967,13 +1046,23 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     out->h2d_bytes = h2d;
     out->tile_boxes = ctx->T32;
     out->tile_threads = ctx->NT32;
-    out->d2h_bytes = (int64_t)(sizeof(slr::LevelCounters) + sizeof(unsigned int));
+    out->d2h_bytes = (int64_t)(sizeof(slr::LevelCounters) + sizeof(unsigned int) + (slopes ? sizeof h_alpha : 0));
+    if (slopes) {
+        const int64_t acap = std::min<int64_t>(ctx->opt.alpha_cap, ctx->cap);
+        for (int t = 0; t <= D; ++t) {
+            out->alpha_boxes += std::min<unsigned long long>(h_alpha[2 * t], (unsigned long long)acap);
+            out->alpha_decided += h_alpha[2 * t + 1];
+        }
+    }
     if (prof) {
         for (int t = 0; t <= D; ++t) {
             float a = 0.f, b = 0.f, c2 = 0.f;
             cudaEventElapsedTime(&a, ctx->prof_ev[(size_t)t * 6 + 0], ctx->prof_ev[(size_t)t * 6 + 1]);
             cudaEventElapsedTime(&b, ctx->prof_ev[(size_t)t * 6 + 1], ctx->prof_ev[(size_t)t * 6 + 2]);
             cudaEventElapsedTime(&c2, ctx->prof_ev[(size_t)t * 6 + 4], ctx->prof_ev[(size_t)t * 6 + 5]);
+            float s3 = 0.f;
+            cudaEventElapsedTime(&s3, ctx->prof_ev[(size_t)t * 6 + 2], ctx->prof_ev[(size_t)t * 6 + 3]);
+            out->alpha_ms += s3;
             out->kernel_ms[0] += a;
             out->kernel_ms[1] += b;
             out->kernel_ms[2] += c2;
@@ -993,28 +1082,29 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     return SLR_OK;
 }
 
-int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, float *row_lo, float *row_hi,
-               float *row_err, uint8_t *cls, int on_device) {
+int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, const float *alpha,
+               float *row_lo, float *row_hi, float *row_err, uint8_t *cls, int on_device) {
     if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
     if (!ctx->has_net || !ctx->has_prop) return fail(ctx, SLR_ESTATE, "network and property must be set");
     if (n < 0 || (n > 0 && (!box_lo || !box_hi))) return fail(ctx, SLR_EINVAL, "bad box arguments");
     if ((row_lo == nullptr) != (row_hi == nullptr)) return fail(ctx, SLR_EINVAL, "row_lo and row_hi go together");
+    if (alpha && ctx->opt.relax_mode != SLR_RELAX_NEURIFY)
+        return fail(ctx, SLR_EUNSUPPORTED, "supplied slopes need relax mode NEURIFY");
     if (n == 0) return SLR_OK;
     CK(ctx, cudaSetDevice(ctx->device));
     int rc = prepare_device(ctx);
     if (rc) return rc;
     const int d = ctx->widths[0];
     const int R = (int)ctx->e.size();
-    const float *dlo = box_lo, *dhi = box_hi;
+    const int64_t H = ctx->H;
+    const float *dlo = box_lo, *dhi = box_hi, *dal = alpha;
     float *drl = row_lo, *drh = row_hi, *dre = row_err;
     uint8_t *dcls = cls;
     if (!on_device) {
-        for (int64_t k = 0; k < n * d; ++k) {
-            if (!std::isfinite(box_lo[k]) || !std::isfinite(box_hi[k]) || box_lo[k] > box_hi[k])
-                return fail(ctx, SLR_EINVAL, "box %lld: bad endpoints in dimension %d", (long long)(k / d), (int)(k % d));
-        }
+        if ((rc = check_boxes(ctx, n, d, box_lo, box_hi))) return rc;
+        const size_t na = alpha ? (size_t)n * H : 0;
         const size_t need = align_up(2 * (size_t)n * d * sizeof(float)) + align_up(3 * (size_t)n * R * sizeof(float)) +
-                            align_up((size_t)n);
+                            align_up((size_t)n) + align_up(na * sizeof(float));
         if ((rc = ensure_scratch(ctx, need))) return rc;
         unsigned char *p = (unsigned char *)ctx->scratch;
         float *slo = (float *)p;
@@ -1025,8 +1115,13 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
         dre = row_err ? (float *)p + 2 * (size_t)n * R : nullptr;
         p += align_up(3 * (size_t)n * R * sizeof(float));
         dcls = cls ? (uint8_t *)p : nullptr;
+        p += align_up((size_t)n);
         CK(ctx, cudaMemcpyAsync(slo, box_lo, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
         CK(ctx, cudaMemcpyAsync(shi, box_hi, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        if (alpha) {
+            CK(ctx, cudaMemcpyAsync(p, alpha, na * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            dal = (const float *)p;
+        }
         dlo = slo;
         dhi = shi;
     }
@@ -1036,6 +1131,8 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
     src.lo = dlo;
     src.hi = dhi;
     src.cap = n;
+    src.alpha = dal;
+    src.alpha_ld = H;
     slr::EvalOutputs o{};
     o.cls = dcls;
     o.row_lo = drl;
@@ -1047,7 +1144,7 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
     }
     o.status = ctx->status;
     CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
-    if (ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok) {
+    if (ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok && alpha == nullptr) {
         const int64_t tiles = (n + ctx->T_tc - 1) / ctx->T_tc;
         const int grid = (int)std::min<int64_t>(tiles, ctx->grid_tc);
         CK(ctx, slr::launch_eval_tc(ctx->T_tc, grid, ctx->smem_tc, ctx->stream, ctx->nf, ctx->tcp, src, o, 0));
@@ -1510,3 +1607,364 @@ extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems,
     if (st & slr::kStatusNearOverflow) return fail(ctx, SLR_EOVERFLOW, "an FP64 re-check list overflowed");
     return SLR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Lower-slope optimisation: the adjoint of the SLR pass and projected Adam.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr float kBeta1 = 0.9f, kBeta2 = 0.999f, kAdamEps = 1e-8f;
+
+slr::AdjArgs adj_base(const slr_ctx *ctx) {
+    slr::AdjArgs a{};
+    a.net = ctx->nf;
+    a.H = ctx->H;
+    a.n_max = ctx->adj_nmax;
+    a.nck = ctx->adj_nck;
+    a.Cprop = ctx->dC;
+    a.n_out = ctx->widths[ctx->K];
+    a.lr = 0.f;
+    a.beta1 = kBeta1;
+    a.beta2 = kBeta2;
+    a.eps = kAdamEps;
+    return a;
+}
+
+void adam_step(slr::AdjArgs &a, int t, float lr) {
+    a.adam_t = t;
+    a.lr = lr;
+    a.beta1_t = (float)std::pow((double)kBeta1, t);
+    a.beta2_t = (float)std::pow((double)kBeta2, t);
+}
+
+int check_adjoint(slr_ctx *ctx) {
+    if (ctx->opt.relax_mode != SLR_RELAX_NEURIFY)
+        return fail(ctx, SLR_EUNSUPPORTED, "the adjoint needs relax mode NEURIFY");
+    if (ctx->adj_grid <= 0)
+        return fail(ctx, SLR_EUNSUPPORTED, "network too large for the adjoint kernel (%zu bytes of shared memory)",
+                    ctx->adj_smem);
+    return SLR_OK;
+}
+
+// Device regions of a slope optimisation over `cap` boxes.
+struct AlphaBuffers {
+    float *alpha, *m, *v, *lo_new, *hi_new, *lo_best, *hi_best;
+    int8_t *dir;
+    int64_t *list;
+};
+
+size_t alpha_bytes(int64_t cap, int64_t H, int R) {
+    return align_up((size_t)cap * H * sizeof(float)) * 3 + align_up((size_t)cap * R * sizeof(float)) * 4 +
+           align_up((size_t)cap) + align_up((size_t)cap * sizeof(int64_t));
+}
+
+AlphaBuffers carve_alpha(void *base, int64_t cap, int64_t H, int R) {
+    unsigned char *p = (unsigned char *)base;
+    AlphaBuffers b;
+    auto take = [&](size_t bytes) {
+        unsigned char *q = p;
+        p += align_up(bytes);
+        return q;
+    };
+    b.alpha = (float *)take((size_t)cap * H * sizeof(float));
+    b.m = (float *)take((size_t)cap * H * sizeof(float));
+    b.v = (float *)take((size_t)cap * H * sizeof(float));
+    b.lo_new = (float *)take((size_t)cap * R * sizeof(float));
+    b.hi_new = (float *)take((size_t)cap * R * sizeof(float));
+    b.lo_best = (float *)take((size_t)cap * R * sizeof(float));
+    b.hi_best = (float *)take((size_t)cap * R * sizeof(float));
+    b.dir = (int8_t *)take((size_t)cap);
+    b.list = (int64_t *)take((size_t)cap * sizeof(int64_t));
+    return b;
+}
+
+// Sound bounds at the slopes in `alpha` (NULL: u/(u-l)) for positions of `src`,
+// written by position.
+int eval_by_position(slr_ctx *ctx, slr::BoxSource src, const float *alpha, float *lo, float *hi, int64_t n_hint) {
+    src.alpha = alpha;
+    src.alpha_ld = ctx->H;
+    slr::EvalOutputs o{};
+    o.row_lo = lo;
+    o.row_hi = hi;
+    o.by_position = 1;
+    o.status = ctx->status;
+    const int64_t tiles = (n_hint + ctx->T32 - 1) / ctx->T32;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ctx->grid32));
+    CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->NT32, grid, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
+    return SLR_OK;
+}
+
+// `steps` projected-Adam steps on the slopes of the boxes of `src` (positions
+// 0..cap-1, count on the device when `count` is set), keeping in (lo_best,
+// hi_best) the intersection of the sound bounds of every step, starting with
+// the slopes u/(u-l); class bytes go to cls_pos (by position) and/or
+// cls_idx (through src.index).  Returns the number of kernel launches in *launches.
+int optimise_slopes(slr_ctx *ctx, const slr::BoxSource &src, int64_t cap, const unsigned long long *count,
+                    const AlphaBuffers &b, int steps, float lr, uint8_t *cls_pos, uint8_t *cls_idx,
+                    unsigned long long *decided, bool want_alpha, int64_t *launches) {
+    int rc;
+    if ((rc = eval_by_position(ctx, src, nullptr, b.lo_new, b.hi_new, cap))) return rc;
+    CK(ctx, slr::launch_merge_bounds(ctx->nf, cap, count, b.lo_new, b.hi_new, b.lo_best, b.hi_best,
+                                     steps == 0 ? cls_pos : nullptr, steps == 0 ? cls_idx : nullptr, src.index, 1,
+                                     steps == 0 ? decided : nullptr, ctx->stream));
+    *launches += 2;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, ctx->adj_grid));
+    slr::AdjArgs a = adj_base(ctx);
+    a.src = src;
+    a.n = cap;
+    a.count = count;
+    a.alpha = b.alpha;
+    a.dir = b.dir;
+    a.adam_m = b.m;
+    a.adam_v = b.v;
+    if (steps == 0 && want_alpha) {
+        a.alpha_mode = slr::kAlphaInit;
+        CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+        *launches += 1;
+    }
+    for (int t = 1; t <= steps; ++t) {
+        a.alpha_mode = t == 1 ? slr::kAlphaInit : slr::kAlphaFree;
+        adam_step(a, t, lr);
+        CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+        if ((rc = eval_by_position(ctx, src, b.alpha, b.lo_new, b.hi_new, cap))) return rc;
+        const bool last = t == steps;
+        CK(ctx, slr::launch_merge_bounds(ctx->nf, cap, count, b.lo_new, b.hi_new, b.lo_best, b.hi_best,
+                                         last ? cls_pos : nullptr, last ? cls_idx : nullptr, src.index, 0,
+                                         last ? decided : nullptr, ctx->stream));
+        *launches += 3;
+    }
+    return SLR_OK;
+}
+
+int ensure_alpha_buf(slr_ctx *ctx, size_t bytes) {
+    if (ctx->alpha_buf_bytes >= bytes) return SLR_OK;
+    cudaFree(ctx->alpha_buf);
+    ctx->alpha_buf = nullptr;
+    ctx->alpha_buf_bytes = 0;
+    CK(ctx, cudaMalloc(&ctx->alpha_buf, bytes));
+    ctx->alpha_buf_bytes = bytes;
+    return SLR_OK;
+}
+
+}  // namespace
+
+// Slope optimisation of the boxes a level of a count leaves UNDECIDED.
+int slr_internal_alpha_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t, int64_t *launches) {
+    const int64_t cap = std::min<int64_t>(ctx->opt.alpha_cap, ctx->cap);
+    const int R = (int)ctx->e.size();
+    int rc = ensure_alpha_buf(ctx, alpha_bytes(cap, ctx->H, R));
+    if (rc) return rc;
+    if (!ctx->alpha_ctr) CK(ctx, cudaMalloc(&ctx->alpha_ctr, 2 * (slr::kMaxDepth + 2) * sizeof(unsigned long long)));
+    const AlphaBuffers b = carve_alpha(ctx->alpha_buf, cap, ctx->H, R);
+    unsigned long long *list_n = ctx->alpha_ctr + 2 * t;
+    CK(ctx, slr::launch_gather_undecided(ctx->cls, frontier.count, ctx->cap, b.list, list_n, cap,
+                                         std::max(1, ctx->sm_count * 4), ctx->stream));
+    *launches += 1;
+    slr::BoxSource src = frontier;
+    src.index = b.list;
+    src.index_count = list_n;
+    src.cap = cap;
+    return optimise_slopes(ctx, src, cap, list_n, b, ctx->opt.alpha_steps, ctx->opt.alpha_lr, nullptr, ctx->cls,
+                           list_n + 1, false, launches);
+}
+
+extern "C" {
+
+int slr_alpha_width(slr_ctx *ctx, int64_t *H) {
+    if (!ctx || !H) return fail(ctx, SLR_EINVAL, "null argument");
+    if (!ctx->has_net) return fail(ctx, SLR_ESTATE, "network must be set");
+    int64_t h = 0;
+    for (int k = 1; k < ctx->K; ++k) h += ctx->widths[k];
+    *H = h;
+    return SLR_OK;
+}
+
+int slr_margin_backward(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, const float *alpha,
+                        const float *g_lo, const float *g_hi, float *row_lo, float *row_hi, float *d_alpha,
+                        float *d_box_lo, float *d_box_hi, float *const *d_W, float *const *d_b, int on_device) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!ctx->has_net || !ctx->has_prop) return fail(ctx, SLR_ESTATE, "network and property must be set");
+    if (n < 0 || (n > 0 && (!box_lo || !box_hi || !g_lo || !g_hi))) return fail(ctx, SLR_EINVAL, "bad arguments");
+    if ((row_lo == nullptr) != (row_hi == nullptr)) return fail(ctx, SLR_EINVAL, "row_lo and row_hi go together");
+    if ((d_box_lo == nullptr) != (d_box_hi == nullptr))
+        return fail(ctx, SLR_EINVAL, "d_box_lo and d_box_hi go together");
+    const int K = ctx->K;
+    bool want_w = d_W != nullptr || d_b != nullptr;
+    if (want_w) {
+        if (!d_W || !d_b) return fail(ctx, SLR_EINVAL, "d_W and d_b go together");
+        for (int k = 0; k < K; ++k)
+            if (!d_W[k] || !d_b[k]) return fail(ctx, SLR_EINVAL, "d_W[%d] or d_b[%d] is NULL", k, k);
+    }
+    CK(ctx, cudaSetDevice(ctx->device));
+    int rc = prepare_device(ctx);
+    if (rc) return rc;
+    if ((rc = check_adjoint(ctx))) return rc;
+    const int d = ctx->widths[0];
+    const int R = (int)ctx->e.size();
+    const int64_t H = ctx->H;
+    size_t wsz = 0;
+    std::vector<size_t> woff(K), boff(K);
+    for (int k = 0; k < K; ++k) {
+        woff[k] = wsz;
+        wsz += align_up((size_t)ctx->widths[k + 1] * ctx->widths[k] * sizeof(float));
+        boff[k] = wsz;
+        wsz += align_up((size_t)ctx->widths[k + 1] * sizeof(float));
+    }
+    // device views: inputs, outputs and the weight-gradient accumulators
+    const size_t s_box = align_up((size_t)n * d * sizeof(float)), s_al = align_up((size_t)n * H * sizeof(float));
+    const size_t s_row = align_up((size_t)n * R * sizeof(float));
+    const size_t need = on_device ? 0 : 4 * s_box + 2 * s_al + 4 * s_row + (want_w ? wsz : 0);
+    if (!on_device && n > 0 && (rc = check_boxes(ctx, n, d, box_lo, box_hi))) return rc;
+    if (need && (rc = ensure_scratch(ctx, need))) return rc;
+    unsigned char *p = (unsigned char *)ctx->scratch;
+    auto take = [&](size_t bytes) {
+        unsigned char *q = p;
+        p += bytes;
+        return q;
+    };
+    const float *dlo = box_lo, *dhi = box_hi, *dal = alpha, *dgl = g_lo, *dgh = g_hi;
+    float *drl = row_lo, *drh = row_hi, *dda = d_alpha, *ddl = d_box_lo, *ddh = d_box_hi;
+    float *dW[slr::kMaxLayers] = {}, *db[slr::kMaxLayers] = {};
+    if (!on_device) {
+        float *t0 = (float *)take(s_box), *t1 = (float *)take(s_box);
+        float *t2 = (float *)take(s_al), *t3 = (float *)take(s_row), *t4 = (float *)take(s_row);
+        drl = row_lo ? (float *)take(s_row) : nullptr;
+        drh = row_lo ? (float *)take(s_row) : nullptr;
+        dda = d_alpha ? (float *)take(s_al) : nullptr;
+        ddl = d_box_lo ? (float *)take(s_box) : nullptr;
+        ddh = d_box_lo ? (float *)take(s_box) : nullptr;
+        if (n > 0) {
+            CK(ctx, cudaMemcpyAsync(t0, box_lo, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            CK(ctx, cudaMemcpyAsync(t1, box_hi, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            if (alpha)
+                CK(ctx, cudaMemcpyAsync(t2, alpha, (size_t)n * H * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            CK(ctx, cudaMemcpyAsync(t3, g_lo, (size_t)n * R * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            CK(ctx, cudaMemcpyAsync(t4, g_hi, (size_t)n * R * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        }
+        dlo = t0;
+        dhi = t1;
+        dal = alpha ? t2 : nullptr;
+        dgl = t3;
+        dgh = t4;
+        if (want_w) {
+            unsigned char *wbase = take(wsz);
+            for (int k = 0; k < K; ++k) {
+                dW[k] = (float *)(wbase + woff[k]);
+                db[k] = (float *)(wbase + boff[k]);
+            }
+            CK(ctx, cudaMemsetAsync(wbase, 0, wsz, ctx->stream));
+        }
+    } else if (want_w) {
+        for (int k = 0; k < K; ++k) {
+            dW[k] = d_W[k];
+            db[k] = d_b[k];
+            CK(ctx, cudaMemsetAsync(dW[k], 0, (size_t)ctx->widths[k + 1] * ctx->widths[k] * sizeof(float), ctx->stream));
+            CK(ctx, cudaMemsetAsync(db[k], 0, (size_t)ctx->widths[k + 1] * sizeof(float), ctx->stream));
+        }
+    }
+    if (n > 0) {
+        slr::AdjArgs a = adj_base(ctx);
+        a.src.mode = 1;
+        a.src.n_explicit = n;
+        a.src.lo = dlo;
+        a.src.hi = dhi;
+        a.src.cap = n;
+        a.n = n;
+        a.alpha_mode = alpha ? slr::kAlphaFree : slr::kAlphaDefault;
+        a.alpha = const_cast<float *>(dal);
+        a.g_lo = dgl;
+        a.g_hi = dgh;
+        a.row_lo = drl;
+        a.row_hi = drh;
+        a.d_alpha = dda;
+        a.d_lo = ddl;
+        a.d_hi = ddh;
+        for (int k = 0; k < K; ++k) {
+            a.dW[k] = dW[k];
+            a.db[k] = db[k];
+        }
+        const int grid = (int)std::min<int64_t>(n, ctx->adj_grid);
+        CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+    }
+    if (!on_device) {
+        auto back = [&](float *host, const float *dev, size_t count) -> int {
+            if (host && count) CK(ctx, cudaMemcpyAsync(host, dev, count * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+            return SLR_OK;
+        };
+        if ((rc = back(row_lo, drl, (size_t)n * R)) || (rc = back(row_hi, drh, (size_t)n * R)) ||
+            (rc = back(d_alpha, dda, (size_t)n * H)) || (rc = back(d_box_lo, ddl, (size_t)n * d)) ||
+            (rc = back(d_box_hi, ddh, (size_t)n * d)))
+            return rc;
+        if (want_w) {
+            for (int k = 0; k < K; ++k) {
+                if ((rc = back(d_W[k], dW[k], (size_t)ctx->widths[k + 1] * ctx->widths[k])) ||
+                    (rc = back(d_b[k], db[k], (size_t)ctx->widths[k + 1])))
+                    return rc;
+            }
+        }
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SLR_OK;
+}
+
+int slr_optimize_alpha(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, int steps, float lr,
+                       float *alpha, float *row_lo, float *row_hi, uint8_t *cls, int on_device) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!ctx->has_net || !ctx->has_prop) return fail(ctx, SLR_ESTATE, "network and property must be set");
+    if (n < 0 || (n > 0 && (!box_lo || !box_hi))) return fail(ctx, SLR_EINVAL, "bad box arguments");
+    if ((row_lo == nullptr) != (row_hi == nullptr)) return fail(ctx, SLR_EINVAL, "row_lo and row_hi go together");
+    if (steps < 0 || steps > 1000) return fail(ctx, SLR_EINVAL, "steps %d out of range [0, 1000]", steps);
+    if (!(lr > 0.f) || !std::isfinite(lr)) return fail(ctx, SLR_EINVAL, "lr must be finite and positive");
+    if (n == 0) return SLR_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    int rc = prepare_device(ctx);
+    if (rc) return rc;
+    if ((rc = check_adjoint(ctx))) return rc;
+    const int d = ctx->widths[0];
+    const int R = (int)ctx->e.size();
+    const int64_t H = ctx->H;
+    const size_t s_box = align_up((size_t)n * d * sizeof(float));
+    const size_t need = alpha_bytes(n, H, R) + align_up((size_t)n) + (on_device ? 0 : 2 * s_box);
+    if (!on_device && (rc = check_boxes(ctx, n, d, box_lo, box_hi))) return rc;
+    if ((rc = ensure_scratch(ctx, need))) return rc;
+    if (!ctx->status) {
+        CK(ctx, cudaMalloc(&ctx->status, sizeof(unsigned int)));
+        CK(ctx, cudaMallocHost(&ctx->h_status, sizeof(unsigned int)));
+    }
+    CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
+    unsigned char *p = (unsigned char *)ctx->scratch;
+    const AlphaBuffers b = carve_alpha(p, n, H, R);
+    p += alpha_bytes(n, H, R);
+    uint8_t *dcls = (uint8_t *)p;
+    p += align_up((size_t)n);
+    const float *dlo = box_lo, *dhi = box_hi;
+    if (!on_device) {
+        float *t0 = (float *)p, *t1 = (float *)(p + s_box);
+        CK(ctx, cudaMemcpyAsync(t0, box_lo, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(t1, box_hi, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        dlo = t0;
+        dhi = t1;
+    }
+    slr::BoxSource src{};
+    src.mode = 1;
+    src.n_explicit = n;
+    src.lo = dlo;
+    src.hi = dhi;
+    src.cap = n;
+    int64_t launches = 0;
+    if ((rc = optimise_slopes(ctx, src, n, nullptr, b, steps, lr, dcls, nullptr, nullptr, alpha != nullptr,
+                              &launches)))
+        return rc;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (row_lo) {
+        CK(ctx, cudaMemcpyAsync(row_lo, b.lo_best, (size_t)n * R * sizeof(float), kind, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(row_hi, b.hi_best, (size_t)n * R * sizeof(float), kind, ctx->stream));
+    }
+    if (cls) CK(ctx, cudaMemcpyAsync(cls, dcls, (size_t)n, kind, ctx->stream));
+    if (alpha) CK(ctx, cudaMemcpyAsync(alpha, b.alpha, (size_t)n * H * sizeof(float), kind, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SLR_OK;
+}
+
+}  // extern "C"

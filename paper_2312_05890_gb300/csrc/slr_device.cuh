@@ -138,6 +138,11 @@ struct BoxSource {
     const double *root_lo;            // float64 root box
     const double *root_w;             // float64 root widths
     int64_t cap;                      // upper bound on n (buffer capacity)
+    // optional lower ReLU slopes (Eq. 1 lower line, any value in [0, 1] is
+    // sound): the box at position k (before indirection) reads row
+    // alpha[k * alpha_ld + ...], one entry per hidden neuron, layers in order
+    const float *alpha;
+    int64_t alpha_ld;
 };
 
 struct EvalOutputs {
@@ -150,6 +155,7 @@ struct EvalOutputs {
     int64_t near_cap;
     unsigned long long *tie_count;  // FP64 pass: boxes whose class still depends on E
     unsigned int *status;
+    int by_position;              // cls/row outputs at the position in the source, not at the index
 };
 
 struct LevelCounters {

@@ -358,7 +358,8 @@ struct EvalTile {
     // ---- one hidden layer: constant, error, concrete bounds, ReLU relaxation ----
     template <class L>
     static __device__ void hidden_epilogue(const L &lay, const Real *sConst, const NetParams<Real> &net, int layer,
-                                           Real gcoef) {
+                                           Real gcoef, const float *alpha = nullptr, int64_t alpha_ld = 0,
+                                           int64_t base = 0, int64_t n = 0, int alpha_off = 0) {
         const int d = net.d;
         const int nrows = net.n[layer];
         const int n_in = net.n[layer - 1];
@@ -417,7 +418,17 @@ struct EvalTile {
                     sig_u = sig_u < (Real)1 ? sig_u : (Real)1;
                     h = A::mul_rn(sig_u, -bd.lu);
                 }
-                sig_l = bd.ul <= (Real)0 ? (Real)0 : A::div_rn(bd.ul, bd.ul - bd.ll);
+                if (bd.ul <= (Real)0) {
+                    sig_l = 0;
+                } else if (alpha != nullptr) {
+                    // a supplied slope, clamped to [0, 1] (NaN -> 0)
+                    // padding slots of the last tile repeat the tile's first box
+                    const int64_t pos = base + b < n ? base + b : base;
+                    const float a = alpha[pos * alpha_ld + alpha_off + p];
+                    sig_l = (Real)fminf(fmaxf(a, 0.f), 1.f);
+                } else {
+                    sig_l = A::div_rn(bd.ul, bd.ul - bd.ll);
+                }
             }
             sig_l = sig_l < (Real)0 ? (Real)0 : (sig_l > (Real)1 ? (Real)1 : sig_l);
             // (C, R) <- ((U' + L') / 2, (U' - L') / 2)
@@ -699,8 +710,11 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
     Tile::init_layer(lay, net, sMh, sMl, sR);
     __syncthreads();
 
+    int alpha_off = 0;
     for (int k = 1; k < net.K; ++k) {
-        Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]));
+        Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
+                              alpha_off);
+        alpha_off += net.n[k];
         const int n_out = net.n[k + 1];
         const int Mpad = (n_out + 7) & ~7;
         Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
@@ -720,15 +734,16 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         const uint8_t opt = classify_rows<Real, T>(net, sLo, sHi, sErr, b, (Real)2);
         const bool near = (cls == kUndecided) && (opt != kUndecided);
         const int64_t idx = sIdx[b];
-        if (out.cls != nullptr) out.cls[idx] = cls;
+        const int64_t oidx = out.by_position ? base + b : idx;
+        if (out.cls != nullptr) out.cls[oidx] = cls;
         if (out.row_lo != nullptr) {
             for (int r = 0; r < R; ++r) {
-                out.row_lo[idx * R + r] = to_lo<Real>(sLo[r * T + b]);
-                out.row_hi[idx * R + r] = to_hi<Real>(sHi[r * T + b]);
+                out.row_lo[oidx * R + r] = to_lo<Real>(sLo[r * T + b]);
+                out.row_hi[oidx * R + r] = to_hi<Real>(sHi[r * T + b]);
             }
         }
         if (out.row_err != nullptr) {
-            for (int r = 0; r < R; ++r) out.row_err[idx * R + r] = to_hi<Real>(sErr[r * T + b]);
+            for (int r = 0; r < R; ++r) out.row_err[oidx * R + r] = to_hi<Real>(sErr[r * T + b]);
         }
         if (near) {
             if (pass == 0 && out.near_list != nullptr) {

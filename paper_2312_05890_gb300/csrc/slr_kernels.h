@@ -49,6 +49,43 @@ cudaError_t launch_compact_batch(const CompactArgs *args, int P, int t, unsigned
                                  cudaStream_t s);
 cudaError_t launch_init_batch(const CompactArgs *args, int P, cudaStream_t s);
 
+// Adjoint of the SLR pass (gradients of a linear loss of the row bounds) and
+// projected Adam on the lower ReLU slopes; one box per CTA.
+enum { kAlphaDefault = 0, kAlphaFree = 1, kAlphaInit = 2 };
+struct AdjArgs {
+    NetParams<float> net;
+    BoxSource src;                  // boxes at positions 0..n-1
+    int64_t n;                      // positions (an upper bound when `count` is set)
+    const unsigned long long *count;  // optional device count of positions
+    int64_t H;                      // hidden neurons (row length of the slope arrays)
+    int n_max;                      // widest layer n[1..K]
+    int nck;                        // hidden layers whose equations stay in shared memory
+    int alpha_mode;                 // kAlphaDefault: u/(u-l), differentiated through; kAlphaFree: read;
+                                    // kAlphaInit: write u/(u-l) to alpha, then treat it as free
+    float *alpha;                   // n x H
+    const float *g_lo, *g_hi;       // n x R upstream adjoints; null: in-kernel decision loss
+    int8_t *dir;                    // decision loss direction per position (1 safe, 2 unsafe)
+    float *row_lo, *row_hi;         // optional: the float32 row bounds (not widened)
+    float *d_alpha;                 // optional n x H
+    float *d_lo, *d_hi;             // optional n x d
+    float *dW[kMaxLayers];          // optional, accumulated: network layout n[k+1] x n[k], last unfolded
+    float *db[kMaxLayers];
+    const float *Cprop;             // property rows (R x n_out) for unfolding the last layer
+    int n_out;
+    int adam_t;                     // > 0: take Adam step t on the slopes
+    float *adam_m, *adam_v;         // n x H
+    float lr, beta1, beta2, eps, beta1_t, beta2_t;
+};
+size_t adjoint_smem_bytes(const AdjArgs &a);
+int adjoint_blocks_per_sm(size_t smem);
+cudaError_t launch_adjoint(const AdjArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_merge_bounds(const NetParams<float> &net, int64_t n, const unsigned long long *count,
+                                const float *lo_new, const float *hi_new, float *lo_best, float *hi_best,
+                                uint8_t *cls_pos, uint8_t *cls_idx, const int64_t *index, int first,
+                                unsigned long long *decided, cudaStream_t s);
+cudaError_t launch_gather_undecided(const uint8_t *cls, const unsigned long long *n, int64_t cap, int64_t *list,
+                                    unsigned long long *list_n, int64_t list_cap, int grid, cudaStream_t s);
+
 cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s);
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,

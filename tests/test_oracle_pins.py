@@ -207,3 +207,17 @@ def test_box_gradient_of_an_affine_network_closed_form():
     np.testing.assert_allclose(g["hi"], (wd + np.abs(wd)) / 2, atol=1e-7)
     # weight gradient: d hi / d w_j = m_j + sign(w_j) r_j
     np.testing.assert_allclose(g["W"][0][0], (lo + hi) / 2 + np.sign(wd) * (hi - lo) / 2, atol=1e-7)
+
+
+def test_default_slope_box_gradient_closed_form():
+    """x -> relu(x) on [l, u], l < 0 < u: lo = u l / (u - l) (slope u/(u-l) on L = x), hi = u (chord)."""
+    from workloads.generators import Network
+    net = Network([np.array([[1.0]], np.float32), np.array([[1.0]], np.float32)],
+                  [np.zeros(1, np.float32), np.zeros(1, np.float32)])
+    l, u = -0.75, 1.25
+    g = oracle.fd_gradients(net, np.array([l]), np.array([u]), None, None, np.array([0.0]), np.array([1.0]))
+    np.testing.assert_allclose(g["lo"], [u * u / (u - l) ** 2], atol=1e-7)
+    np.testing.assert_allclose(g["hi"], [-l * l / (u - l) ** 2], atol=1e-7)
+    g = oracle.fd_gradients(net, np.array([l]), np.array([u]), None, None, np.array([1.0]), np.array([0.0]))
+    np.testing.assert_allclose(g["lo"], [0.0], atol=1e-7)
+    np.testing.assert_allclose(g["hi"], [1.0], atol=1e-7)
