@@ -183,6 +183,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (MB)")
+    ap.add_argument("--alpha-steps", type=int, default=0,
+                    help="projected-Adam steps on the lower ReLU slopes of each level's undecided boxes")
+    ap.add_argument("--alpha-lr", type=float, default=0.1)
+    ap.add_argument("--tile", default="",
+                    help="boxes x threads per CTA of the FP32 evaluation kernel, e.g. 16x256 (default: timed choice)")
+    ap.add_argument("--alpha-cap", type=int, default=1 << 20,
+                    help="most undecided boxes per level whose slopes are optimised")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -199,6 +206,8 @@ def main():
     workload = f"{p.name} D={D} seed={args.seed}"
     config = {"workload": workload, "widths": p.net.widths, "depth": D, "rows": p.prop.R,
               "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}"}
+    if args.alpha_steps:
+        config["slopes"] = f"{args.alpha_steps} projected-Adam steps (lr {args.alpha_lr}) per undecided box"
 
     if args.impl == "reference":
         if rank != 0:
@@ -239,7 +248,18 @@ def main():
     flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device="cuda")
     c = pkg.Counter(local_rank)
     c.set_problem(p)
-    c.set_options(profile=1)
+    tile = {}
+    if args.tile:
+        tb, tt = (int(x) for x in args.tile.lower().split("x"))
+        tile = {"tile_boxes": tb, "tile_threads": tt}
+    fixed = None
+    if args.alpha_steps:
+        c.set_options(**tile)
+        fixed = c.count(D)      # the fixed-slope count, for the comparison below
+        c.set_options(profile=1, alpha_steps=args.alpha_steps, alpha_lr=args.alpha_lr, alpha_cap=args.alpha_cap,
+                      **tile)
+    else:
+        c.set_options(profile=1, **tile)
     for _ in range(args.warmup):
         c.count(D)
 
@@ -250,6 +270,7 @@ def main():
     t_wall = time.perf_counter()
     dev_ms, boxes, kern = [], 0, [0.0, 0.0, 0.0]
     launches = 0
+    alpha_ms = 0.0
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -259,6 +280,7 @@ def main():
         launches += r["launches"]
         for i in range(3):
             kern[i] += r["kernel_ms"][i]
+        alpha_ms += r["alpha_ms"]
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t_wall
@@ -311,7 +333,7 @@ def main():
                "sample": f"levels 0..{lv - 1} of the same count, {cb} boxes, {cs:.1f} s, one process per core"}
 
     if rank == 0:
-        print(json.dumps({
+        line = {
             "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -325,7 +347,15 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks,
-        }))
+        }
+        if fixed is not None:
+            line["slope_opt"] = {
+                "alpha_boxes": last["alpha_boxes"], "alpha_decided": last["alpha_decided"],
+                "alpha_ms_per_step": alpha_ms / args.steps,
+                "fixed_slopes": {"unsafe_lo": fixed["unsafe_lo"], "unsafe_hi": fixed["unsafe_hi"],
+                                 "boxes": fixed["boxes"], "device_ms": fixed["device_ms"],
+                                 "boxes_per_s": fixed["boxes"] / (fixed["device_ms"] / 1e3)}}
+        print(json.dumps(line))
     c.close()
     if dist is not None:
         dist.destroy_process_group()

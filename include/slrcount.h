@@ -79,6 +79,9 @@ typedef struct {
     float alpha_lr;         /* Adam step size of those steps; default 0.1 */
     int64_t alpha_cap;      /* most UNDECIDED boxes per level whose slopes are optimised
                                (the rest keep fixed slopes); default 1<<16 */
+    int32_t tile_boxes;     /* FP32 evaluation kernel: boxes per CTA (64, 32, 16, 8 or 4) and */
+    int32_t tile_threads;   /* threads per CTA (256 or 128); 0, 0 = chosen by timing (default).
+                               A pair the network cannot run with gives SLR_EUNSUPPORTED. */
 } slr_options;
 
 #define SLR_MAX_LEVELS 63

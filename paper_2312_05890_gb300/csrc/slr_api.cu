@@ -280,7 +280,8 @@ std::vector<TileChoice> tile_candidates(const slr::NetParams<Real> &p) {
             c.smem = slr::eval_smem_bytes<Real>(T, p.d, p.R, p.n_max_pad, p.n_in_max);
             if (c.smem > (size_t)kMaxSmem) continue;
             if (slr::eval_gemm_items(T, p.d, p.n_max_pad) > 2 * NT) continue;
-            c.blocks = sizeof(Real) == 4 ? slr::eval_blocks_per_sm_f32(T, NT, c.smem)
+            c.blocks = sizeof(Real) == 4 ? slr::eval_blocks_per_sm_f32(T, NT, c.smem,
+                                                                       slr::eval_gemm_items(T, p.d, p.n_max_pad))
                                          : slr::eval_blocks_per_sm_f64(T, NT, c.smem);
             if (c.blocks <= 0) continue;
             out.push_back(c);
@@ -511,7 +512,17 @@ int prepare_device(slr_ctx *ctx) {
         return fail(ctx, SLR_EUNSUPPORTED, "network too large for the fused FP32 kernel (d=%d, widest=%d)",
                     ctx->nf.d, ctx->nf.n_max_pad);
     TileChoice best = c32[0];
-    if (c32.size() > 1) {
+    if (ctx->opt.tile_boxes > 0) {
+        bool found = false;
+        for (const TileChoice &c : c32)
+            if (c.T == ctx->opt.tile_boxes && c.NT == ctx->opt.tile_threads) {
+                best = c;
+                found = true;
+            }
+        if (!found)
+            return fail(ctx, SLR_EUNSUPPORTED, "tile %d x %d is not available for this network", ctx->opt.tile_boxes,
+                        ctx->opt.tile_threads);
+    } else if (c32.size() > 1) {
         if ((rc = autotune(ctx, c32, best))) return rc;
     }
     ctx->T32 = best.T;
@@ -704,6 +715,8 @@ void slr_default_options(slr_options *opt) {
     opt->alpha_steps = 0;
     opt->alpha_lr = 0.1f;
     opt->alpha_cap = (int64_t)1 << 16;
+    opt->tile_boxes = 0;
+    opt->tile_threads = 0;
 }
 
 int slr_create(slr_ctx **out, int device, void *cuda_stream) {
@@ -792,7 +805,11 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
         if (opt->relax_mode != SLR_RELAX_NEURIFY)
             return fail(ctx, SLR_EUNSUPPORTED, "slope optimisation needs relax mode NEURIFY");
     }
-    if (opt->relax_mode != ctx->opt.relax_mode || opt->precision != ctx->opt.precision) ctx->dev_dirty = true;
+    if ((opt->tile_boxes == 0) != (opt->tile_threads == 0))
+        return fail(ctx, SLR_EINVAL, "tile_boxes and tile_threads are set together");
+    if (opt->relax_mode != ctx->opt.relax_mode || opt->precision != ctx->opt.precision ||
+        opt->tile_boxes != ctx->opt.tile_boxes || opt->tile_threads != ctx->opt.tile_threads)
+        ctx->dev_dirty = true;
     ctx->opt = *opt;
     return SLR_OK;
 }

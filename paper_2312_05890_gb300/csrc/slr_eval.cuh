@@ -173,7 +173,7 @@ struct RowBounds {
     }
 };
 
-template <typename Real, int T, int NT>
+template <typename Real, int T, int NT, int KI = 2>
 struct EvalTile {
     using A = Arith<Real>;
     // FP32 carries the constants as compensated pairs; FP64 is precise enough
@@ -270,14 +270,20 @@ struct EvalTile {
     template <class L>
     static __device__ void const_phase(const L &lay, Real *sConst, const Real *sW, int Mpad,
                                        const NetParams<Real> &net, int layer) {
+        const int pairs = (net.n[layer + 1] + 1) / 2;
+        for (int item = threadIdx.x; item < pairs * T; item += NT) const_item(lay, sConst, sW, Mpad, net, layer, item);
+    }
+
+    template <class L>
+    static __device__ __forceinline__ void const_item(const L &lay, Real *sConst, const Real *sW, int Mpad,
+                                                      const NetParams<Real> &net, int layer, int item) {
         const int d = net.d;
         const int n_in = net.n[layer];
         const int n_out = net.n[layer + 1];
         const bool last = layer + 1 == net.K;
         const Real *bias = net.b[layer];
         const int nmp = net.n_max_pad;
-        const int pairs = (n_out + 1) / 2;
-        for (int item = threadIdx.x; item < pairs * T; item += NT) {
+        {
             const int q = item / T;
             const int b = item - q * T;
             const int p0 = 2 * q;
@@ -460,11 +466,11 @@ struct EvalTile {
     }
 
     // ---- C' = W C, R' = |W| R over the coefficient, N and E columns ---------------
-    // The constant of C is not part of this product: const_phase computes it
+    // The constant of C is not part of this product: const_item computes it
     // with error-free transformations.  The state is updated in place: every
     // thread first accumulates its (at most kItems) 8 x 4 tiles in registers,
     // then, after a barrier, overwrites the rows.
-    static constexpr int kItems = 2;
+    static constexpr int kItems = KI;
 
     static __device__ __forceinline__ void tile_mac(const Real *wp, const Real *xp, int n_in, int Mpad, int NS,
                                                     bool is_abs, Real (&acc)[8][4]) {
@@ -507,11 +513,17 @@ struct EvalTile {
         }
     }
 
-    static __device__ void contract(Real *S, const Real *sW, int n_in, int Mpad, int d, int NS) {
+    // The next layer's constants (n_const items of const_item) share the phase:
+    // they fill the threads that hold fewer product tiles, and they read the
+    // state before the barrier like the tiles do.
+    template <class L>
+    static __device__ void contract(const L &lay, Real *sConst, const NetParams<Real> &net, int layer, Real *S,
+                                    const Real *sW, int n_in, int Mpad, int d, int NS) {
         const int QW = d * T / 4;             // quads of C coefficient columns
         const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
         const int Q = QW + QA;
         const int total = (Mpad / 8) * Q;
+        const int n_const = ((net.n[layer + 1] + 1) / 2) * T;
         Real acc[kItems][8][4];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
@@ -523,6 +535,12 @@ struct EvalTile {
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
                 tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
             }
+        }
+        // combined index space [0, total + n_const): indices past `total` are constants
+        {
+            int idx = threadIdx.x + ((total - (int)threadIdx.x + NT - 1) / NT) * NT;
+            if (idx < total) idx += NT;
+            for (; idx < total + n_const; idx += NT) const_item(lay, sConst, sW, Mpad, net, layer, idx - total);
         }
         __syncthreads();
 #pragma unroll
@@ -656,11 +674,11 @@ __device__ __forceinline__ int64_t source_count(const BoxSource &src) {
 // pass 1: re-check of such a list in the higher precision (writes the class,
 //         counts the boxes still depending on E as ties).
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int NT>
+template <typename Real, int T, int NT, int KI = 2>
 __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, const EvalOutputs &out, const int pass,
                           const TileSmem<Real> &sm, const int64_t base, const int64_t n) {
     using A = Arith<Real>;
-    using Tile = EvalTile<Real, T, NT>;
+    using Tile = EvalTile<Real, T, NT, KI>;
     const int d = net.d;
     const int R = net.R;
     const int NS = T * state_cols(d);
@@ -719,8 +737,8 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         const int Mpad = (n_out + 7) & ~7;
         Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
         __syncthreads();
-        Tile::const_phase(lay, sConst, sW, Mpad, net, k);
-        Tile::contract(sS, sW, net.n[k], Mpad, d, NS);   // barrier inside, then in-place store
+        // constants and products; barrier inside, then the in-place store
+        Tile::contract(lay, sConst, net, k, sS, sW, net.n[k], Mpad, d, NS);
         __syncthreads();
     }
     Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
@@ -764,14 +782,22 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
 // ---------------------------------------------------------------------------
 // The kernel: persistent over tiles of one problem's boxes.
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? 2 : 1)
+// Resident CTAs per SM the register budget is sized for: two with two product
+// tiles per thread; with one tile per thread (small T) three CTAs of 256 or
+// six of 128 threads.
+template <typename Real, int NT, int KI>
+constexpr int eval_min_blocks() {
+    return sizeof(Real) != 4 ? 1 : (KI == 2 ? 2 : (NT == 256 ? 3 : 6));
+}
+
+template <typename Real, int T, int NT, int KI = 2>
+__global__ void __launch_bounds__(NT, (eval_min_blocks<Real, NT, KI>()))
 slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutputs out, const int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileSmem<Real> sm = carve_smem<Real, T>(smem_raw, net.n_max_pad, net.d, net.n_in_max, net.R);
     const int64_t n = source_count(src);
     for (int64_t base = (int64_t)blockIdx.x * T; base < n; base += (int64_t)gridDim.x * T)
-        eval_tile<Real, T, NT>(net, src, out, pass, sm, base, n);
+        eval_tile<Real, T, NT, KI>(net, src, out, pass, sm, base, n);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,37 +4,44 @@
 
 namespace slr {
 
-template <int T, int NT>
+template <int T, int NT, int KI>
 static cudaError_t launch_t(int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass) {
-    auto k = slr_eval_kernel<float, T, NT>;
+    auto k = slr_eval_kernel<float, T, NT, KI>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, s>>>(net, src, out, pass);
     return cudaGetLastError();
 }
 
-template <int T, int NT>
+template <int T, int NT, int KI>
 static int occ_t(size_t smem) {
-    auto k = slr_eval_kernel<float, T, NT>;
+    auto k = slr_eval_kernel<float, T, NT, KI>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, smem) != cudaSuccess) return 0;
     return nb;
 }
 
-#define SLR_DISPATCH(NT_, CALL)          \
-    switch (T) {                          \
-        case 64: return CALL<64, NT_>(grid, smem, s, net, src, out, pass);    \
-        case 32: return CALL<32, NT_>(grid, smem, s, net, src, out, pass);    \
-        case 16: return CALL<16, NT_>(grid, smem, s, net, src, out, pass);    \
-        case 8: return CALL<8, NT_>(grid, smem, s, net, src, out, pass);      \
-        case 4: return CALL<4, NT_>(grid, smem, s, net, src, out, pass);      \
-        default: break;                   \
+// Tiles of 8 or fewer boxes whose product tiles fit one per thread run the
+// one-tile-per-thread instantiation (fewer registers, more resident CTAs).
+static int items_per_thread(int T, int NT, int items) { return (T <= 8 && items <= NT) ? 1 : 2; }
+
+#define SLR_DISPATCH(NT_, CALL)                                                                \
+    switch (T * 10 + KI) {                                                                     \
+        case 642: return CALL<64, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
+        case 322: return CALL<32, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
+        case 162: return CALL<16, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
+        case 82: return CALL<8, NT_, 2>(grid, smem, s, net, src, out, pass);                   \
+        case 81: return CALL<8, NT_, 1>(grid, smem, s, net, src, out, pass);                   \
+        case 42: return CALL<4, NT_, 2>(grid, smem, s, net, src, out, pass);                   \
+        case 41: return CALL<4, NT_, 1>(grid, smem, s, net, src, out, pass);                   \
+        default: break;                                                                        \
     }
 
 cudaError_t launch_eval_f32(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass) {
+    const int KI = items_per_thread(T, NT, eval_gemm_items(T, net.d, net.n_max_pad));
     if (NT == 256) {
         SLR_DISPATCH(256, launch_t)
     } else if (NT == 128) {
@@ -43,22 +50,26 @@ cudaError_t launch_eval_f32(int T, int NT, int grid, size_t smem, cudaStream_t s
     return cudaErrorInvalidValue;
 }
 
-int eval_blocks_per_sm_f32(int T, int NT, size_t smem) {
-    switch (NT * 100 + T) {
-        case 25664: return occ_t<64, 256>(smem);
-        case 25632: return occ_t<32, 256>(smem);
-        case 25616: return occ_t<16, 256>(smem);
-        case 25608: return occ_t<8, 256>(smem);
-        case 25604: return occ_t<4, 256>(smem);
-        case 12864: return occ_t<64, 128>(smem);
-        case 12832: return occ_t<32, 128>(smem);
-        case 12816: return occ_t<16, 128>(smem);
-        case 12808: return occ_t<8, 128>(smem);
-        case 12804: return occ_t<4, 128>(smem);
+int eval_blocks_per_sm_f32(int T, int NT, size_t smem, int items) {
+    const int KI = items_per_thread(T, NT, items);
+    switch (NT * 1000 + T * 10 + KI) {
+        case 256642: return occ_t<64, 256, 2>(smem);
+        case 256322: return occ_t<32, 256, 2>(smem);
+        case 256162: return occ_t<16, 256, 2>(smem);
+        case 256082: return occ_t<8, 256, 2>(smem);
+        case 256081: return occ_t<8, 256, 1>(smem);
+        case 256042: return occ_t<4, 256, 2>(smem);
+        case 256041: return occ_t<4, 256, 1>(smem);
+        case 128642: return occ_t<64, 128, 2>(smem);
+        case 128322: return occ_t<32, 128, 2>(smem);
+        case 128162: return occ_t<16, 128, 2>(smem);
+        case 128082: return occ_t<8, 128, 2>(smem);
+        case 128081: return occ_t<8, 128, 1>(smem);
+        case 128042: return occ_t<4, 128, 2>(smem);
+        case 128041: return occ_t<4, 128, 1>(smem);
         default: return 0;
     }
 }
-
 
 template <int T>
 static cudaError_t launch_batch_t(int grid, size_t smem, cudaStream_t s, const NetParams<float> *nets,

@@ -18,8 +18,10 @@ cudaError_t launch_eval_f32(int T, int NT, int grid, size_t smem, cudaStream_t s
                             const BoxSource &src, const EvalOutputs &out, int pass);
 cudaError_t launch_eval_f64(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass);
-// Resident CTAs per SM of the evaluation kernel at tile size T, NT threads and this smem.
-int eval_blocks_per_sm_f32(int T, int NT, size_t smem);
+// Resident CTAs per SM of the evaluation kernel at tile size T, NT threads and
+// this smem; `items` = eval_gemm_items of the network (selects the
+// one-product-tile-per-thread instantiation where it fits).
+int eval_blocks_per_sm_f32(int T, int NT, size_t smem, int items);
 int eval_blocks_per_sm_f64(int T, int NT, size_t smem);
 
 // Tensor-core evaluation (FP32 state, split-TF32 contraction on tcgen05).
