@@ -179,6 +179,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="acas")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--depth", type=int, default=0, help="depth cap (default: the workload's)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
@@ -202,7 +203,7 @@ def main():
         return bench_batch(args, world, rank, local_rank)
     # weak scaling: rank r counts its own problem of the same shape (seed + r)
     p = gen.make(args.workload, args.seed + rank)
-    D = p.depth
+    D = args.depth or p.depth
     workload = f"{p.name} D={D} seed={args.seed}"
     config = {"workload": workload, "widths": p.net.widths, "depth": D, "rows": p.prop.R,
               "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}"}

@@ -82,6 +82,11 @@ typedef struct {
     int32_t tile_boxes;     /* FP32 evaluation kernel: boxes per CTA (64, 32, 16, 8 or 4) and */
     int32_t tile_threads;   /* threads per CTA (256 or 128); 0, 0 = chosen by timing (default).
                                A pair the network cannot run with gives SLR_EUNSUPPORTED. */
+    int32_t wide;           /* 1: always use the wide path (per-box state in GPU memory, each
+                               layer one tensor-core product, no FP64 re-check); 0 (default):
+                               only for networks whose per-box state does not fit the fused
+                               shared-memory kernel */
+    int32_t reserved2;      /* must be 0 */
 } slr_options;
 
 #define SLR_MAX_LEVELS 63

@@ -92,6 +92,15 @@ struct slr_ctx {
     void *alpha_buf = nullptr;            // slope optimisation during a count
     size_t alpha_buf_bytes = 0;
     unsigned long long *alpha_ctr = nullptr;  // per level: undecided list length, then decided
+    bool wide = false;                    // per-box state in HBM, one tensor-core product per layer
+    int wide_NP = 0, wide_Bc = 0;
+    void *wide_img = nullptr;             // TF32 pieces of W and |W| per layer
+    const float *w_hi[slr::kMaxLayers] = {}, *w_lo[slr::kMaxLayers] = {};
+    const float *wa_hi[slr::kMaxLayers] = {}, *wa_lo[slr::kMaxLayers] = {};
+    const float *w0t = nullptr;           // layer 1 transposed (d x n_1)
+    int w_Kpad[slr::kMaxLayers] = {};
+    void *wide_buf = nullptr;             // chunk state
+    size_t wide_buf_bytes = 0;
 
     int64_t cap = 0, near_cap = 0;
     uint64_t *codes[2] = {nullptr, nullptr};
@@ -477,6 +486,150 @@ int autotune(slr_ctx *ctx, const std::vector<TileChoice> &cands, TileChoice &bes
     return SLR_OK;
 }
 
+// Wide path: TF32 pieces of W and |W| of every layer k >= 1 (the last one
+// folded with the property), zero padded to multiples of 128 rows and 32
+// columns, and the chunk size for the per-box state.
+int build_wide(slr_ctx *ctx, const HostLayers<float> &L) {
+    const slr::NetParams<float> &nf = ctx->nf;
+    const int K = nf.K;
+    const int d = nf.d;
+    int np = 32;
+    for (int k = 1; k <= K; ++k) np = std::max(np, (nf.n[k] + 31) & ~31);
+    ctx->wide_NP = np;
+    std::vector<size_t> offs(K, 0);
+    size_t total = align_up((size_t)d * nf.n[1] * sizeof(float));   // W_1 transposed first
+    for (int k = 1; k < K; ++k) {
+        const int Mpad = (nf.n[k + 1] + 127) & ~127, Kpad = (nf.n[k] + 31) & ~31;
+        ctx->w_Kpad[k] = Kpad;
+        offs[k] = total;
+        total += 4 * align_up((size_t)Mpad * Kpad * sizeof(float));
+    }
+    if (ctx->wide_img) cudaFree(ctx->wide_img);
+    ctx->wide_img = nullptr;
+    {
+        std::vector<unsigned char> host(total, 0);
+        float *w0t = (float *)host.data();
+        for (int p = 0; p < nf.n[1]; ++p)
+            for (int j = 0; j < d; ++j) w0t[(size_t)j * nf.n[1] + p] = L.W[0][(size_t)p * d + j];
+        for (int k = 1; k < K; ++k) {
+            const int n_in = nf.n[k], n_out = nf.n[k + 1];
+            const int Mpad = (n_out + 127) & ~127, Kpad = ctx->w_Kpad[k];
+            const size_t one = align_up((size_t)Mpad * Kpad * sizeof(float));
+            float *hi = (float *)(host.data() + offs[k]);
+            float *lo = (float *)(host.data() + offs[k] + one);
+            float *ahi = (float *)(host.data() + offs[k] + 2 * one);
+            float *alo = (float *)(host.data() + offs[k] + 3 * one);
+            for (int p = 0; p < n_out; ++p) {
+                for (int i = 0; i < n_in; ++i) {
+                    const float v = L.W[k][(size_t)i * n_out + p];   // transposed float weights
+                    const float h = tf32_host(v);
+                    const float l = tf32_host(v - h);
+                    const size_t o = (size_t)p * Kpad + i;
+                    hi[o] = h;
+                    lo[o] = l;
+                    ahi[o] = std::fabs(h);
+                    alo[o] = v >= 0.f ? l : -l;
+                }
+            }
+        }
+        CK(ctx, cudaMalloc(&ctx->wide_img, total));
+        CK(ctx, cudaMemcpy(ctx->wide_img, host.data(), total, cudaMemcpyHostToDevice));
+        ctx->h2d_pending += (int64_t)total;
+        ctx->w0t = (const float *)ctx->wide_img;
+        for (int k = 1; k < K; ++k) {
+            const int Mpad = (nf.n[k + 1] + 127) & ~127;
+            const size_t one = align_up((size_t)Mpad * ctx->w_Kpad[k] * sizeof(float));
+            const unsigned char *b = (const unsigned char *)ctx->wide_img + offs[k];
+            ctx->w_hi[k] = (const float *)b;
+            ctx->w_lo[k] = (const float *)(b + one);
+            ctx->wa_hi[k] = (const float *)(b + 2 * one);
+            ctx->wa_lo[k] = (const float *)(b + 3 * one);
+        }
+    }
+    // chunk: the boxes whose state fits about 3 GB
+    const int R = nf.R;
+    const size_t per_box = sizeof(float) * ((size_t)np * (2 * (size_t)d + 2 * (size_t)(d + 3) + 5) + 3 * (size_t)d +
+                                            3 * (size_t)R) + sizeof(int64_t) + 64;
+    int64_t bc = (int64_t)(((size_t)3 << 30) / per_box);
+    bc = std::max<int64_t>(1, std::min<int64_t>(bc, 8192));
+    while (bc > 1 && (int64_t)bc * (d + 3) > ((int64_t)1 << 30)) bc /= 2;
+    ctx->wide_Bc = (int)bc;
+    return SLR_OK;
+}
+
+int ensure_wide_buf(slr_ctx *ctx) {
+    const int d = ctx->nf.d, np = ctx->wide_NP, R = ctx->nf.R;
+    const size_t bc = (size_t)ctx->wide_Bc;
+    const size_t need = 2 * align_up(bc * d * np * 4) + 2 * align_up(bc * (d + 3) * np * 4) + 5 * align_up(bc * np * 4) +
+                        3 * align_up(bc * d * 4) + 3 * align_up(bc * R * 4) + align_up(bc * 8);
+    if (ctx->wide_buf_bytes >= need) return SLR_OK;
+    cudaFree(ctx->wide_buf);
+    ctx->wide_buf = nullptr;
+    ctx->wide_buf_bytes = 0;
+    CK(ctx, cudaMalloc(&ctx->wide_buf, need));
+    CK(ctx, cudaMemsetAsync(ctx->wide_buf, 0, need, ctx->stream));
+    ctx->wide_buf_bytes = need;
+    return SLR_OK;
+}
+
+// Bound positions [0, n) of `src` on the wide path, chunk by chunk.
+int run_wide(slr_ctx *ctx, const slr::BoxSource &src, int64_t n, const slr::EvalOutputs &out, int64_t *launches) {
+    int rc = ensure_wide_buf(ctx);
+    if (rc) return rc;
+    const slr::NetParams<float> &nf = ctx->nf;
+    const int K = nf.K, d = nf.d, np = ctx->wide_NP, R = nf.R, sms = ctx->sm_count;
+    const size_t bc = (size_t)ctx->wide_Bc;
+    unsigned char *p = (unsigned char *)ctx->wide_buf;
+    auto take = [&](size_t bytes) {
+        float *q = (float *)p;
+        p += align_up(bytes);
+        return q;
+    };
+    float *Cb[2] = {take(bc * d * np * 4), take(bc * d * np * 4)};
+    float *Rb[2] = {take(bc * (d + 3) * np * 4), take(bc * (d + 3) * np * 4)};
+    float *Ch = take(bc * np * 4), *Cl = take(bc * np * 4);
+    float *Kh = take(bc * np * 4), *Kl = take(bc * np * 4), *Ke = take(bc * np * 4);
+    float *mh = take(bc * d * 4), *ml = take(bc * d * 4), *rr = take(bc * d * 4);
+    float *lo = take(bc * R * 4), *hi = take(bc * R * 4), *er = take(bc * R * 4);
+    int64_t *bidx = (int64_t *)take(bc * 8);
+    for (int64_t base = 0; base < n; base += (int64_t)bc) {
+        const int nb = (int)std::min<int64_t>((int64_t)bc, n - base);
+        CK(ctx, slr::launch_wide_box(src, base, nb, d, mh, ml, rr, bidx, sms, ctx->stream));
+        int cur = 0;
+        CK(ctx, slr::launch_wide_init(nf, ctx->w0t, nb, np, mh, ml, rr, Cb[cur], Rb[cur], Ch, Cl, ctx->stream));
+        *launches += 2;
+        for (int k = 1; k < K; ++k) {
+            const int nxt = cur ^ 1;
+            slr::WideGemmArgs ga{};
+            ga.status = out.status;
+            ga.g[0] = slr::WideGemm{ctx->w_hi[k], ctx->w_lo[k], Cb[cur], Cb[nxt], nf.n[k + 1], nf.n[k], ctx->w_Kpad[k],
+                                    nb * d, np, np};
+            ga.g[1] = slr::WideGemm{ctx->wa_hi[k], ctx->wa_lo[k], Rb[cur], Rb[nxt], nf.n[k + 1], nf.n[k],
+                                    ctx->w_Kpad[k], nb * (d + 3), np, np};
+            CK(ctx, slr::launch_wide_gemm(ga, 2, ctx->stream));
+            CK(ctx, slr::launch_wide_const(nf, k, nb, np, Ch, Cl, Rb[cur], Kh, Kl, Ke, sms, ctx->stream));
+            const float g = slr::tc_gamma(ctx->w_Kpad[k]);
+            if (k + 1 < K) {
+                CK(ctx, slr::launch_wide_hidden(nf, k + 1, nb, np, g, Cb[nxt], Rb[nxt], Ch, Cl, Kh, Kl, Ke,
+                                                ctx->stream));
+            } else {
+                CK(ctx, slr::launch_wide_final(nf, nb, np, g, Cb[nxt], Rb[nxt], Ch, Cl, Kh, Kl, Ke, lo, hi, er,
+                                               ctx->stream));
+            }
+            *launches += 3;
+            cur = nxt;
+        }
+        if (K == 1) {
+            CK(ctx, slr::launch_wide_final(nf, nb, np, 0.f, Cb[cur], Rb[cur], Ch, Cl, Kh, Kl, Ke, lo, hi, er,
+                                           ctx->stream));
+            *launches += 1;
+        }
+        CK(ctx, slr::launch_wide_classify(nf, nb, base, lo, hi, er, bidx, out, sms, ctx->stream));
+        *launches += 1;
+    }
+    return SLR_OK;
+}
+
 int prepare_device(slr_ctx *ctx) {
     if (!ctx->dev_dirty) return SLR_OK;
     if (ctx->widths.back() != (int)(ctx->C.size() / std::max<size_t>(1, ctx->e.size())))
@@ -508,9 +661,18 @@ int prepare_device(slr_ctx *ctx) {
     ctx->h2d_pending += (int64_t)bytes;
     (void)rc;
     const std::vector<TileChoice> c32 = tile_candidates(ctx->nf);
-    if (c32.empty())
-        return fail(ctx, SLR_EUNSUPPORTED, "network too large for the fused FP32 kernel (d=%d, widest=%d)",
-                    ctx->nf.d, ctx->nf.n_max_pad);
+    ctx->wide = ctx->opt.wide != 0 || c32.empty();
+    if (ctx->wide) {
+        if ((rc = build_wide(ctx, Lf))) return rc;
+        ctx->T32 = ctx->NT32 = 0;
+        ctx->T64 = 0;
+        ctx->tc_ok = false;
+        ctx->H = 0;
+        for (int k = 1; k < ctx->K; ++k) ctx->H += ctx->widths[k];
+        ctx->adj_grid = 0;
+        ctx->dev_dirty = false;
+        return SLR_OK;
+    }
     TileChoice best = c32[0];
     if (ctx->opt.tile_boxes > 0) {
         bool found = false;
@@ -671,6 +833,7 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
         return fail(ctx, SLR_ESTATE,
                     "slr_count_noalloc needs the network and property on the device: call slr_count (or "
                     "slr_bounds with n >= 1) once after setting them");
+    if (ctx->wide) return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc does not run the wide path");
     v->device = ctx->device;
     v->stream = ctx->stream;
     v->d = ctx->widths[0];
@@ -717,6 +880,8 @@ void slr_default_options(slr_options *opt) {
     opt->alpha_cap = (int64_t)1 << 16;
     opt->tile_boxes = 0;
     opt->tile_threads = 0;
+    opt->wide = 0;
+    opt->reserved2 = 0;
 }
 
 int slr_create(slr_ctx **out, int device, void *cuda_stream) {
@@ -766,6 +931,8 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->scratch);
     cudaFree(ctx->alpha_buf);
     cudaFree(ctx->alpha_ctr);
+    cudaFree(ctx->wide_img);
+    cudaFree(ctx->wide_buf);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -805,10 +972,13 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
         if (opt->relax_mode != SLR_RELAX_NEURIFY)
             return fail(ctx, SLR_EUNSUPPORTED, "slope optimisation needs relax mode NEURIFY");
     }
+    if (opt->reserved2 != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
+    if (opt->wide != 0 && opt->wide != 1) return fail(ctx, SLR_EINVAL, "wide must be 0 or 1");
     if ((opt->tile_boxes == 0) != (opt->tile_threads == 0))
         return fail(ctx, SLR_EINVAL, "tile_boxes and tile_threads are set together");
     if (opt->relax_mode != ctx->opt.relax_mode || opt->precision != ctx->opt.precision ||
-        opt->tile_boxes != ctx->opt.tile_boxes || opt->tile_threads != ctx->opt.tile_threads)
+        opt->tile_boxes != ctx->opt.tile_boxes || opt->tile_threads != ctx->opt.tile_threads ||
+        opt->wide != ctx->opt.wide)
         ctx->dev_dirty = true;
     ctx->opt = *opt;
     return SLR_OK;
@@ -926,7 +1096,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     CK(ctx, slr::launch_init_count(ctx->codes[0], ctx->ctr, ctx->stream));
 
     const bool leaves = ctx->opt.record_leaves != 0;
-    const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0;
+    const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0 && !ctx->wide;
     const bool slopes = ctx->opt.alpha_steps > 0;
     if (slopes) {
         if ((rc = check_adjoint(ctx))) return rc;
@@ -967,7 +1137,19 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         o.tie_count = &ctx->ctr->ties;
         o.status = ctx->status;
         CK(ctx, mark(t, 0));
-        if (use_tc) {
+        if (ctx->wide) {
+            // the chunk loop needs the level's size on the host
+            CK(ctx, cudaMemcpyAsync(&ctx->h_ctr->frontier_n[t], &ctx->ctr->frontier_n[t], sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            const int64_t nt = std::min<int64_t>((int64_t)ctx->h_ctr->frontier_n[t], ctx->cap);
+            slr::EvalOutputs ow{};
+            ow.cls = ctx->cls;
+            ow.tie_count = &ctx->ctr->ties;
+            ow.status = ctx->status;
+            if ((rc = run_wide(ctx, src, nt, ow, &launches))) return rc;
+            CK(ctx, mark(t, 1));
+        } else if (use_tc) {
             // tier 1 on the tensor cores; boxes whose class depends on its
             // widening are re-bounded by the FP32 path (tier 2), and those whose
             // class still depends on the FP32 widening in FP64 (tier 3)
@@ -1061,8 +1243,8 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     out->device_ms = ms;
     out->launches = launches;
     out->h2d_bytes = h2d;
-    out->tile_boxes = ctx->T32;
-    out->tile_threads = ctx->NT32;
+    out->tile_boxes = ctx->wide ? ctx->wide_Bc : ctx->T32;
+    out->tile_threads = ctx->wide ? 0 : ctx->NT32;
     out->d2h_bytes = (int64_t)(sizeof(slr::LevelCounters) + sizeof(unsigned int) + (slopes ? sizeof h_alpha : 0));
     if (slopes) {
         const int64_t acap = std::min<int64_t>(ctx->opt.alpha_cap, ctx->cap);
@@ -1161,7 +1343,11 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
     }
     o.status = ctx->status;
     CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
-    if (ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok && alpha == nullptr) {
+    if (ctx->wide) {
+        if (alpha) return fail(ctx, SLR_EUNSUPPORTED, "supplied slopes are not available on the wide path");
+        int64_t launches = 0;
+        if ((rc = run_wide(ctx, src, n, o, &launches))) return rc;
+    } else if (ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok && alpha == nullptr) {
         const int64_t tiles = (n + ctx->T_tc - 1) / ctx->T_tc;
         const int grid = (int)std::min<int64_t>(tiles, ctx->grid_tc);
         CK(ctx, slr::launch_eval_tc(ctx->T_tc, grid, ctx->smem_tc, ctx->stream, ctx->nf, ctx->tcp, src, o, 0));

@@ -141,36 +141,65 @@ struct SimtLayout {
 };
 
 // Concrete bounds of the raw equations U = C + R, L = C - R of one row over
-// the box (Sec. 2.2: const +- sum_j |coeff_j| in the normalised input), with
-// outward rounding so that they bound the stored equations exactly.
+// the box (Sec. 2.2: const +- sum_j |coeff_j| in the normalised input), summed
+// in round-to-nearest; `delta` bounds how far each of the four lies from the
+// exact bound of the stored equations (callers add it to the row's E), and the
+// magnitudes NC, NR round upward.
 template <typename Real>
 struct RowBounds {
     Real uu, lu, ul, ll;   // max U, min U, max L, min L
     Real NC, NR;           // sum |C_j| over coefficients, sum |R_j| incl. its constant
+    Real delta;            // rounding of uu, lu, ul, ll
+    Real SU, SL;           // sum |C_j + R_j|, sum |C_j - R_j|
+    __device__ __forceinline__ void reset() {
+        SU = SL = NC = NR = 0;
+    }
+    __device__ __forceinline__ void add(Real c, Real r) {
+        using A = Arith<Real>;
+        SU = SU + A::abs(c + r);
+        SL = SL + A::abs(c - r);
+        NC = A::add_up(NC, A::abs(c));
+        NR = A::add_up(NR, A::abs(r));
+    }
+    // partial sums over disjoint coefficient sets (any order: delta covers it)
+    __device__ __forceinline__ void merge(const RowBounds &o) {
+        using A = Arith<Real>;
+        SU = SU + o.SU;
+        SL = SL + o.SL;
+        NC = A::add_up(NC, o.NC);
+        NR = A::add_up(NR, o.NR);
+    }
+    __device__ __forceinline__ void finish(int d, Real chi, Real clo, Real rd) {
+        using A = Arith<Real>;
+        NR = A::add_up(NR, A::abs(rd));
+        const Real cu = (chi + rd) + clo;
+        const Real cl = (chi - rd) + clo;
+        uu = cu + SU;
+        lu = cu - SU;
+        ul = cl + SL;
+        ll = cl - SL;
+        // each of the d + 3 roundings (the terms c +- r, the running sums, the
+        // constant and the final sum) is at most u times a partial magnitude
+        const Real g = gam<Real>(d + 4);
+        const Real mag = A::add_up(A::add_up(SU, SL), A::add_up(A::add_up(A::abs(chi), A::abs(rd)), A::abs(clo)));
+        delta = A::mul_up(g, A::mul_up(mag, (Real)1 + g));
+    }
     template <class Row>
     __device__ __forceinline__ void compute(const Row &R, int d, Real chi, Real clo) {
-        using A = Arith<Real>;
-        Real SU = 0, SL = 0;
-        NC = 0;
-        NR = 0;
-        for (int j = 0; j < d; ++j) {
-            const Real c = R(j);
-            const Real r = R(d + 1 + j);
-            SU = A::add_up(SU, A::abs(c + r));
-            SL = A::add_up(SL, A::abs(c - r));
-            NC = A::add_up(NC, A::abs(c));
-            NR = A::add_up(NR, A::abs(r));
-        }
-        const Real rd = R(2 * d + 1);
-        NR = A::add_up(NR, A::abs(rd));
-        // |c +- r| <= |fl(c +- r)| (1 + u): cover the round-to-nearest of each term
-        SU = A::mul_up(SU, (Real)1 + A::ulp2);
-        SL = A::mul_up(SL, (Real)1 + A::ulp2);
-        uu = A::add_up(A::add_up(A::add_up(chi, rd), clo), SU);
-        lu = A::add_dn(A::add_dn(A::add_dn(chi, rd), clo), -SU);
-        ul = A::add_up(A::add_up(A::add_up(chi, -rd), clo), SL);
-        ll = A::add_dn(A::add_dn(A::add_dn(chi, -rd), clo), -SL);
+        reset();
+        for (int j = 0; j < d; ++j) add(R(j), R(d + 1 + j));
+        finish(d, chi, clo, R(2 * d + 1));
     }
+};
+
+// What the ReLU relaxation (Eq. 1) does to one row: keep it (active), zero it
+// (inactive) or map every coefficient pair (c, r) to (pp c + qq r, qq c + pp r)
+// (unstable), and the row's new constant, radius constant, N and E.
+template <typename Real>
+struct RelaxPlan {
+    int kind;              // 0 active, 1 inactive, 2 unstable
+    Real pp, qq;
+    Real nh, nl, rd, E, N;
 };
 
 template <typename Real, int T, int NT, int KI = 2>
@@ -361,6 +390,123 @@ struct EvalTile {
         E = A::add_up(A::mul_up(R(cE(d)), (Real)1 + (Real)2 * gcoef), eps);
     }
 
+    // ---- ReLU relaxation (Eq. 1) of one hidden row from its concrete bounds ---------
+    // chi, clo: the row's constant (float-float); rd: its radius constant; E: its
+    // error bound including bd.delta.  a_ptr: the supplied lower slope of the
+    // row, or null for u_l / (u_l - l_l).
+    static __device__ __forceinline__ RelaxPlan<Real> plan_row(const RowBounds<Real> &bd, int d, int relax_mode,
+                                                               Real chi, Real clo, Real rd, Real E,
+                                                               const float *a_ptr) {
+        RelaxPlan<Real> pl;
+        if (bd.ll >= (Real)0) {
+            // stable active: relu is the identity on [L - E, U + E] up to
+            // U + E >= lu + E >= 0, so the equations and E carry over
+            pl.kind = 0;
+            pl.pp = 1;
+            pl.qq = 0;
+            pl.nh = chi;
+            pl.nl = clo;
+            pl.rd = rd;
+            pl.N = A::add_up(bd.NC, bd.NR);
+            pl.E = E;
+            return pl;
+        }
+        if (bd.uu <= (Real)0) {
+            // stable inactive: relu(z) lies in [0, max(0, uu + E)]
+            pl.kind = 1;
+            pl.pp = 0;
+            pl.qq = 0;
+            pl.nh = 0;
+            pl.nl = 0;
+            pl.rd = 0;
+            pl.N = 0;
+            const Real top = A::add_up(bd.uu, E);
+            pl.E = top > (Real)0 ? top : (Real)0;
+            return pl;
+        }
+        // unstable: U' = sig_u (U - l) and L' = sig_l L (Eq. 1).  Applied to
+        // U + E over [lu + E, uu + E] the chord misses relu by (1 - sig_u) E
+        // and shifts by sig_u E, and sig_l (L - E) <= relu(L - E): E carries over.
+        Real sig_u, sig_l, h;
+        if (relax_mode == kRelaxPaperLiteral) {
+            sig_u = A::div_up(bd.uu, A::add_dn(bd.uu, -bd.ll));
+            sig_u = sig_u < (Real)1 ? sig_u : (Real)1;
+            h = A::mul_rn(sig_u, -bd.ll);
+            sig_l = A::div_rn(bd.uu, bd.uu - bd.ll);
+        } else {
+            if (bd.lu >= (Real)0) {
+                sig_u = 1;
+                h = 0;
+            } else {
+                sig_u = A::div_up(bd.uu, A::add_dn(bd.uu, -bd.lu));
+                sig_u = sig_u < (Real)1 ? sig_u : (Real)1;
+                h = A::mul_rn(sig_u, -bd.lu);
+            }
+            if (bd.ul <= (Real)0) {
+                sig_l = 0;
+            } else if (a_ptr != nullptr) {
+                // a supplied slope, clamped to [0, 1] (NaN -> 0)
+                sig_l = (Real)fminf(fmaxf(*a_ptr, 0.f), 1.f);
+            } else {
+                sig_l = A::div_rn(bd.ul, bd.ul - bd.ll);
+            }
+        }
+        sig_l = sig_l < (Real)0 ? (Real)0 : (sig_l > (Real)1 ? (Real)1 : sig_l);
+        // (C, R) <- ((U' + L') / 2, (U' - L') / 2)
+        pl.kind = 2;
+        pl.pp = (sig_u + sig_l) * (Real)0.5;
+        pl.qq = (sig_u - sig_l) * (Real)0.5;
+        const Real hh = h * (Real)0.5;
+        Real ph, pe;
+        two_prod<Real>(pl.pp, chi, ph, pe);
+        const Real rest = pe + A::fma_rn(pl.pp, clo, A::fma_rn(pl.qq, rd, hh));
+        two_sum<Real>(ph, rest, pl.nh, pl.nl);
+        pl.rd = A::fma_rn(pl.qq, chi, A::fma_rn(pl.qq, clo, A::fma_rn(pl.pp, rd, hh)));
+        const Real sig_max = sig_u > sig_l ? sig_u : sig_l;
+        const Real tot = A::add_up(A::add_up(bd.NC, bd.NR), A::add_up(A::abs(chi), A::abs(clo)));
+        const Real mag = A::add_up(A::mul_up(sig_max, tot), h);
+        const Real err = A::add_up(A::mul_up((Real)8 * A::ulp2, mag), (Real)(2 * d + 8) * A::tiny);
+        pl.E = A::add_up(E, err);
+        pl.N = A::mul_up(A::add_up(mag, A::add_up(err, err)), (Real)1 + (Real)4 * A::ulp2);
+        return pl;
+    }
+
+    // one coefficient pair of a row under the plan
+    static __device__ __forceinline__ void apply_plan(const RelaxPlan<Real> &pl, Real &c, Real &r) {
+        if (pl.kind == 1) {
+            c = 0;
+            r = 0;
+        } else if (pl.kind == 2) {
+            const Real c0 = c, r0 = r;
+            c = A::fma_rn(pl.pp, c0, pl.qq * r0);
+            r = A::fma_rn(pl.qq, c0, pl.pp * r0);
+        }
+    }
+
+    // ---- bounds and ReLU relaxation of one hidden row, in place ----------------------
+    template <class Row>
+    static __device__ __forceinline__ void relax_row(const Row &R, int d, int relax_mode, Real chi, Real clo, Real E,
+                                                     const float *a_ptr) {
+        const int cr = cR(d);
+        RowBounds<Real> bd;
+        bd.compute(R, d, chi, clo);
+        E = A::add_up(E, bd.delta);
+        const RelaxPlan<Real> pl = plan_row(bd, d, relax_mode, chi, clo, R(cr + d), E, a_ptr);
+        if (pl.kind != 0) {
+            for (int j = 0; j < d; ++j) {
+                Real c = R(j), r = R(cr + j);
+                apply_plan(pl, c, r);
+                R(j) = c;
+                R(cr + j) = r;
+            }
+        }
+        R(cCh(d)) = pl.nh;
+        R(cCl(d)) = pl.nl;
+        R(cr + d) = pl.rd;
+        R(cN(d)) = pl.N;
+        R(cE(d)) = pl.E;
+    }
+
     // ---- one hidden layer: constant, error, concrete bounds, ReLU relaxation ----
     template <class L>
     static __device__ void hidden_epilogue(const L &lay, const Real *sConst, const NetParams<Real> &net, int layer,
@@ -373,7 +519,6 @@ struct EvalTile {
             const int p = item / T;
             const int b = item - p * T;
             const auto R = lay.row(p, b);
-            const int cr = cR(d);
             Real chi, clo, E;
             if (layer > 1) {
                 finish_contraction(R, sConst, net.n_max_pad, p, b, d, n_in, gcoef, chi, clo, E);
@@ -382,85 +527,13 @@ struct EvalTile {
                 clo = R(cCl(d));
                 E = R(cE(d));
             }
-            RowBounds<Real> bd;
-            bd.compute(R, d, chi, clo);
-            if (bd.ll >= (Real)0) {
-                // stable active: relu is the identity on [L - E, U + E] up to
-                // U + E >= lu + E >= 0, so the equations and E carry over
-                R(cCh(d)) = chi;
-                R(cCl(d)) = clo;
-                R(cN(d)) = A::add_up(bd.NC, bd.NR);
-                R(cE(d)) = E;
-                lay.finish_row(p, b);
-                continue;
+            const float *a_ptr = nullptr;
+            if (alpha != nullptr) {
+                // padding slots of the last tile repeat the tile's first box
+                const int64_t pos = base + b < n ? base + b : base;
+                a_ptr = alpha + pos * alpha_ld + alpha_off + p;
             }
-            if (bd.uu <= (Real)0) {
-                // stable inactive: relu(z) lies in [0, max(0, uu + E)]
-                for (int j = 0; j < d; ++j) R(j) = 0;
-                for (int j = 0; j <= d; ++j) R(cr + j) = 0;
-                R(cCh(d)) = 0;
-                R(cCl(d)) = 0;
-                R(cN(d)) = 0;
-                const Real top = A::add_up(bd.uu, E);
-                R(cE(d)) = top > (Real)0 ? top : (Real)0;
-                lay.finish_row(p, b);
-                continue;
-            }
-            // unstable: U' = sig_u (U - l) and L' = sig_l L (Eq. 1).  Applied to
-            // U + E over [lu + E, uu + E] the chord misses relu by (1 - sig_u) E
-            // and shifts by sig_u E, and sig_l (L - E) <= relu(L - E): E carries over.
-            Real sig_u, sig_l, h;
-            if (net.relax_mode == kRelaxPaperLiteral) {
-                sig_u = A::div_up(bd.uu, A::add_dn(bd.uu, -bd.ll));
-                sig_u = sig_u < (Real)1 ? sig_u : (Real)1;
-                h = A::mul_rn(sig_u, -bd.ll);
-                sig_l = A::div_rn(bd.uu, bd.uu - bd.ll);
-            } else {
-                if (bd.lu >= (Real)0) {
-                    sig_u = 1;
-                    h = 0;
-                } else {
-                    sig_u = A::div_up(bd.uu, A::add_dn(bd.uu, -bd.lu));
-                    sig_u = sig_u < (Real)1 ? sig_u : (Real)1;
-                    h = A::mul_rn(sig_u, -bd.lu);
-                }
-                if (bd.ul <= (Real)0) {
-                    sig_l = 0;
-                } else if (alpha != nullptr) {
-                    // a supplied slope, clamped to [0, 1] (NaN -> 0)
-                    // padding slots of the last tile repeat the tile's first box
-                    const int64_t pos = base + b < n ? base + b : base;
-                    const float a = alpha[pos * alpha_ld + alpha_off + p];
-                    sig_l = (Real)fminf(fmaxf(a, 0.f), 1.f);
-                } else {
-                    sig_l = A::div_rn(bd.ul, bd.ul - bd.ll);
-                }
-            }
-            sig_l = sig_l < (Real)0 ? (Real)0 : (sig_l > (Real)1 ? (Real)1 : sig_l);
-            // (C, R) <- ((U' + L') / 2, (U' - L') / 2)
-            const Real pp = (sig_u + sig_l) * (Real)0.5;
-            const Real qq = (sig_u - sig_l) * (Real)0.5;
-            for (int j = 0; j < d; ++j) {
-                const Real c = R(j);
-                const Real r = R(cr + j);
-                R(j) = A::fma_rn(pp, c, qq * r);
-                R(cr + j) = A::fma_rn(qq, c, pp * r);
-            }
-            const Real rd = R(cr + d);
-            const Real hh = h * (Real)0.5;
-            Real ph, pe, nh, nl;
-            two_prod<Real>(pp, chi, ph, pe);
-            const Real rest = pe + A::fma_rn(pp, clo, A::fma_rn(qq, rd, hh));
-            two_sum<Real>(ph, rest, nh, nl);
-            R(cCh(d)) = nh;
-            R(cCl(d)) = nl;
-            R(cr + d) = A::fma_rn(qq, chi, A::fma_rn(qq, clo, A::fma_rn(pp, rd, hh)));
-            const Real sig_max = sig_u > sig_l ? sig_u : sig_l;
-            const Real tot = A::add_up(A::add_up(bd.NC, bd.NR), A::add_up(A::abs(chi), A::abs(clo)));
-            const Real mag = A::add_up(A::mul_up(sig_max, tot), h);
-            const Real err = A::add_up(A::mul_up((Real)8 * A::ulp2, mag), (Real)(2 * d + 8) * A::tiny);
-            R(cE(d)) = A::add_up(E, err);
-            R(cN(d)) = A::mul_up(A::add_up(mag, A::add_up(err, err)), (Real)1 + (Real)4 * A::ulp2);
+            relax_row(R, d, net.relax_mode, chi, clo, E, a_ptr);
             lay.finish_row(p, b);
         }
     }
@@ -586,6 +659,7 @@ struct EvalTile {
             }
             RowBounds<Real> bd;
             bd.compute(Rw, d, chi, clo);
+            E = A::add_up(E, bd.delta);
             sLo[r * T + b] = A::add_dn(bd.ll, -E);
             sHi[r * T + b] = A::add_up(bd.uu, E);
             sErr[r * T + b] = E;

@@ -26,47 +26,15 @@
 // SBO = (K / 4) 144 between 8-row groups.
 #include "slr_eval.cuh"
 #include "slr_kernels.h"
+#include "slr_tc_util.cuh"
 
 namespace slr {
+
+using namespace tc;
 
 namespace {
 
 constexpr int kTcThreads = 256;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version; no swizzle, base offset 0
-    return d;
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-    return __uint_as_float(t);
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after `limit` polls (the caller then reports
-// kStatusTimeout and stops using the tensor core).
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, int limit) {
-    for (int it = 0; it < limit; ++it)
-        if (mbar_try_wait(addr, parity)) return true;
-    return false;
-}
 
 __device__ __forceinline__ int boff(int n, int k, int sbo) {
     return (n >> 3) * sbo + (k >> 2) * kTcLbo + (n & 7) * 16 + (k & 3) * 4;

@@ -88,6 +88,34 @@ cudaError_t launch_merge_bounds(const NetParams<float> &net, int64_t n, const un
 cudaError_t launch_gather_undecided(const uint8_t *cls, const unsigned long long *n, int64_t cap, int64_t *list,
                                     unsigned long long *list_n, int64_t list_cap, int grid, cudaStream_t s);
 
+// Wide networks: per-box state in HBM, one tensor-core product per layer.
+struct WideGemm {
+    const float *Ahi, *Alo;   // TF32 pieces of W (or |W|), Mpad x Kpad row-major, zero padded
+    const float *B;           // column col, element k at B[col * ldb + k] (k < K)
+    float *D;                 // D[col * ldd + m] for m < M
+    int M, K, Kpad, ncols, ldb, ldd;
+};
+struct WideGemmArgs {
+    WideGemm g[2];
+    unsigned int *status;
+};
+size_t wide_gemm_smem_bytes();
+cudaError_t launch_wide_gemm(const WideGemmArgs &args, int nprob, cudaStream_t s);
+cudaError_t launch_wide_box(const BoxSource &src, int64_t base, int nb, int d, float *mh, float *ml, float *rr,
+                            int64_t *bidx, int sms, cudaStream_t s);
+cudaError_t launch_wide_init(const NetParams<float> &net, const float *W0t, int nb, int NP, const float *mh,
+                             const float *ml, const float *rr, float *C, float *Rr, float *Ch, float *Cl, cudaStream_t s);
+cudaError_t launch_wide_const(const NetParams<float> &net, int k, int nb, int NP, const float *Ch, const float *Cl,
+                              const float *Rr, float *Kh, float *Kl, float *Ke, int sms, cudaStream_t s);
+cudaError_t launch_wide_hidden(const NetParams<float> &net, int layer, int nb, int NP, float gcoef, float *C, float *Rr,
+                               float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke, cudaStream_t s);
+cudaError_t launch_wide_final(const NetParams<float> &net, int nb, int NP, float gcoef, float *C, float *Rr, float *Ch,
+                              float *Cl, const float *Kh, const float *Kl, const float *Ke, float *lo, float *hi,
+                              float *err, cudaStream_t s);
+cudaError_t launch_wide_classify(const NetParams<float> &net, int nb, int64_t base, const float *lo, const float *hi,
+                                 const float *err, const int64_t *bidx, const EvalOutputs &out, int sms,
+                                 cudaStream_t s);
+
 cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t s);
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,

@@ -1,0 +1,625 @@
+// Wide networks: the SLR state of a chunk of boxes lives in HBM and every
+// affine layer is one batched GEMM on the tensor cores.
+//
+// For networks whose per-box state does not fit a shared-memory tile (many
+// inputs, wide layers: Sec. 3 notes that SLR's memory grows with the number of
+// input nodes), each box keeps, per neuron p of the current layer,
+//   C[b][j][p]  j < d        centre-equation coefficients (normalised input),
+//   Rr[b][j][p] j < d + 3    radius coefficients, radius constant, N (row
+//                            magnitude) and E (rounding-error bound),
+//   Ch[b][p], Cl[b][p]       centre constant as a float-float pair,
+// with neurons the fastest index (row stride NP, a multiple of 32).  Each
+// column (b, j) is then a K-major operand of the next layer's product
+//   C' = W C   (M = n_out, K = n_in, N = boxes x d columns),
+//   R' = |W| R (N = boxes x (d + 3) columns, R, N and E together),
+// computed by `wide_gemm_kernel` with tcgen05 (kind::tf32) in three-term split
+// precision: x = hi + lo in TF32 pieces, products lo*hi + hi*lo + hi*hi
+// accumulated in FP32 in tensor memory, covered in E by gamma_tc(K) of
+// sum |W| N like the tile kernel's tensor-core path.  The constants (one
+// column) take the float-float route on the CUDA cores (`wide_const_kernel`),
+// and `wide_hidden_kernel` applies the error update, the concrete bounds and
+// the ReLU relaxation (Eq. 1) row by row in place, with the same code as the
+// tile kernel (EvalTile::relax_row).
+#include <algorithm>
+
+#include "slr_eval.cuh"
+#include "slr_kernels.h"
+#include "slr_tc_util.cuh"
+
+namespace slr {
+
+using namespace tc;
+
+namespace {
+
+using WTile = EvalTile<float, 1, 1>;   // only its static row helpers are used
+
+constexpr int kWN = 256;                          // GEMM tile: columns
+constexpr int kWM = 128;                          // rows (tensor-memory lanes)
+constexpr int kWK = 32;                           // K per pipeline stage
+constexpr int kWSbo = (kWK / 4) * kTcLbo;         // bytes between 8-row core-matrix groups
+constexpr int kWABytes = (kWM / 8) * kWSbo;       // one A piece of a stage
+constexpr int kWBBytes = (kWN / 8) * kWSbo;       // one B piece of a stage
+constexpr int kWStage = 2 * kWABytes + 2 * kWBBytes;
+constexpr int kWThreads = 256;
+
+// One row (box b, neuron p) of the HBM state, with the tile kernel's column numbering.
+struct WideRow {
+    float *C, *Rr, *Ch, *Cl;
+    int64_t b;
+    int p, d, NP;
+    __device__ __forceinline__ float &operator()(int c) const {
+        if (c < d) return C[((size_t)b * d + c) * NP + p];
+        if (c == d) return Ch[(size_t)b * NP + p];
+        if (c == 2 * d + 4) return Cl[(size_t)b * NP + p];
+        return Rr[((size_t)b * (d + 3) + (c - d - 1)) * NP + p];
+    }
+};
+
+__device__ __forceinline__ int wboff(int r, int k) { return (r >> 3) * kWSbo + (k >> 2) * kTcLbo + (r & 7) * 16; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Boxes of the chunk: centre (float-float) and radius, outward (Sec. 2.2).
+// ---------------------------------------------------------------------------
+__global__ void wide_box_kernel(const BoxSource src, int64_t base, int nb, int d, float *mh, float *ml, float *rr,
+                                int64_t *bidx) {
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < (int64_t)nb * d;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(item / d);
+        const int i = (int)(item - (int64_t)b * d);
+        const int64_t k = base + b;
+        const int64_t idx = src.index != nullptr ? src.index[k] : k;
+        double m64, r64, pad;
+        if (src.mode == 0) {
+            const unsigned long long code = src.codes[idx];
+            const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
+            const unsigned long long kk = pext64(code, mask);
+            const int c = __popcll(mask);
+            const double w = src.root_w[i];
+            const double a = src.root_lo[i];
+            r64 = ldexp(w, -(c + 1));
+            m64 = a + w * ldexp((double)(2 * kk + 1), -(c + 1));
+            pad = ldexp(fabs(m64) + fabs(a) + w, -50);
+        } else {
+            const double lo = (double)src.lo[idx * d + i];
+            const double hi = (double)src.hi[idx * d + i];
+            m64 = 0.5 * (lo + hi);
+            r64 = 0.5 * (hi - lo);
+            pad = ldexp(fabs(m64) + fabs(r64), -52);
+        }
+        float h, l, r;
+        split_centre<float>(m64, r64, pad, h, l, r);
+        mh[item] = h;
+        ml[item] = l;
+        rr[item] = r;
+        if (i == 0) bidx[b] = idx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row kernels: a block is 32 rows (threadIdx.x) of one box (blockIdx.y) with
+// the d coefficients of each row split over 8 slices (threadIdx.y), so that a
+// warp reads 32 consecutive neurons of one coefficient column.  The slices'
+// partial sums are merged in shared memory, one thread per row plans the
+// relaxation, and all slices apply it.
+// ---------------------------------------------------------------------------
+constexpr int kRowsX = 32, kSlicesY = 8;
+
+// Layer 1: C = [W_1 diag(r) | W_1 m + b_1], R = 0 (Sec. 3), then its ReLU
+// relaxation when it is a hidden layer.  W0t: W_1 transposed (d x n_1).
+__global__ void __launch_bounds__(kRowsX * kSlicesY)
+wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const float *mh, const float *ml,
+                 const float *rr, float *C, float *Rr, float *Ch, float *Cl) {
+    using A = Arith<float>;
+    __shared__ RowBounds<float> part[kSlicesY][kRowsX];
+    __shared__ RelaxPlan<float> plan[kRowsX];
+    const int d = net.d;
+    const int n1 = net.n[1];
+    const int lane = threadIdx.x, sl = threadIdx.y;
+    const int p = blockIdx.x * kRowsX + lane;
+    const int64_t b = blockIdx.y;
+    const bool live = p < n1;
+    const WideRow R{C, Rr, Ch, Cl, b, live ? p : 0, d, NP};
+    const float *rb = rr + b * d;
+    RowBounds<float> bd;
+    bd.reset();
+    if (live) {
+        for (int j = sl; j < d; j += kSlicesY) {
+            const float c = A::mul_rn(W0t[(size_t)j * n1 + p], rb[j]);
+            R(j) = c;
+            R(WTile::cR(d) + j) = 0.f;
+            bd.add(c, 0.f);
+        }
+    }
+    part[sl][lane] = bd;
+    __syncthreads();
+    if (sl == 0 && live) {
+        RowBounds<float> t = part[0][lane];
+        for (int y = 1; y < kSlicesY; ++y) t.merge(part[y][lane]);
+        // the constant W_1 m + b_1, error-free products and a compensated sum
+        const float bp = net.b[0][p];
+        float s = bp, e = 0.f, sabs = fabsf(bp);
+        for (int j = 0; j < d; ++j) {
+            const float wj = W0t[(size_t)j * n1 + p];
+            float p1, pe, tt, se;
+            two_prod<float>(wj, mh[b * d + j], p1, pe);
+            two_sum<float>(s, p1, tt, se);
+            s = tt;
+            e = A::fma_rn(wj, ml[b * d + j], e + (pe + se));
+            sabs = sabs + fabsf(p1);
+        }
+        float chi, clo;
+        two_sum<float>(s, e, chi, clo);
+        const float S1 = t.NC;
+        const float g = gam<float>(d + 2);
+        float E = A::add_up(uerr<float>(S1), A::mul_up(A::mul_up(2.f * g, g), A::mul_up(sabs, 1.f + gam<float>(d))));
+        E = A::add_up(E, (float)(d + 4) * A::tiny);
+        if (net.K == 1) {
+            // folded property layer applied to x itself: |x_j| <= |m_j| + r_j
+            float fe = net.fold_berr[p];
+            for (int j = 0; j < d; ++j) {
+                const float xm = A::add_up(A::add_up(fabsf(mh[b * d + j]), fabsf(ml[b * d + j])), rb[j]);
+                fe = A::add_up(fe, A::mul_up(net.fold_err[p * d + j], xm));
+            }
+            E = A::add_up(E, fe);
+        }
+        RelaxPlan<float> pl;
+        pl.kind = 0;
+        pl.pp = 1.f;
+        pl.qq = 0.f;
+        pl.nh = chi;
+        pl.nl = clo;
+        pl.rd = 0.f;
+        pl.N = S1;
+        pl.E = E;
+        if (net.K > 1) {
+            t.finish(d, chi, clo, 0.f);
+            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, A::add_up(E, t.delta), nullptr);
+        }
+        plan[lane] = pl;
+    }
+    __syncthreads();
+    if (live) {
+        const RelaxPlan<float> pl = plan[lane];
+        if (pl.kind != 0) {
+            for (int j = sl; j < d; j += kSlicesY) {
+                float c = R(j), r = R(WTile::cR(d) + j);
+                WTile::apply_plan(pl, c, r);
+                R(j) = c;
+                R(WTile::cR(d) + j) = r;
+            }
+        }
+        if (sl == 0) {
+            R(WTile::cCh(d)) = pl.nh;
+            R(WTile::cCl(d)) = pl.nl;
+            R(WTile::cRd(d)) = pl.rd;
+            R(WTile::cN(d)) = pl.N;
+            R(WTile::cE(d)) = pl.E;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Constants of layer k + 1: sum_i W[p][i] (Ch_i + Cl_i) + b_p, error-free
+// products and compensated sums, with the error bound (and, for the folded
+// property layer, the rounding of the folded weights).
+// ---------------------------------------------------------------------------
+__global__ void wide_const_kernel(const NetParams<float> net, int k, int nb, int NP, const float *Ch, const float *Cl,
+                                  const float *Rr, float *Kh, float *Kl, float *Ke) {
+    using A = Arith<float>;
+    const int d = net.d;
+    const int n_in = net.n[k];
+    const int n_out = net.n[k + 1];
+    const bool last = k + 1 == net.K;
+    const float *Wt = net.Wt[k];
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < (int64_t)nb * n_out;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = item / n_out;
+        const int p = (int)(item - b * n_out);
+        float s = net.b[k][p], e = 0.f, a = fabsf(s), f = 0.f;
+        for (int i = 0; i < n_in; ++i) {
+            const float w = Wt[(size_t)i * n_out + p];
+            const float h = Ch[b * NP + i];
+            const float l = Cl[b * NP + i];
+            float p1, pe, t, se;
+            two_prod<float>(w, h, p1, pe);
+            two_sum<float>(s, p1, t, se);
+            s = t;
+            e = A::fma_rn(w, l, e + (pe + se));
+            a = a + fabsf(p1);
+            if (last) {
+                const float nN = Rr[((size_t)b * (d + 3) + d + 1) * NP + i];
+                const float nE = Rr[((size_t)b * (d + 3) + d + 2) * NP + i];
+                const float z = A::add_up(A::add_up(fabsf(nN), fabsf(h)), A::add_up(fabsf(l), fabsf(nE)));
+                f = A::add_up(f, A::mul_up(net.fold_err[p * n_in + i], z));
+            }
+        }
+        const float g = gam<float>(n_in + 2);
+        const float g2 = A::mul_up(2.f * g, g);
+        float hi, lo;
+        two_sum<float>(s, e, hi, lo);
+        float err = A::mul_up(g2, A::mul_up(a, 1.f + gam<float>(n_in)));
+        if (last) err = A::add_up(err, A::add_up(f, net.fold_berr[p]));
+        Kh[b * NP + p] = hi;
+        Kl[b * NP + p] = lo;
+        Ke[b * NP + p] = err;
+    }
+}
+
+namespace {
+
+// The contraction's constant and error (E' = |W| E (1 + 2 g) + g |W| N (1 + g) + constant error).
+__device__ __forceinline__ void wide_finish(const WideRow &R, const float *Kh, const float *Kl, const float *Ke,
+                                            int NP, int n_in, float gcoef, float &chi, float &clo, float &E) {
+    using A = Arith<float>;
+    const int d = R.d;
+    chi = Kh[R.b * NP + R.p];
+    clo = Kl[R.b * NP + R.p];
+    const float wN = R(WTile::cN(d));
+    float eps = A::mul_up(gcoef, A::mul_up(wN, 1.f + gcoef));
+    eps = A::add_up(A::add_up(eps, Ke[R.b * NP + R.p]), (float)(n_in + 4) * A::tiny);
+    E = A::add_up(A::mul_up(R(WTile::cE(d)), 1.f + 2.f * gcoef), eps);
+}
+
+}  // namespace
+
+// Hidden layer `layer` after its product: error, bounds, ReLU relaxation in place.
+__global__ void __launch_bounds__(kRowsX * kSlicesY)
+wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, float *C, float *Rr, float *Ch,
+                   float *Cl, const float *Kh, const float *Kl, const float *Ke) {
+    using A = Arith<float>;
+    __shared__ RowBounds<float> part[kSlicesY][kRowsX];
+    __shared__ RelaxPlan<float> plan[kRowsX];
+    const int d = net.d;
+    const int n = net.n[layer];
+    const int n_in = net.n[layer - 1];
+    const int lane = threadIdx.x, sl = threadIdx.y;
+    const int p = blockIdx.x * kRowsX + lane;
+    const int64_t b = blockIdx.y;
+    const bool live = p < n;
+    const WideRow R{C, Rr, Ch, Cl, b, live ? p : 0, d, NP};
+    RowBounds<float> bd;
+    bd.reset();
+    if (live)
+        for (int j = sl; j < d; j += kSlicesY) bd.add(R(j), R(WTile::cR(d) + j));
+    part[sl][lane] = bd;
+    __syncthreads();
+    if (sl == 0 && live) {
+        RowBounds<float> t = part[0][lane];
+        for (int y = 1; y < kSlicesY; ++y) t.merge(part[y][lane]);
+        float chi, clo, E;
+        wide_finish(R, Kh, Kl, Ke, NP, n_in, gcoef, chi, clo, E);
+        const float rd = R(WTile::cRd(d));
+        t.finish(d, chi, clo, rd);
+        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, A::add_up(E, t.delta), nullptr);
+    }
+    __syncthreads();
+    if (live) {
+        const RelaxPlan<float> pl = plan[lane];
+        if (pl.kind != 0) {
+            for (int j = sl; j < d; j += kSlicesY) {
+                float c = R(j), r = R(WTile::cR(d) + j);
+                WTile::apply_plan(pl, c, r);
+                R(j) = c;
+                R(WTile::cR(d) + j) = r;
+            }
+        }
+        if (sl == 0) {
+            R(WTile::cCh(d)) = pl.nh;
+            R(WTile::cCl(d)) = pl.nl;
+            R(WTile::cRd(d)) = pl.rd;
+            R(WTile::cN(d)) = pl.N;
+            R(WTile::cE(d)) = pl.E;
+        }
+    }
+}
+
+// Property rows: sound bounds lo = min L' - E, hi = max U' + E (Sec. 3 check).
+__global__ void __launch_bounds__(kRowsX * kSlicesY)
+wide_final_kernel(const NetParams<float> net, int NP, float gcoef, float *C, float *Rr, float *Ch, float *Cl,
+                  const float *Kh, const float *Kl, const float *Ke, float *lo, float *hi, float *err) {
+    using A = Arith<float>;
+    __shared__ RowBounds<float> part[kSlicesY][kRowsX];
+    const int d = net.d;
+    const int R = net.R;
+    const int n_in = net.n[net.K - 1];
+    const int lane = threadIdx.x, sl = threadIdx.y;
+    const int r = blockIdx.x * kRowsX + lane;
+    const int64_t b = blockIdx.y;
+    const bool live = r < R;
+    const WideRow Rw{C, Rr, Ch, Cl, b, live ? r : 0, d, NP};
+    RowBounds<float> bd;
+    bd.reset();
+    if (live)
+        for (int j = sl; j < d; j += kSlicesY) bd.add(Rw(j), Rw(WTile::cR(d) + j));
+    part[sl][lane] = bd;
+    __syncthreads();
+    if (sl == 0 && live) {
+        RowBounds<float> t = part[0][lane];
+        for (int y = 1; y < kSlicesY; ++y) t.merge(part[y][lane]);
+        float chi, clo, E;
+        if (net.K > 1) {
+            wide_finish(Rw, Kh, Kl, Ke, NP, n_in, gcoef, chi, clo, E);
+        } else {
+            chi = Rw(WTile::cCh(d));
+            clo = Rw(WTile::cCl(d));
+            E = Rw(WTile::cE(d));
+        }
+        t.finish(d, chi, clo, Rw(WTile::cRd(d)));
+        E = A::add_up(E, t.delta);
+        lo[b * R + r] = A::add_dn(t.ll, -E);
+        hi[b * R + r] = A::add_up(t.uu, E);
+        err[b * R + r] = E;
+    }
+}
+
+namespace {
+
+__device__ __forceinline__ uint8_t wide_class(const NetParams<float> &net, const float *lo, const float *hi,
+                                              const float *err, float shift) {
+    bool any_in = false, all_out = true;
+    int r0 = 0;
+    for (int cl = 0; cl < net.n_clauses; ++cl) {
+        const int r1 = net.clause_end[cl];
+        bool all_in = true, some_out = false;
+        for (int r = r0; r < r1; ++r) {
+            const float e2 = shift * err[r];
+            const float l = lo[r] + e2;
+            const float h = hi[r] - e2;
+            const bool st = net.strict[r] != 0;
+            all_in = all_in && (st ? (l > 0.f) : (l >= 0.f));
+            some_out = some_out || (st ? (h <= 0.f) : (h < 0.f));
+        }
+        any_in = any_in || all_in;
+        all_out = all_out && some_out;
+        r0 = r1;
+    }
+    return any_in ? kUnsafe : (all_out ? kSafe : kUndecided);
+}
+
+}  // namespace
+
+// Class of each box of the chunk (Sec. 3 check) and the outputs.  Boxes whose
+// class depends on E (their optimistic class differs) stay UNDECIDED and are
+// counted in tie_count: the wide path has no FP64 re-check.
+__global__ void wide_classify_kernel(const NetParams<float> net, int nb, int64_t base, const float *lo,
+                                     const float *hi, const float *err, const int64_t *bidx, const EvalOutputs out) {
+    const int R = net.R;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const float *l = lo + (size_t)b * R, *h = hi + (size_t)b * R, *e = err + (size_t)b * R;
+        const uint8_t cls = wide_class(net, l, h, e, 0.f);
+        const uint8_t opt = wide_class(net, l, h, e, 2.f);
+        const int64_t oidx = out.by_position ? base + b : bidx[b];
+        if (out.cls != nullptr) out.cls[oidx] = cls;
+        if (out.row_lo != nullptr) {
+            for (int r = 0; r < R; ++r) {
+                out.row_lo[oidx * R + r] = l[r];
+                out.row_hi[oidx * R + r] = h[r];
+            }
+        }
+        if (out.row_err != nullptr)
+            for (int r = 0; r < R; ++r) out.row_err[oidx * R + r] = e[r];
+        if (cls == kUndecided && opt != kUndecided && out.tie_count != nullptr) atomicAdd(out.tie_count, 1ull);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// D[col][m] = sum_k A[m][k] B[col][k] for m < M, col < ncols: one 128 x 256
+// tile per CTA, K in stages of 32 (two stages in shared memory, loads of the
+// next stage overlapping the tensor core), accumulator in tensor memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmArgs args) {
+    extern __shared__ __align__(1024) unsigned char smem_w[];
+    const WideGemm &G = args.g[blockIdx.z];
+    const int n0 = blockIdx.x * kWN;
+    const int m0 = blockIdx.y * kWM;
+    if (n0 >= G.ncols || m0 >= G.M) return;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_w + 2 * kWStage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_w + 2 * kWStage + 2 * sizeof(uint64_t));
+    int *sAbort = reinterpret_cast<int *>(smem_w + 2 * kWStage + 2 * sizeof(uint64_t) + 4);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *sAbort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kWN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const int wait_limit = 1 << 24;
+    // kind::tf32, FP32 accumulate, both operands K-major, N = 256, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kWN >> 3) << 17) |
+                           ((uint32_t)(kWM >> 4) << 24);
+    const int nch = G.Kpad / kWK;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const int s = c & 1;
+        unsigned char *st = smem_w + s * kWStage;
+        unsigned char *sAh = st, *sAl = st + kWABytes, *sBh = st + 2 * kWABytes, *sBl = st + 2 * kWABytes + kWBBytes;
+        if (c >= 2 && ok) {
+            // the products of stage s issued two chunks ago have finished reading it
+            if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((c - 2) >> 1) & 1), wait_limit)) ok = false;
+        }
+        if (!ok) atomicExch(sAbort, 1);
+        __syncthreads();
+        if (*sAbort) break;
+        const int k0 = c * kWK;
+        // A: rows m0.., TF32 pieces pre-split on the host (zero padded to Mpad x Kpad)
+        for (int q = tid; q < kWM * kWK / 4; q += kWThreads) {
+            const int r = q >> 3;
+            const int kq = (q & 7) * 4;
+            const size_t g = (size_t)(m0 + r) * G.Kpad + k0 + kq;
+            *reinterpret_cast<float4 *>(sAh + wboff(r, kq)) = *reinterpret_cast<const float4 *>(G.Ahi + g);
+            *reinterpret_cast<float4 *>(sAl + wboff(r, kq)) = *reinterpret_cast<const float4 *>(G.Alo + g);
+        }
+        // B: columns n0.., split into TF32 pieces here (zero beyond K and ncols)
+        for (int q = tid; q < kWN * kWK / 4; q += kWThreads) {
+            const int cn = q >> 3;
+            const int kq = (q & 7) * 4;
+            const int col = n0 + cn;
+            const int k = k0 + kq;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (col < G.ncols) {
+                const float *src = G.B + (size_t)col * G.ldb + k;
+                if (k + 3 < G.K) {
+                    const float4 x = *reinterpret_cast<const float4 *>(src);
+                    v[0] = x.x;
+                    v[1] = x.y;
+                    v[2] = x.z;
+                    v[3] = x.w;
+                } else {
+                    for (int t = 0; t < 4; ++t)
+                        if (k + t < G.K) v[t] = src[t];
+                }
+            }
+            float4 h, l;
+            h.x = tf32_rna(v[0]);
+            h.y = tf32_rna(v[1]);
+            h.z = tf32_rna(v[2]);
+            h.w = tf32_rna(v[3]);
+            l.x = tf32_rna(v[0] - h.x);
+            l.y = tf32_rna(v[1] - h.y);
+            l.z = tf32_rna(v[2] - h.z);
+            l.w = tf32_rna(v[3] - h.w);
+            *reinterpret_cast<float4 *>(sBh + wboff(cn, kq)) = h;
+            *reinterpret_cast<float4 *>(sBl + wboff(cn, kq)) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t pa[3] = {smem_u32(sAh), smem_u32(sAl), smem_u32(sAh)};
+            const uint32_t pb[3] = {smem_u32(sBl), smem_u32(sBh), smem_u32(sBh)};
+            for (int step = 0; step < kWK / 8; ++step) {
+                for (int ps = 0; ps < 3; ++ps) {
+                    const uint64_t da = umma_desc(pa[ps] + step * 2 * kTcLbo, kTcLbo, kWSbo);
+                    const uint64_t db = umma_desc(pb[ps] + step * 2 * kTcLbo, kTcLbo, kWSbo);
+                    const uint32_t acc = (c > 0 || step > 0 || ps > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[s]))
+                : "memory");
+        }
+    }
+    // the last commit covers every product issued before it
+    if (!*sAbort && nch > 0) {
+        const int cl = nch - 1;
+        if (!mbar_wait(smem_u32(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1), wait_limit)) atomicExch(sAbort, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (!*sAbort) {
+        const int quad = warp & 3;
+        const int half = warp >> 2;
+        const int m = m0 + quad * 32 + lane;
+        for (int cc = 0; cc < kWN / 2; cc += 8) {
+            uint32_t r[8];
+            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * (kWN / 2) + cc);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < G.M) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int col = n0 + half * (kWN / 2) + cc + j;
+                    if (col < G.ncols) G.D[(size_t)col * G.ldd + m] = __uint_as_float(r[j]);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(args.status, kStatusTimeout);
+        // a timed-out product may still be running: give it a bounded chance to finish
+        for (int s = 0; s < 2; ++s) mbar_wait(smem_u32(&mbar[s]), 0u, wait_limit);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWN));
+}
+
+size_t wide_gemm_smem_bytes() { return 2 * (size_t)kWStage + 64; }
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+static int grid_for(int64_t items, int sms) {
+    const int64_t g = (items + 255) / 256;
+    const int64_t cap = (int64_t)sms * 16;
+    return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
+cudaError_t launch_wide_box(const BoxSource &src, int64_t base, int nb, int d, float *mh, float *ml, float *rr,
+                            int64_t *bidx, int sms, cudaStream_t s) {
+    wide_box_kernel<<<grid_for((int64_t)nb * d, sms), 256, 0, s>>>(src, base, nb, d, mh, ml, rr, bidx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_init(const NetParams<float> &net, const float *W0t, int nb, int NP, const float *mh,
+                             const float *ml, const float *rr, float *C, float *Rr, float *Ch, float *Cl, cudaStream_t s) {
+    const dim3 grid((net.n[1] + kRowsX - 1) / kRowsX, nb), block(kRowsX, kSlicesY);
+    wide_init_kernel<<<grid, block, 0, s>>>(net, W0t, NP, mh, ml, rr, C, Rr, Ch, Cl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_const(const NetParams<float> &net, int k, int nb, int NP, const float *Ch, const float *Cl,
+                              const float *Rr, float *Kh, float *Kl, float *Ke, int sms, cudaStream_t s) {
+    wide_const_kernel<<<grid_for((int64_t)nb * net.n[k + 1], sms), 256, 0, s>>>(net, k, nb, NP, Ch, Cl, Rr, Kh, Kl,
+                                                                                  Ke);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_hidden(const NetParams<float> &net, int layer, int nb, int NP, float gcoef, float *C, float *Rr,
+                               float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke, cudaStream_t s) {
+    const dim3 grid((net.n[layer] + kRowsX - 1) / kRowsX, nb), block(kRowsX, kSlicesY);
+    wide_hidden_kernel<<<grid, block, 0, s>>>(net, layer, NP, gcoef, C, Rr, Ch, Cl, Kh, Kl, Ke);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_final(const NetParams<float> &net, int nb, int NP, float gcoef, float *C, float *Rr, float *Ch,
+                              float *Cl, const float *Kh, const float *Kl, const float *Ke, float *lo, float *hi,
+                              float *err, cudaStream_t s) {
+    const dim3 grid((net.R + kRowsX - 1) / kRowsX, nb), block(kRowsX, kSlicesY);
+    wide_final_kernel<<<grid, block, 0, s>>>(net, NP, gcoef, C, Rr, Ch, Cl, Kh, Kl, Ke, lo, hi, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_classify(const NetParams<float> &net, int nb, int64_t base, const float *lo, const float *hi,
+                                 const float *err, const int64_t *bidx, const EvalOutputs &out, int sms,
+                                 cudaStream_t s) {
+    wide_classify_kernel<<<grid_for(nb, sms), 256, 0, s>>>(net, nb, base, lo, hi, err, bidx, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_gemm(const WideGemmArgs &args, int nprob, cudaStream_t s) {
+    int gx = 1, gy = 1;
+    for (int i = 0; i < nprob; ++i) {
+        gx = std::max(gx, (args.g[i].ncols + kWN - 1) / kWN);
+        gy = std::max(gy, (args.g[i].M + kWM - 1) / kWM);
+    }
+    const size_t smem = wide_gemm_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    wide_gemm_kernel<<<dim3(gx, gy, nprob), kWThreads, smem, s>>>(args);
+    return cudaGetLastError();
+}
+
+}  // namespace slr

@@ -7,5 +7,5 @@ the CUDA library can be fed the same inputs.
 """
 from .generators import (  # noqa: F401
     Network, Property, Problem, CONFIGS, make, tiny, acas_shaped, nav_shaped,
-    linear_2d, single_layer_1d, rare_violation, mc_violation_rate, batched_uneven,
+    linear_2d, single_layer_1d, rare_violation, mc_violation_rate, batched_uneven, mnist_shaped,
 )

@@ -175,6 +175,19 @@ def _nav_raw(seed):
     return Problem("nav_22-64-64-3", net, lo, hi, prop, 24, seed)
 
 
+def _mnist_raw(seed, radius=0.02):
+    rng = np.random.default_rng(seed)
+    net = _mlp(rng, [784, 256, 256, 256, 10])
+    x0 = rng.random(784)
+    lo = np.clip(x0 - radius, 0.0, 1.0).astype(np.float32)
+    hi = np.clip(x0 + radius, 0.0, 1.0).astype(np.float32)
+    # unsafe: class 0 is not the argmax, OR_j (y_j - y_0 >= 0)
+    clauses = [[(_unit(10, j) - _unit(10, 0), 0.0, False)] for j in range(1, 10)]
+    p = Problem("mnist_784-256x3-10", net, lo, hi, _prop(clauses), 12, seed)
+    p.extra["centre"] = x0.astype(np.float32)
+    return p
+
+
 @functools.lru_cache(maxsize=64)
 def tiny(seed: int = 0) -> Problem:
     """2 -> 8 -> 8 -> 1 on [-1,1]^2, unsafe y < 0, depth 16; VR in [5%, 95%]."""
@@ -191,6 +204,18 @@ def acas_shaped(seed: int = 0) -> Problem:
 def nav_shaped(seed: int = 0) -> Problem:
     """22 -> 64 -> 64 -> 3 (mapless-navigation shape, Sec. 4), action 1 argmax, depth 24; VR in [5%, 50%]."""
     return _first_in_window(_nav_raw, seed, (0.05, 0.5))
+
+
+@functools.lru_cache(maxsize=16)
+def mnist_shaped(seed: int = 0) -> Problem:
+    """784 -> 3x256 -> 10 (an MNIST-classifier shape), L-inf ball of radius 0.02 around a
+    random point of [0,1]^784 clipped to [0,1], class 0 stays argmax, depth 12.  The
+    first seed at or above `seed` whose network puts class 0 on top at the centre."""
+    for s in range(seed, seed + 1000):
+        p = _mnist_raw(s)
+        if int(np.argmax(_forward(p.net, p.extra["centre"][None])[0])) == 0:
+            return p
+    raise RuntimeError("no seed puts class 0 on top")
 
 
 def linear_2d(seed: int = 0, depth: int = 12) -> Problem:
@@ -288,6 +313,7 @@ CONFIGS = {
     "tiny": tiny,
     "acas": acas_shaped,
     "nav": nav_shaped,
+    "mnist": mnist_shaped,
 }
 
 
