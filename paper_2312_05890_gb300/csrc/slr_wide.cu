@@ -410,11 +410,77 @@ __global__ void wide_classify_kernel(const NetParams<float> net, int nb, int64_t
 // tile per CTA, K in stages of 32 (two stages in shared memory, loads of the
 // next stage overlapping the tensor core), accumulator in tensor memory.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmArgs args) {
+// Operands of one K stage, held in registers between their global loads and
+// their shared-memory stores (the loads of stage c + 1 are in flight while
+// stage c is stored and multiplied).
+struct WideStageRegs {
+    float4 ah[kWM * kWK / 4 / kWThreads], al[kWM * kWK / 4 / kWThreads];
+    float4 b[kWN * kWK / 4 / kWThreads];
+};
+
+__device__ __forceinline__ void wide_load_stage(const WideGemm &G, int m0, int n0, int k0, int tid, WideStageRegs &r) {
+#pragma unroll
+    for (int u = 0; u < kWM * kWK / 4 / kWThreads; ++u) {
+        const int q = tid + u * kWThreads;
+        const size_t g = (size_t)(m0 + (q >> 3)) * G.Kpad + k0 + (q & 7) * 4;
+        r.ah[u] = __ldg(reinterpret_cast<const float4 *>(G.Ahi + g));
+        r.al[u] = __ldg(reinterpret_cast<const float4 *>(G.Alo + g));
+    }
+#pragma unroll
+    for (int u = 0; u < kWN * kWK / 4 / kWThreads; ++u) {
+        const int q = tid + u * kWThreads;
+        const int col = n0 + (q >> 3);
+        const int k = k0 + (q & 7) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col < G.ncols) {
+            const float *src = G.B + (size_t)col * G.ldb + k;
+            if (k + 3 < G.K) {
+                v = *reinterpret_cast<const float4 *>(src);
+            } else {
+                if (k < G.K) v.x = src[0];
+                if (k + 1 < G.K) v.y = src[1];
+                if (k + 2 < G.K) v.z = src[2];
+            }
+        }
+        r.b[u] = v;
+    }
+}
+
+__device__ __forceinline__ void wide_store_stage(unsigned char *st, int tid, const WideStageRegs &r) {
+    unsigned char *sAh = st, *sAl = st + kWABytes, *sBh = st + 2 * kWABytes, *sBl = st + 2 * kWABytes + kWBBytes;
+#pragma unroll
+    for (int u = 0; u < kWM * kWK / 4 / kWThreads; ++u) {
+        const int q = tid + u * kWThreads;
+        const int o = wboff(q >> 3, (q & 7) * 4);
+        *reinterpret_cast<float4 *>(sAh + o) = r.ah[u];
+        *reinterpret_cast<float4 *>(sAl + o) = r.al[u];
+    }
+#pragma unroll
+    for (int u = 0; u < kWN * kWK / 4 / kWThreads; ++u) {
+        const int q = tid + u * kWThreads;
+        const int o = wboff(q >> 3, (q & 7) * 4);
+        const float4 v = r.b[u];
+        float4 h, l;
+        h.x = tf32_rna(v.x);
+        h.y = tf32_rna(v.y);
+        h.z = tf32_rna(v.z);
+        h.w = tf32_rna(v.w);
+        l.x = tf32_rna(v.x - h.x);
+        l.y = tf32_rna(v.y - h.y);
+        l.z = tf32_rna(v.z - h.z);
+        l.w = tf32_rna(v.w - h.w);
+        *reinterpret_cast<float4 *>(sBh + o) = h;
+        *reinterpret_cast<float4 *>(sBl + o) = l;
+    }
+}
+
+__global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmArgs args, int gy) {
     extern __shared__ __align__(1024) unsigned char smem_w[];
     const WideGemm &G = args.g[blockIdx.z];
-    const int n0 = blockIdx.x * kWN;
-    const int m0 = blockIdx.y * kWM;
+    // the M tiles of one column block are neighbours in the launch order, so
+    // the second reads the B columns from L2
+    const int n0 = (blockIdx.x / gy) * kWN;
+    const int m0 = (blockIdx.x % gy) * kWM;
     if (n0 >= G.ncols || m0 >= G.M) return;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -443,6 +509,8 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmA
                            ((uint32_t)(kWM >> 4) << 24);
     const int nch = G.Kpad / kWK;
     bool ok = true;
+    WideStageRegs regs;
+    if (nch > 0) wide_load_stage(G, m0, n0, 0, tid, regs);
     for (int c = 0; c < nch; ++c) {
         const int s = c & 1;
         unsigned char *st = smem_w + s * kWStage;
@@ -452,51 +520,11 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmA
             if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((c - 2) >> 1) & 1), wait_limit)) ok = false;
         }
         if (!ok) atomicExch(sAbort, 1);
-        __syncthreads();
-        if (*sAbort) break;
-        const int k0 = c * kWK;
-        // A: rows m0.., TF32 pieces pre-split on the host (zero padded to Mpad x Kpad)
-        for (int q = tid; q < kWM * kWK / 4; q += kWThreads) {
-            const int r = q >> 3;
-            const int kq = (q & 7) * 4;
-            const size_t g = (size_t)(m0 + r) * G.Kpad + k0 + kq;
-            *reinterpret_cast<float4 *>(sAh + wboff(r, kq)) = *reinterpret_cast<const float4 *>(G.Ahi + g);
-            *reinterpret_cast<float4 *>(sAl + wboff(r, kq)) = *reinterpret_cast<const float4 *>(G.Alo + g);
-        }
-        // B: columns n0.., split into TF32 pieces here (zero beyond K and ncols)
-        for (int q = tid; q < kWN * kWK / 4; q += kWThreads) {
-            const int cn = q >> 3;
-            const int kq = (q & 7) * 4;
-            const int col = n0 + cn;
-            const int k = k0 + kq;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (col < G.ncols) {
-                const float *src = G.B + (size_t)col * G.ldb + k;
-                if (k + 3 < G.K) {
-                    const float4 x = *reinterpret_cast<const float4 *>(src);
-                    v[0] = x.x;
-                    v[1] = x.y;
-                    v[2] = x.z;
-                    v[3] = x.w;
-                } else {
-                    for (int t = 0; t < 4; ++t)
-                        if (k + t < G.K) v[t] = src[t];
-                }
-            }
-            float4 h, l;
-            h.x = tf32_rna(v[0]);
-            h.y = tf32_rna(v[1]);
-            h.z = tf32_rna(v[2]);
-            h.w = tf32_rna(v[3]);
-            l.x = tf32_rna(v[0] - h.x);
-            l.y = tf32_rna(v[1] - h.y);
-            l.z = tf32_rna(v[2] - h.z);
-            l.w = tf32_rna(v[3] - h.w);
-            *reinterpret_cast<float4 *>(sBh + wboff(cn, kq)) = h;
-            *reinterpret_cast<float4 *>(sBl + wboff(cn, kq)) = l;
-        }
+        if (ok) wide_store_stage(st, tid, regs);
+        if (c + 1 < nch) wide_load_stage(G, m0, n0, (c + 1) * kWK, tid, regs);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (*sAbort) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t pa[3] = {smem_u32(sAh), smem_u32(sAl), smem_u32(sAh)};
@@ -618,7 +646,7 @@ cudaError_t launch_wide_gemm(const WideGemmArgs &args, int nprob, cudaStream_t s
     const size_t smem = wide_gemm_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    wide_gemm_kernel<<<dim3(gx, gy, nprob), kWThreads, smem, s>>>(args);
+    wide_gemm_kernel<<<dim3(gx * gy, 1, nprob), kWThreads, smem, s>>>(args, gy);
     return cudaGetLastError();
 }
 
