@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 SMS = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20          # written between timed steps (> 129 MB L2)
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 / BF16 tensor rates of GB300
 
 # DRAM bytes per box of the FP32 evaluation kernel from one ncu capture of the
 # kernel source hashed below (profiles/slr_eval_f32_acas.md); reported as
@@ -187,6 +188,8 @@ def main():
     ap.add_argument("--alpha-steps", type=int, default=0,
                     help="projected-Adam steps on the lower ReLU slopes of each level's undecided boxes")
     ap.add_argument("--alpha-lr", type=float, default=0.1)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32"],
+                    help="contraction of the fused kernel: FP32 CUDA cores or split-TF32 tensor cores")
     ap.add_argument("--tile", default="",
                     help="boxes x threads per CTA of the FP32 evaluation kernel, e.g. 16x256 (default: timed choice)")
     ap.add_argument("--alpha-cap", type=int, default=1 << 20,
@@ -253,6 +256,9 @@ def main():
     if args.tile:
         tb, tt = (int(x) for x in args.tile.lower().split("x"))
         tile = {"tile_boxes": tb, "tile_threads": tt}
+    if args.precision == "tf32":
+        tile["precision"] = pkg.PREC_TC_TF32
+        config["precision"] = "split-TF32 tensor-core contraction (tcgen05), FP32 re-bound and FP64 re-check"
     fixed = None
     if args.alpha_steps:
         c.set_options(**tile)
@@ -272,6 +278,7 @@ def main():
     dev_ms, boxes, kern = [], 0, [0.0, 0.0, 0.0]
     launches = 0
     alpha_ms = 0.0
+    gemm_ms, gemm_flop, gemm_launches = 0.0, 0.0, 0
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -282,6 +289,9 @@ def main():
         for i in range(3):
             kern[i] += r["kernel_ms"][i]
         alpha_ms += r["alpha_ms"]
+        gemm_ms += r["gemm_ms"]
+        gemm_flop += r["gemm_flop"]
+        gemm_launches += r["gemm_launches"]
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t_wall
@@ -326,6 +336,19 @@ def main():
                 "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk:.0f} MHz (sampled median)",
                 "flop_per_box": fpb, "kernel_share": kern[0] / max(1e-9, sum(dev_ms)),
                 "avg_launch_ms": kern[0] / eval_launches}
+    if gemm_launches:
+        # wide path: the per-layer products on the tensor cores dominate
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        tf32_peak = peaks["bf16_tflops"] * TF32_PER_BF16
+        ach = gemm_flop / (gemm_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": ach / tf32_peak, "traffic": None, "kernel": "wide_gemm_kernel (tcgen05 kind::tf32)",
+                    "peak_basis": f"measured bf16 burst {peaks['bf16_tflops']} TFLOP/s x nominal TF32/BF16 "
+                                  f"ratio {TF32_PER_BF16:.3f}",
+                    "flop_basis": "2 M K (2d + 1) per box and layer (W C on d columns, |W| R on d + 1); "
+                                  "the kernel issues 3 split products for each",
+                    "executed_tflops": 3 * ach, "kernel_share": gemm_ms / max(1e-9, sum(dev_ms)),
+                    "avg_launch_ms": gemm_ms / gemm_launches, "launches": gemm_launches}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

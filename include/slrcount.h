@@ -117,6 +117,9 @@ typedef struct {
     uint64_t alpha_boxes;   /* alpha_steps > 0: boxes whose slopes were optimised */
     uint64_t alpha_decided; /* of those, boxes that the optimised slopes decided */
     double alpha_ms;        /* with profile: device time of the slope optimisation */
+    double gemm_ms;         /* with profile, wide path: device time of the tensor-core products */
+    int64_t gemm_launches;  /* wide path: product launches */
+    double gemm_flop;       /* wide path: algorithmic FLOP of those products (2 M N K each) */
 } slr_result;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to

@@ -60,7 +60,8 @@ class slr_result(ctypes.Structure):
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
                 ("rechecked_fp32", ctypes.c_uint64), ("alpha_boxes", ctypes.c_uint64),
-                ("alpha_decided", ctypes.c_uint64), ("alpha_ms", ctypes.c_double)]
+                ("alpha_decided", ctypes.c_uint64), ("alpha_ms", ctypes.c_double),
+                ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_int64), ("gemm_flop", ctypes.c_double)]
 
     def to_dict(self):
         n = self.depth + 1
@@ -72,6 +73,8 @@ class slr_result(ctypes.Structure):
                     tile=(int(self.tile_boxes), int(self.tile_threads)),
                     rechecked_fp32=int(self.rechecked_fp32), alpha_boxes=int(self.alpha_boxes),
                     alpha_decided=int(self.alpha_decided), alpha_ms=float(self.alpha_ms),
+                    gemm_ms=float(self.gemm_ms), gemm_launches=int(self.gemm_launches),
+                    gemm_flop=float(self.gemm_flop),
                     level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 

@@ -101,6 +101,10 @@ struct slr_ctx {
     int w_Kpad[slr::kMaxLayers] = {};
     void *wide_buf = nullptr;             // chunk state
     size_t wide_buf_bytes = 0;
+    std::vector<cudaEvent_t> gemm_ev;     // profile: a pair around each product launch
+    size_t gemm_ev_used = 0;
+    int64_t gemm_launches = 0;
+    double gemm_flop = 0;
 
     int64_t cap = 0, near_cap = 0;
     uint64_t *codes[2] = {nullptr, nullptr};
@@ -606,7 +610,22 @@ int run_wide(slr_ctx *ctx, const slr::BoxSource &src, int64_t n, const slr::Eval
                                     nb * d, np, np};
             ga.g[1] = slr::WideGemm{ctx->wa_hi[k], ctx->wa_lo[k], Rb[cur], Rb[nxt], nf.n[k + 1], nf.n[k],
                                     ctx->w_Kpad[k], nb * (d + 3), np, np};
+            const bool prof = ctx->opt.profile != 0;
+            if (prof) {
+                while (ctx->gemm_ev.size() < ctx->gemm_ev_used + 2) {
+                    cudaEvent_t e;
+                    CK(ctx, cudaEventCreate(&e));
+                    ctx->gemm_ev.push_back(e);
+                }
+                CK(ctx, cudaEventRecord(ctx->gemm_ev[ctx->gemm_ev_used], ctx->stream));
+            }
             CK(ctx, slr::launch_wide_gemm(ga, 2, ctx->stream));
+            if (prof) {
+                CK(ctx, cudaEventRecord(ctx->gemm_ev[ctx->gemm_ev_used + 1], ctx->stream));
+                ctx->gemm_ev_used += 2;
+            }
+            ctx->gemm_launches += 1;
+            ctx->gemm_flop += 2.0 * nf.n[k + 1] * nf.n[k] * ((double)nb * (2 * d + 1));
             CK(ctx, slr::launch_wide_const(nf, k, nb, np, Ch, Cl, Rb[cur], Kh, Kl, Ke, sms, ctx->stream));
             const float g = slr::tc_gamma(ctx->w_Kpad[k]);
             if (k + 1 < K) {
@@ -939,6 +958,7 @@ int slr_destroy(slr_ctx *ctx) {
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->gemm_ev) cudaEventDestroy(e);
     if (ctx->batch) {
         if (ctx->batch->graph) cudaGraphExecDestroy(ctx->batch->graph);
         cudaFree(ctx->batch->arena);
@@ -1117,6 +1137,9 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         return prof ? cudaEventRecord(ctx->prof_ev[(size_t)t * 6 + slot], ctx->stream) : cudaSuccess;
     };
     int64_t launches = 1;
+    ctx->gemm_ev_used = 0;
+    ctx->gemm_launches = 0;
+    ctx->gemm_flop = 0;
     CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
     for (int t = 0; t <= D; ++t) {
         slr::BoxSource src{};
@@ -1266,6 +1289,13 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
             out->kernel_ms[1] += b;
             out->kernel_ms[2] += c2;
         }
+    }
+    out->gemm_launches = ctx->gemm_launches;
+    out->gemm_flop = ctx->gemm_flop;
+    for (size_t i = 0; i + 1 < ctx->gemm_ev_used; i += 2) {
+        float g = 0.f;
+        cudaEventElapsedTime(&g, ctx->gemm_ev[i], ctx->gemm_ev[i + 1]);
+        out->gemm_ms += g;
     }
     ctx->n_leaves = leaves ? (int64_t)c.leaves : 0;
     ctx->leaves_valid = leaves;

@@ -141,54 +141,62 @@ struct SimtLayout {
 };
 
 // Concrete bounds of the raw equations U = C + R, L = C - R of one row over
-// the box (Sec. 2.2: const +- sum_j |coeff_j| in the normalised input), summed
-// in round-to-nearest; `delta` bounds how far each of the four lies from the
-// exact bound of the stored equations (callers add it to the row's E), and the
-// magnitudes NC, NR round upward.
+// the box (Sec. 2.2: const +- sum_j |coeff_j| in the normalised input), with
+// outward rounding so that they bound the stored equations exactly; the same
+// sums in round-to-nearest give `delta`, how far the outward bounds lie from
+// the nearest-rounded ones (reported with the property rows' error, so that
+// bound -+ error is the plain FP32 SLR bound).
 template <typename Real>
 struct RowBounds {
-    Real uu, lu, ul, ll;   // max U, min U, max L, min L
+    Real uu, lu, ul, ll;   // max U, min U, max L, min L (outward)
     Real NC, NR;           // sum |C_j| over coefficients, sum |R_j| incl. its constant
-    Real delta;            // rounding of uu, lu, ul, ll
-    Real SU, SL;           // sum |C_j + R_j|, sum |C_j - R_j|
+    Real delta;            // outward minus nearest-rounded, for max U and min L
+    Real SU, SL;           // sum |C_j + R_j|, sum |C_j - R_j| (upward)
+    Real SUn, SLn;         // the same sums rounded to nearest
     __device__ __forceinline__ void reset() {
-        SU = SL = NC = NR = 0;
+        SU = SL = SUn = SLn = NC = NR = 0;
     }
     __device__ __forceinline__ void add(Real c, Real r) {
         using A = Arith<Real>;
-        SU = SU + A::abs(c + r);
-        SL = SL + A::abs(c - r);
+        const Real u = A::abs(c + r), l = A::abs(c - r);
+        SU = A::add_up(SU, u);
+        SL = A::add_up(SL, l);
+        SUn = SUn + u;
+        SLn = SLn + l;
         NC = A::add_up(NC, A::abs(c));
         NR = A::add_up(NR, A::abs(r));
     }
-    // partial sums over disjoint coefficient sets (any order: delta covers it)
+    // partial sums over disjoint coefficient sets
     __device__ __forceinline__ void merge(const RowBounds &o) {
         using A = Arith<Real>;
-        SU = SU + o.SU;
-        SL = SL + o.SL;
+        SU = A::add_up(SU, o.SU);
+        SL = A::add_up(SL, o.SL);
+        SUn = SUn + o.SUn;
+        SLn = SLn + o.SLn;
         NC = A::add_up(NC, o.NC);
         NR = A::add_up(NR, o.NR);
     }
-    __device__ __forceinline__ void finish(int d, Real chi, Real clo, Real rd) {
+    __device__ __forceinline__ void finish(Real chi, Real clo, Real rd) {
         using A = Arith<Real>;
         NR = A::add_up(NR, A::abs(rd));
-        const Real cu = (chi + rd) + clo;
-        const Real cl = (chi - rd) + clo;
-        uu = cu + SU;
-        lu = cu - SU;
-        ul = cl + SL;
-        ll = cl - SL;
-        // each of the d + 3 roundings (the terms c +- r, the running sums, the
-        // constant and the final sum) is at most u times a partial magnitude
-        const Real g = gam<Real>(d + 4);
-        const Real mag = A::add_up(A::add_up(SU, SL), A::add_up(A::add_up(A::abs(chi), A::abs(rd)), A::abs(clo)));
-        delta = A::mul_up(g, A::mul_up(mag, (Real)1 + g));
+        // |c +- r| <= |fl(c +- r)| (1 + u): cover the round-to-nearest of each term
+        const Real su = A::mul_up(SU, (Real)1 + A::ulp2);
+        const Real sl = A::mul_up(SL, (Real)1 + A::ulp2);
+        uu = A::add_up(A::add_up(A::add_up(chi, rd), clo), su);
+        lu = A::add_dn(A::add_dn(A::add_dn(chi, rd), clo), -su);
+        ul = A::add_up(A::add_up(A::add_up(chi, -rd), clo), sl);
+        ll = A::add_dn(A::add_dn(A::add_dn(chi, -rd), clo), -sl);
+        const Real uun = ((chi + rd) + clo) + SUn;
+        const Real lln = ((chi - rd) + clo) - SLn;
+        const Real du = A::add_up(uu, -uun), dl = A::add_up(lln, -ll);
+        delta = du > dl ? du : dl;
+        delta = delta > (Real)0 ? delta : (Real)0;
     }
     template <class Row>
     __device__ __forceinline__ void compute(const Row &R, int d, Real chi, Real clo) {
         reset();
         for (int j = 0; j < d; ++j) add(R(j), R(d + 1 + j));
-        finish(d, chi, clo, R(2 * d + 1));
+        finish(chi, clo, R(2 * d + 1));
     }
 };
 
@@ -392,7 +400,7 @@ struct EvalTile {
 
     // ---- ReLU relaxation (Eq. 1) of one hidden row from its concrete bounds ---------
     // chi, clo: the row's constant (float-float); rd: its radius constant; E: its
-    // error bound including bd.delta.  a_ptr: the supplied lower slope of the
+    // error bound.  a_ptr: the supplied lower slope of the
     // row, or null for u_l / (u_l - l_l).
     static __device__ __forceinline__ RelaxPlan<Real> plan_row(const RowBounds<Real> &bd, int d, int relax_mode,
                                                                Real chi, Real clo, Real rd, Real E,
@@ -490,7 +498,6 @@ struct EvalTile {
         const int cr = cR(d);
         RowBounds<Real> bd;
         bd.compute(R, d, chi, clo);
-        E = A::add_up(E, bd.delta);
         const RelaxPlan<Real> pl = plan_row(bd, d, relax_mode, chi, clo, R(cr + d), E, a_ptr);
         if (pl.kind != 0) {
             for (int j = 0; j < d; ++j) {
@@ -659,10 +666,9 @@ struct EvalTile {
             }
             RowBounds<Real> bd;
             bd.compute(Rw, d, chi, clo);
-            E = A::add_up(E, bd.delta);
             sLo[r * T + b] = A::add_dn(bd.ll, -E);
             sHi[r * T + b] = A::add_up(bd.uu, E);
-            sErr[r * T + b] = E;
+            sErr[r * T + b] = A::add_up(E, bd.delta);
         }
     }
 };

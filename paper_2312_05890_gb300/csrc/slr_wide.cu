@@ -105,7 +105,7 @@ __global__ void wide_box_kernel(const BoxSource src, int64_t base, int nb, int d
 // partial sums are merged in shared memory, one thread per row plans the
 // relaxation, and all slices apply it.
 // ---------------------------------------------------------------------------
-constexpr int kRowsX = 32, kSlicesY = 8;
+constexpr int kRowsX = 32, kSlicesY = 16;
 
 // Layer 1: C = [W_1 diag(r) | W_1 m + b_1], R = 0 (Sec. 3), then its ReLU
 // relaxation when it is a hidden layer.  W0t: W_1 transposed (d x n_1).
@@ -175,8 +175,8 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
         pl.N = S1;
         pl.E = E;
         if (net.K > 1) {
-            t.finish(d, chi, clo, 0.f);
-            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, A::add_up(E, t.delta), nullptr);
+            t.finish(chi, clo, 0.f);
+            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, E, nullptr);
         }
         plan[lane] = pl;
     }
@@ -292,8 +292,8 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
         float chi, clo, E;
         wide_finish(R, Kh, Kl, Ke, NP, n_in, gcoef, chi, clo, E);
         const float rd = R(WTile::cRd(d));
-        t.finish(d, chi, clo, rd);
-        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, A::add_up(E, t.delta), nullptr);
+        t.finish(chi, clo, rd);
+        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, nullptr);
     }
     __syncthreads();
     if (live) {
@@ -347,11 +347,10 @@ wide_final_kernel(const NetParams<float> net, int NP, float gcoef, float *C, flo
             clo = Rw(WTile::cCl(d));
             E = Rw(WTile::cE(d));
         }
-        t.finish(d, chi, clo, Rw(WTile::cRd(d)));
-        E = A::add_up(E, t.delta);
+        t.finish(chi, clo, Rw(WTile::cRd(d)));
         lo[b * R + r] = A::add_dn(t.ll, -E);
         hi[b * R + r] = A::add_up(t.uu, E);
-        err[b * R + r] = E;
+        err[b * R + r] = A::add_up(E, t.delta);
     }
 }
 
