@@ -50,8 +50,11 @@ enum { SLR_SAFE = 0, SLR_UNSAFE = 1, SLR_UNDECIDED = 2 };
 /* Reading of Eq. 1 (Sec. 2.2).
  * NEURIFY: the upper line uses the bounds (l_u, u_u) of the upper equation and
  *   the lower slope those (l_l, u_l) of the lower equation (default).
- * PAPER_LITERAL: one pair (l, u) = (min of Eq_l, max of Eq_u) serves both. */
-enum { SLR_RELAX_NEURIFY = 0, SLR_RELAX_PAPER_LITERAL = 1 };
+ * PAPER_LITERAL: one pair (l, u) = (min of Eq_l, max of Eq_u) serves both.
+ * INTERVAL: no relaxation: every hidden neuron keeps only its interval
+ *   [relu(min), relu(max)] (Moore interval propagation, the paper's naive
+ *   "Exact Count" baseline of Sec. 4), for comparing split counts. */
+enum { SLR_RELAX_NEURIFY = 0, SLR_RELAX_PAPER_LITERAL = 1, SLR_RELAX_INTERVAL = 2 };
 
 /* Arithmetic of the symbolic contraction U' = W+ U + W- L + b, L' = W+ L + W- U + b.
  * FP32: IEEE FP32 FMA on the CUDA cores (the constant terms as float-float

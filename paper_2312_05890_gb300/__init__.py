@@ -20,7 +20,7 @@ SLR_OK = 0
 STATUS = {0: "SLR_OK", -1: "SLR_EINVAL", -2: "SLR_ENOMEM", -3: "SLR_ECUDA", -4: "SLR_ESTATE",
           -5: "SLR_EOVERFLOW", -6: "SLR_ETIMEOUT", -7: "SLR_EUNSUPPORTED"}
 SAFE, UNSAFE, UNDECIDED = 0, 1, 2
-RELAX_NEURIFY, RELAX_PAPER_LITERAL = 0, 1
+RELAX_NEURIFY, RELAX_PAPER_LITERAL, RELAX_INTERVAL = 0, 1, 2
 PREC_FP32 = 0
 PREC_TC_TF32 = 1
 MAX_LEVELS = 63

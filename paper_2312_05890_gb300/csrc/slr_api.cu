@@ -975,7 +975,8 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
     if (!ctx || !opt) return fail(ctx, SLR_EINVAL, "null argument");
     if (opt->precision != SLR_PREC_FP32 && opt->precision != SLR_PREC_TC_TF32)
         return fail(ctx, SLR_EINVAL, "precision %d unknown", opt->precision);
-    if (opt->relax_mode != SLR_RELAX_NEURIFY && opt->relax_mode != SLR_RELAX_PAPER_LITERAL)
+    if (opt->relax_mode != SLR_RELAX_NEURIFY && opt->relax_mode != SLR_RELAX_PAPER_LITERAL &&
+        opt->relax_mode != SLR_RELAX_INTERVAL)
         return fail(ctx, SLR_EINVAL, "relax_mode %d unknown", opt->relax_mode);
     if (opt->frontier_cap < 2 || opt->frontier_cap > ((int64_t)1 << 34))
         return fail(ctx, SLR_EINVAL, "frontier_cap %lld out of range", (long long)opt->frontier_cap);

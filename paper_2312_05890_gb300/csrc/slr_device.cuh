@@ -33,7 +33,7 @@ constexpr int kMaxWidth = 1024;   // neurons per layer
 constexpr int kMaxDepth = 62;
 
 enum : uint8_t { kSafe = 0, kUnsafe = 1, kUndecided = 2 };
-enum : int { kRelaxNeurify = 0, kRelaxPaperLiteral = 1 };
+enum : int { kRelaxNeurify = 0, kRelaxPaperLiteral = 1, kRelaxInterval = 2 };
 
 enum : uint32_t {
     kStatusOverflow = 1u,      // a level exceeded the frontier capacity

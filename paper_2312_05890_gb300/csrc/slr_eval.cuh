@@ -406,6 +406,23 @@ struct EvalTile {
                                                                Real chi, Real clo, Real rd, Real E,
                                                                const float *a_ptr) {
         RelaxPlan<Real> pl;
+        if (relax_mode == kRelaxInterval) {
+            // Moore intervals: relu is monotone and 1-Lipschitz, so the row becomes
+            // the constant interval [relu(ll), relu(uu)] (centre exact as a
+            // float-float pair, radius rounded up) and E carries over
+            const Real a = bd.ll > (Real)0 ? bd.ll : (Real)0;
+            const Real b = bd.uu > (Real)0 ? bd.uu : (Real)0;
+            pl.kind = 1;
+            pl.pp = 0;
+            pl.qq = 0;
+            two_sum<Real>(a, b, pl.nh, pl.nl);
+            pl.nh *= (Real)0.5;
+            pl.nl *= (Real)0.5;
+            pl.rd = A::mul_up(A::add_up(b, -a), (Real)0.5);
+            pl.N = pl.rd;
+            pl.E = A::add_up(E, (Real)4 * A::tiny);
+            return pl;
+        }
         if (bd.ll >= (Real)0) {
             // stable active: relu is the identity on [L - E, U + E] up to
             // U + E >= lu + E >= 0, so the equations and E carry over

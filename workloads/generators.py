@@ -314,6 +314,7 @@ CONFIGS = {
     "acas": acas_shaped,
     "nav": nav_shaped,
     "mnist": mnist_shaped,
+    "rare": rare_violation,
 }
 
 
