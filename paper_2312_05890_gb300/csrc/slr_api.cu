@@ -1231,7 +1231,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
                                     ctx->cap, t, D, leaves ? ctx->leaf_codes : nullptr, ctx->leaf_depth,
                                     ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream));
         CK(ctx, mark(t, 5));
-        ++launches;
+        launches += 2;
     }
     CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost, ctx->stream));

@@ -158,6 +158,9 @@ struct EvalOutputs {
     int by_position;              // cls/row outputs at the position in the source, not at the index
 };
 
+// Blocks of the order-preserving compaction (each takes one contiguous range).
+constexpr int kCompactBlocks = 1024;
+
 struct LevelCounters {
     unsigned long long unsafe_lo;
     unsigned long long undecided_at_D;
@@ -172,6 +175,7 @@ struct LevelCounters {
     unsigned long long frontier_n[kMaxDepth + 2];   // boxes at each level
     unsigned long long near_n[kMaxDepth + 2];       // re-check list length at each level
     unsigned long long near2_n[kMaxDepth + 2];      // second re-check list (tensor-core path)
+    unsigned int block_count[kCompactBlocks];       // order-preserving compaction: per-block undecided
 };
 
 // Largest shapes of the problems of one batched launch (shared-memory carve).
@@ -186,7 +190,7 @@ __host__ __device__ inline int state_cols(int d) { return 2 * d + 5; }
 // Contraction tiles (8 rows x 4 columns) per CTA of the fused kernel; each of
 // its threads holds at most two in registers, so this must not exceed 2 x 256.
 __host__ __device__ inline int eval_gemm_items(int T, int d, int n_max_pad) {
-    return (n_max_pad / 8) * ((2 * d + 3) * T / 4);
+    return (n_max_pad / 8) * ((2 * d + 4) * T / 4);
 }
 
 // Shared-memory footprint of the fused evaluation kernel for a tile of T boxes.
@@ -196,6 +200,7 @@ __host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max
     size_t s = 0;
     s += (size_t)n_max_pad * NS * sizeof(Real);            // state, updated in place
     s += 3 * (size_t)n_max_pad * T * sizeof(Real);         // next layer's constants (hi, lo, error)
+    s += 2 * (size_t)n_max_pad * sizeof(Real);             // reference box's constants
     s += (size_t)n_in_max * n_max_pad * sizeof(Real);      // staged weights (transposed)
     s += 3 * (size_t)T * d * sizeof(Real);                 // box centres (hi, lo) and radii
     s += 3 * (size_t)T * R * sizeof(Real);                 // row lo / hi / E

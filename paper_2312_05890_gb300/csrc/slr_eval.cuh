@@ -384,13 +384,30 @@ struct EvalTile {
     // ---- add the contraction's constant and error; returns (chi, clo, E) -------
     // gcoef bounds the relative rounding of the contraction's coefficient
     // columns (gamma_n * sum_i |W_pi| N_i, from the |W| N column).
+    // With `delta`, the constant is the reference box's (slot b = 0 of sConst)
+    // plus the product W delta the contraction left in the constant column.
     template <class Row>
     static __device__ __forceinline__ void finish_contraction(const Row &R, const Real *sConst, int nmp, int p, int b,
                                                               int d, int n_in, Real gcoef, Real &chi, Real &clo,
-                                                              Real &E) {
-        chi = sConst[p * T + b];
-        clo = sConst[(nmp + p) * T + b];
-        const Real cerr = sConst[(2 * nmp + p) * T + b];
+                                                              Real &E, bool delta = false) {
+        Real cerr;
+        if (delta) {
+            const Real ch = sConst[p * T], cl = sConst[(nmp + p) * T];
+            cerr = sConst[(2 * nmp + p) * T];
+            if (b == 0) {
+                chi = ch;
+                clo = cl;
+            } else {
+                Real e;
+                two_sum<Real>(ch, R(cCh(d)), chi, e);
+                clo = e + cl;
+                cerr = A::add_up(cerr, uerr<Real>(A::abs(clo)));
+            }
+        } else {
+            chi = sConst[p * T + b];
+            clo = sConst[(nmp + p) * T + b];
+            cerr = sConst[(2 * nmp + p) * T + b];
+        }
         const Real wN = R(cN(d));
         Real eps = A::mul_up(gcoef, A::mul_up(wN, (Real)1 + gcoef));
         eps = A::add_up(A::add_up(eps, cerr), (Real)(n_in + 4) * A::tiny);
@@ -535,7 +552,7 @@ struct EvalTile {
     template <class L>
     static __device__ void hidden_epilogue(const L &lay, const Real *sConst, const NetParams<Real> &net, int layer,
                                            Real gcoef, const float *alpha = nullptr, int64_t alpha_ld = 0,
-                                           int64_t base = 0, int64_t n = 0, int alpha_off = 0) {
+                                           int64_t base = 0, int64_t n = 0, int alpha_off = 0, bool delta = false) {
         const int d = net.d;
         const int nrows = net.n[layer];
         const int n_in = net.n[layer - 1];
@@ -545,7 +562,7 @@ struct EvalTile {
             const auto R = lay.row(p, b);
             Real chi, clo, E;
             if (layer > 1) {
-                finish_contraction(R, sConst, net.n_max_pad, p, b, d, n_in, gcoef, chi, clo, E);
+                finish_contraction(R, sConst, net.n_max_pad, p, b, d, n_in, gcoef, chi, clo, E, delta);
             } else {
                 chi = R(cCh(d));
                 clo = R(cCl(d));
@@ -560,6 +577,68 @@ struct EvalTile {
             relax_row(R, d, net.relax_mode, chi, clo, E, a_ptr);
             lay.finish_row(p, b);
         }
+    }
+
+    // ---- constants as reference + offset (float path, hidden -> hidden layers) -----
+    // The boxes of a tile are neighbours in the bisection tree, so their
+    // constants are close.  Box 0's float-float constants go to sRef; every
+    // other box keeps delta = (h + l) - (h_0 + l_0) in its constant column,
+    // which the contraction then multiplies by W with the coefficients.  The
+    // rounding of delta joins the row's E, and |delta| its magnitude N (the
+    // product's rounding is bounded by gamma |W| N).  Box 0's own constant
+    // column is left unchanged and ignored after the product.
+    template <class L>
+    static __device__ void delta_prep(const L &lay, Real *sRef, const NetParams<Real> &net, int layer) {
+        const int d = net.d;
+        const int n_in = net.n[layer];
+        const int nmp = net.n_max_pad;
+        for (int item = threadIdx.x; item < n_in * T; item += NT) {
+            const int i = item / T;
+            const int b = item - i * T;
+            const auto Rb = lay.row(i, b);
+            const auto R0 = lay.row(i, 0);
+            const Real hr = R0(cCh(d)), lr = R0(cCl(d));
+            if (b == 0) {
+                sRef[i] = hr;
+                sRef[nmp + i] = lr;
+                continue;
+            }
+            const Real h = Rb(cCh(d)), l = Rb(cCl(d));
+            Real s, e;
+            two_sum<Real>(h, -hr, s, e);
+            const Real dl = l - lr;
+            const Real t = e + dl;
+            const Real dv = s + t;
+            const Real err = A::add_up(A::add_up(uerr<Real>(A::add_up(A::abs(l), A::abs(lr))), uerr<Real>(A::abs(t))),
+                                       uerr<Real>(A::abs(dv)));
+            Rb(cCh(d)) = dv;
+            Rb(cE(d)) = A::add_up(Rb(cE(d)), err);
+            Rb(cN(d)) = A::add_up(Rb(cN(d)), A::abs(dv));
+        }
+    }
+
+    // One output row's constant at the reference box: sum_i W[p][i] (h_i + l_i) + b_p,
+    // error-free products and compensated sums, written to slot b = 0 of sConst.
+    static __device__ __forceinline__ void ref_item(Real *sConst, const Real *sRef, const Real *sW, int Mpad,
+                                                    const NetParams<Real> &net, int layer, int p) {
+        const int n_in = net.n[layer];
+        const int nmp = net.n_max_pad;
+        Real s = net.b[layer][p], e = 0, a = A::abs(s);
+        for (int i = 0; i < n_in; ++i) {
+            const Real w = sW[i * Mpad + p];
+            Real p1, pe, t, se;
+            two_prod<Real>(w, sRef[i], p1, pe);
+            two_sum<Real>(s, p1, t, se);
+            s = t;
+            e = A::fma_rn(w, sRef[nmp + i], e + (pe + se));
+            a = a + A::abs(p1);
+        }
+        const Real g = gam<Real>(n_in + 2);
+        Real hi, lo;
+        two_sum<Real>(s, e, hi, lo);
+        sConst[p * T] = hi;
+        sConst[(nmp + p) * T] = lo;
+        sConst[(2 * nmp + p) * T] = A::mul_up(A::mul_up((Real)2 * g, g), A::mul_up(a, (Real)1 + gam<Real>(n_in)));
     }
 
     // ---- C' = W C, R' = |W| R over the coefficient, N and E columns ---------------
@@ -614,13 +693,14 @@ struct EvalTile {
     // they fill the threads that hold fewer product tiles, and they read the
     // state before the barrier like the tiles do.
     template <class L>
-    static __device__ void contract(const L &lay, Real *sConst, const NetParams<Real> &net, int layer, Real *S,
-                                    const Real *sW, int n_in, int Mpad, int d, int NS) {
-        const int QW = d * T / 4;             // quads of C coefficient columns
+    static __device__ void contract(const L &lay, Real *sConst, const Real *sRef, const NetParams<Real> &net,
+                                    int layer, Real *S, const Real *sW, int n_in, int Mpad, int d, int NS,
+                                    bool delta) {
+        const int QW = (d + 1) * T / 4;       // quads of C coefficient columns and the constant column
         const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
         const int Q = QW + QA;
         const int total = (Mpad / 8) * Q;
-        const int n_const = ((net.n[layer + 1] + 1) / 2) * T;
+        const int n_const = delta ? net.n[layer + 1] : ((net.n[layer + 1] + 1) / 2) * T;
         Real acc[kItems][8][4];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
@@ -637,7 +717,10 @@ struct EvalTile {
         {
             int idx = threadIdx.x + ((total - (int)threadIdx.x + NT - 1) / NT) * NT;
             if (idx < total) idx += NT;
-            for (; idx < total + n_const; idx += NT) const_item(lay, sConst, sW, Mpad, net, layer, idx - total);
+            for (; idx < total + n_const; idx += NT) {
+                if (delta) ref_item(sConst, sRef, sW, Mpad, net, layer, idx - total);
+                else const_item(lay, sConst, sW, Mpad, net, layer, idx - total);
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -722,7 +805,7 @@ __device__ __forceinline__ uint8_t classify_rows(const NetParams<Real> &net, con
 // ---------------------------------------------------------------------------
 template <typename Real>
 struct TileSmem {
-    Real *sS, *sConst, *sW, *sMh, *sMl, *sR, *sLo, *sHi, *sErr;
+    Real *sS, *sConst, *sRef, *sW, *sMh, *sMl, *sR, *sLo, *sHi, *sErr;
     int64_t *sIdx;
 };
 
@@ -734,6 +817,8 @@ __device__ __forceinline__ TileSmem<Real> carve_smem(unsigned char *sp, int nmp,
     sp += (size_t)nmp * NS * sizeof(Real);
     m.sConst = reinterpret_cast<Real *>(sp);
     sp += 3 * (size_t)nmp * T * sizeof(Real);
+    m.sRef = reinterpret_cast<Real *>(sp);
+    sp += 2 * (size_t)nmp * sizeof(Real);
     m.sW = reinterpret_cast<Real *>(sp);
     sp += (size_t)n_in_max * nmp * sizeof(Real);
     m.sMh = reinterpret_cast<Real *>(sp);
@@ -825,17 +910,24 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
     Tile::init_layer(lay, net, sMh, sMl, sR);
     __syncthreads();
 
+    // float: hidden -> hidden constants as a reference box's plus offsets
+    constexpr bool dconst = Tile::kCompensated;
     int alpha_off = 0;
     for (int k = 1; k < net.K; ++k) {
         Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
-                              alpha_off);
+                              alpha_off, dconst);
         alpha_off += net.n[k];
         const int n_out = net.n[k + 1];
         const int Mpad = (n_out + 7) & ~7;
         Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
+        const bool dk = dconst && k + 1 < net.K;
+        if (dk) {
+            __syncthreads();
+            Tile::delta_prep(lay, sm.sRef, net, k);
+        }
         __syncthreads();
         // constants and products; barrier inside, then the in-place store
-        Tile::contract(lay, sConst, net, k, sS, sW, net.n[k], Mpad, d, NS);
+        Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk);
         __syncthreads();
     }
     Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);

@@ -31,6 +31,8 @@ static int items_per_thread(int T, int NT, int items) { return (T <= 8 && items 
     switch (T * 10 + KI) {                                                                     \
         case 642: return CALL<64, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
         case 322: return CALL<32, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
+        case 202: return CALL<20, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
+        case 122: return CALL<12, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
         case 162: return CALL<16, NT_, 2>(grid, smem, s, net, src, out, pass);                 \
         case 82: return CALL<8, NT_, 2>(grid, smem, s, net, src, out, pass);                   \
         case 81: return CALL<8, NT_, 1>(grid, smem, s, net, src, out, pass);                   \
@@ -55,14 +57,18 @@ int eval_blocks_per_sm_f32(int T, int NT, size_t smem, int items) {
     switch (NT * 1000 + T * 10 + KI) {
         case 256642: return occ_t<64, 256, 2>(smem);
         case 256322: return occ_t<32, 256, 2>(smem);
+        case 256202: return occ_t<20, 256, 2>(smem);
         case 256162: return occ_t<16, 256, 2>(smem);
+        case 256122: return occ_t<12, 256, 2>(smem);
         case 256082: return occ_t<8, 256, 2>(smem);
         case 256081: return occ_t<8, 256, 1>(smem);
         case 256042: return occ_t<4, 256, 2>(smem);
         case 256041: return occ_t<4, 256, 1>(smem);
         case 128642: return occ_t<64, 128, 2>(smem);
         case 128322: return occ_t<32, 128, 2>(smem);
+        case 128202: return occ_t<20, 128, 2>(smem);
         case 128162: return occ_t<16, 128, 2>(smem);
+        case 128122: return occ_t<12, 128, 2>(smem);
         case 128082: return occ_t<8, 128, 2>(smem);
         case 128081: return occ_t<8, 128, 1>(smem);
         case 128042: return occ_t<4, 128, 2>(smem);

@@ -6,8 +6,9 @@
 //   SAFE       drops the box,
 //   UNDECIDED  writes the two children codes 2c, 2c+1 to the next level when
 //              t < D, or adds one unit to the undecided volume when t = D.
-// Each warp aggregates its counts and its output slots with one atomic per
-// warp (ballot + popc); integer sums make the result independent of order.
+// The single-problem count keeps the frontier's order (two passes, below);
+// the batched count appends with one atomic per warp (ballot + popc).
+// Integer sums make the volumes independent of order either way.
 #include "slr_eval.cuh"
 #include "slr_kernels.h"
 
@@ -95,13 +96,149 @@ __device__ __forceinline__ void compact_body(const uint64_t *__restrict__ codes_
     }
 }
 
+// ---- order-preserving compaction (single problem) ---------------------------
+// Block b of kCompactBlocks takes the contiguous range [b CH, (b+1) CH) of the
+// level; the first pass counts its UNDECIDED boxes, the second writes their
+// children at the block's exclusive prefix plus the in-block rank.  The next
+// frontier keeps the order of the current one, so it stays sorted by path
+// code: consecutive boxes are neighbours in the bisection tree, and the whole
+// count is independent of scheduling.
+__device__ __forceinline__ void compact_range(int64_t n, int64_t &lo, int64_t &hi) {
+    int64_t ch = (n + kCompactBlocks - 1) / kCompactBlocks;
+    ch = (ch + 255) & ~(int64_t)255;
+    lo = (int64_t)blockIdx.x * ch;
+    hi = lo + ch < n ? lo + ch : n;
+}
+
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    __syncthreads();
+    return tot;
+}
+
+__global__ void __launch_bounds__(256)
+compact_count_kernel(const uint8_t *__restrict__ cls, LevelCounters *ctr, int64_t cap, int t) {
+    __shared__ unsigned sh[8];
+    const unsigned long long n_raw = ctr->frontier_n[t];
+    const int64_t n = (int64_t)n_raw < cap ? (int64_t)n_raw : cap;
+    int64_t lo, hi;
+    compact_range(n, lo, hi);
+    unsigned c = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += cls[i] == kUndecided ? 1u : 0u;
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) ctr->block_count[blockIdx.x] = c;
+}
+
 __global__ void __launch_bounds__(256)
 compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
                uint64_t *__restrict__ codes_out, LevelCounters *ctr, unsigned int *status,
                int64_t cap, int t, int D, uint64_t *leaf_codes, uint8_t *leaf_depth,
                uint8_t *leaf_cls, int64_t leaf_cap) {
-    compact_body(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes, leaf_depth, leaf_cls, leaf_cap,
-                 blockIdx.x, gridDim.x);
+    __shared__ unsigned sh[8];
+    __shared__ unsigned long long s_off;
+    const unsigned long long n_raw = ctr->frontier_n[t];
+    const int64_t n = (int64_t)n_raw < cap ? (int64_t)n_raw : cap;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // exclusive prefix of the blocks before this one (and, in block 0, the total)
+    unsigned long long before = 0, total = 0;
+    for (int b = threadIdx.x; b < kCompactBlocks; b += blockDim.x) {
+        const unsigned long long v = ctr->block_count[b];
+        total += v;
+        if (b < (int)blockIdx.x) before += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+    }
+    __shared__ unsigned long long sb[8], st8[8];
+    if (lane == 0) {
+        sb[warp] = before;
+        st8[warp] = total;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, z = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sb[w];
+            z += st8[w];
+        }
+        s_off = a;
+        if (blockIdx.x == 0) {
+            ctr->level_boxes[t] = (unsigned long long)n;
+            atomicAdd(&ctr->boxes, (unsigned long long)n);
+            if (t < D) {
+                ctr->frontier_n[t + 1] = 2ull * z;
+                if ((int64_t)(2ull * z) > cap) atomicOr(status, kStatusOverflow);
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long off = s_off;
+    int64_t lo, hi;
+    compact_range(n, lo, hi);
+    unsigned long long n_unsafe = 0, n_safe = 0, n_und = 0;
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < hi;
+        const uint8_t c = valid ? cls[i] : (uint8_t)255;
+        const uint64_t code = valid ? codes_in[i] : 0ull;
+        const bool und = c == kUndecided;
+        const unsigned m_und = __ballot_sync(0xffffffffu, und);
+        n_unsafe += __popc(__ballot_sync(0xffffffffu, c == kUnsafe));
+        n_safe += __popc(__ballot_sync(0xffffffffu, c == kSafe));
+        n_und += __popc(m_und);
+        // in-block rank: warps in order
+        if (lane == 0) sh[warp] = __popc(m_und);
+        __syncthreads();
+        unsigned wbefore = 0, ctot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) wbefore += sh[w];
+            ctot += sh[w];
+        }
+        __syncthreads();
+        if (t < D && und) {
+            const int64_t pos = 2 * (int64_t)(off + wbefore + __popc(m_und & lt_mask));
+            if (pos + 1 < cap) {
+                codes_out[pos] = code << 1;
+                codes_out[pos + 1] = (code << 1) | 1ull;
+            }
+        }
+        off += ctot;
+        if (leaf_codes != nullptr) {
+            const bool leaf = (c == kUnsafe) || (c == kSafe) || (und && t == D);
+            const unsigned m_leaf = __ballot_sync(0xffffffffu, leaf);
+            unsigned long long slot = 0;
+            if (lane == 0 && m_leaf != 0u) slot = atomicAdd(&ctr->leaves, (unsigned long long)__popc(m_leaf));
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (leaf) {
+                const int64_t pos = (int64_t)slot + __popc(m_leaf & lt_mask);
+                if (pos < leaf_cap) {
+                    leaf_codes[pos] = code;
+                    leaf_depth[pos] = (uint8_t)t;
+                    leaf_cls[pos] = c;
+                } else {
+                    atomicOr(status, kStatusLeafOverflow);
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        if (n_unsafe) {
+            atomicAdd(&ctr->level_unsafe[t], n_unsafe);
+            atomicAdd(&ctr->unsafe_lo, n_unsafe << (D - t));
+        }
+        if (n_safe) atomicAdd(&ctr->level_safe[t], n_safe);
+        if (n_und) {
+            atomicAdd(&ctr->level_undecided[t], n_und);
+            if (t == D) atomicAdd(&ctr->undecided_at_D, n_und);
+        }
+    }
 }
 
 // ---- batched counting: many problems advance one level per step ------------
@@ -178,8 +315,10 @@ cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
                            uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
                            int64_t leaf_cap, int grid, cudaStream_t s) {
-    compact_kernel<<<grid, 256, 0, s>>>(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes,
-                                        leaf_depth, leaf_cls, leaf_cap);
+    (void)grid;
+    compact_count_kernel<<<kCompactBlocks, 256, 0, s>>>(cls, ctr, cap, t);
+    compact_kernel<<<kCompactBlocks, 256, 0, s>>>(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes,
+                                                  leaf_depth, leaf_cls, leaf_cap);
     return cudaGetLastError();
 }
 

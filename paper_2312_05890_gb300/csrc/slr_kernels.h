@@ -9,11 +9,12 @@
 namespace slr {
 
 // Tile sizes (boxes per CTA) the evaluation kernel is built for.
-constexpr int kTileSizes[] = {64, 32, 16, 8, 4};
+constexpr int kTileSizes[] = {64, 32, 20, 16, 12, 8, 4};
 constexpr int kThreadCounts[] = {256, 128};
 
 // Fused evaluation (kernel (b) plus its contraction); one instantiation per
-// working precision.  `T` must be one of kTileSizes and `NT` of kThreadCounts.
+// working precision.  `T` must be one of kTileSizes and `NT` of kThreadCounts
+// (tiles of 20 and 12 boxes exist in FP32 only).
 cudaError_t launch_eval_f32(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass);
 cudaError_t launch_eval_f64(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,

@@ -156,7 +156,7 @@ extern "C" int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out) {
         }
         NA_CK(slr::launch_compact(codes[t & 1], cls, codes[(t + 1) & 1], ctr, status, kFrontierCap, t, D, nullptr,
                                   nullptr, nullptr, 0, v.sm_count * 4, s));
-        ++launches;
+        launches += 2;
     }
     NA_CK(cudaEventRecord(v.ev1, s));
     slr::LevelCounters c;
