@@ -37,9 +37,16 @@ struct AdjSmem {
     float *m, *r;        // box centre and radius (d)
     float *lo, *hi;      // row bounds (R)
     float *glo, *ghi;    // upstream adjoints of the row bounds (R)
-    float *dm, *dr;      // box gradients (d)
     float *tmp;          // R x n_{K-1}: folded-layer weight gradient before unfolding
 };
+
+// Floats of one box's shared-memory state.
+__host__ __device__ inline size_t adj_box_floats(const AdjArgs &a) {
+    const size_t PQ = (size_t)a.n_max * (a.net.d + 1);
+    const size_t tmp = (size_t)a.net.R * (a.net.K > 1 ? a.net.n[a.net.K - 1] : a.net.d);
+    const size_t f = 8 * PQ + 5 * (size_t)a.H + 2 * (size_t)a.nck * PQ + 2 * (size_t)a.net.d + 4 * (size_t)a.net.R + tmp;
+    return (f + 3) & ~(size_t)3;
+}
 
 __device__ AdjSmem carve_adj(float *sp, const AdjArgs &a) {
     const int Q = a.net.d + 1;
@@ -61,11 +68,19 @@ __device__ AdjSmem carve_adj(float *sp, const AdjArgs &a) {
     s.hi = sp; sp += a.net.R;
     s.glo = sp; sp += a.net.R;
     s.ghi = sp; sp += a.net.R;
-    s.dm = sp; sp += a.net.d;
-    s.dr = sp; sp += a.net.d;
     s.tmp = sp;
     return s;
 }
+
+// The boxes a CTA works on together: box q (q < nb) at position pos0 + q,
+// its state at base + q * stride floats.
+struct Group {
+    float *base;
+    size_t stride;
+    int nb;
+    int64_t pos0;
+    __device__ __forceinline__ AdjSmem box(const AdjArgs &a, int q) const { return carve_adj(base + q * stride, a); }
+};
 
 // Weight w[p][i] of layer k (0-based, k = K-1 is the folded last layer).
 __device__ __forceinline__ float weight(const NetParams<float> &net, int k, int p, int i) {
@@ -79,14 +94,25 @@ __device__ __forceinline__ int hidden_offset(const NetParams<float> &net, int la
     return off;
 }
 
+__device__ __forceinline__ float *chk_u(const AdjArgs &a, const AdjSmem &s, int layer) {
+    return s.chk + (size_t)(layer - 1) * 2 * a.n_max * (a.net.d + 1);
+}
+__device__ __forceinline__ float *chk_l(const AdjArgs &a, const AdjSmem &s, int layer) {
+    return chk_u(a, s, layer) + (size_t)a.n_max * (a.net.d + 1);
+}
+
 // Layer 1 in the normalised box coordinates x = m + r * xi:
 // U = L = [W_1 diag(r) | W_1 m + b_1].
-__device__ void build_layer1(const AdjArgs &a, const AdjSmem &s, float *U, float *L) {
+__device__ void build_layer1(const AdjArgs &a, const Group &g) {
     const NetParams<float> &net = a.net;
     const int d = net.d, Q = d + 1, n1 = net.n[1];
-    for (int it = threadIdx.x; it < n1 * Q; it += blockDim.x) {
-        const int p = it % n1;
-        const int c = it / n1;
+    const int work = n1 * Q;
+    for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
+        const int q = it / work;
+        const int li = it - q * work;
+        const int p = li % n1;
+        const int c = li / n1;
+        const AdjSmem s = g.box(a, q);
         float v;
         if (c < d) {
             v = weight(net, 0, p, c) * s.r[c];
@@ -94,21 +120,27 @@ __device__ void build_layer1(const AdjArgs &a, const AdjSmem &s, float *U, float
             v = __ldg(net.b[0] + p);
             for (int i = 0; i < d; ++i) v = fmaf(weight(net, 0, p, i), s.m[i], v);
         }
-        U[p * Q + c] = v;
-        L[p * Q + c] = v;
+        s.U[p * Q + c] = v;
+        s.L[p * Q + c] = v;
     }
 }
 
 // Relaxation of hidden layer `layer` (Eq. 1, per-equation bounds) from its
-// pre-activation equations (U, L) and stored scalars, written as centre and
-// radius of the post-activation pair.
-__device__ void relax_layer(const AdjArgs &a, const AdjSmem &s, int layer, const float *U, const float *L) {
+// pre-activation equations and stored scalars, written as centre and radius
+// of the post-activation pair.  from_chk: read the kept copy of the layer.
+__device__ void relax_layer(const AdjArgs &a, const Group &g, int layer, bool from_chk) {
     const NetParams<float> &net = a.net;
     const int Q = net.d + 1, n = net.n[layer], H = a.H;
     const int off = hidden_offset(net, layer);
-    for (int it = threadIdx.x; it < n * Q; it += blockDim.x) {
-        const int j = it % n;
-        const int c = it / n;
+    const int work = n * Q;
+    for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
+        const int q = it / work;
+        const int li = it - q * work;
+        const int j = li % n;
+        const int c = li / n;
+        const AdjSmem s = g.box(a, q);
+        const float *U = from_chk ? chk_u(a, s, layer) : s.U;
+        const float *L = from_chk ? chk_l(a, s, layer) : s.L;
         const float ll = s.scal[off + j], ul = s.scal[H + off + j];
         const float lu = s.scal[2 * H + off + j], uu = s.scal[3 * H + off + j];
         const float al = s.scal[4 * H + off + j];
@@ -134,38 +166,64 @@ __device__ void relax_layer(const AdjArgs &a, const AdjSmem &s, int layer, const
     }
 }
 
+constexpr int kAdjCols = 8;   // equation columns one thread carries through a product
+
 // U' = W C + |W| Rr + b, L' = W C - |W| Rr + b for layer index k (0-based),
-// mapping the post-activation of hidden layer k to layer k + 1.
-__device__ void contract(const AdjArgs &a, const AdjSmem &s, int k, float *U, float *L) {
+// mapping the post-activation of hidden layer k to layer k + 1.  One item is
+// an output row of one box and up to kAdjCols columns (independent sums).
+__device__ void contract(const AdjArgs &a, const Group &g, int k) {
     const NetParams<float> &net = a.net;
     const int Q = net.d + 1, n_in = net.n[k], n_out = net.n[k + 1];
-    for (int it = threadIdx.x; it < n_out * Q; it += blockDim.x) {
-        const int p = it % n_out;
-        const int c = it / n_out;
-        float cc = c == net.d ? __ldg(net.b[k] + p) : 0.f, rr = 0.f;
+    const int nch = (Q + kAdjCols - 1) / kAdjCols;
+    const int work = n_out * nch;
+    for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
+        const int q = it / work;
+        const int li = it - q * work;
+        const int p = li % n_out;
+        const int c0 = (li / n_out) * kAdjCols;
+        const int nc = Q - c0 < kAdjCols ? Q - c0 : kAdjCols;
+        const AdjSmem s = g.box(a, q);
+        float cc[kAdjCols], rr[kAdjCols];
+#pragma unroll
+        for (int c = 0; c < kAdjCols; ++c) {
+            cc[c] = 0.f;
+            rr[c] = 0.f;
+        }
         for (int i = 0; i < n_in; ++i) {
             const float w = weight(net, k, p, i);
-            cc = fmaf(w, s.C[i * Q + c], cc);
-            rr = fmaf(fabsf(w), s.Rr[i * Q + c], rr);
+            const float aw = fabsf(w);
+            const float *ci = s.C + i * Q + c0, *ri = s.Rr + i * Q + c0;
+#pragma unroll
+            for (int c = 0; c < kAdjCols; ++c) {
+                if (c < nc) {
+                    cc[c] = fmaf(w, ci[c], cc[c]);
+                    rr[c] = fmaf(aw, ri[c], rr[c]);
+                }
+            }
         }
-        U[p * Q + c] = cc + rr;
-        L[p * Q + c] = cc - rr;
+        const float bp = __ldg(net.b[k] + p);
+#pragma unroll
+        for (int c = 0; c < kAdjCols; ++c) {
+            if (c < nc) {
+                const float cv = c0 + c == net.d ? cc[c] + bp : cc[c];
+                s.U[p * Q + c0 + c] = cv + rr[c];
+                s.L[p * Q + c0 + c] = cv - rr[c];
+            }
+        }
     }
 }
 
-__device__ __forceinline__ float *chk_u(const AdjArgs &a, const AdjSmem &s, int layer) {
-    return s.chk + (size_t)(layer - 1) * 2 * a.n_max * (a.net.d + 1);
-}
-__device__ __forceinline__ float *chk_l(const AdjArgs &a, const AdjSmem &s, int layer) {
-    return chk_u(a, s, layer) + (size_t)a.n_max * (a.net.d + 1);
-}
-
-// Concrete bounds of hidden layer `layer` and the slope each neuron uses.
-__device__ void concretize_layer(const AdjArgs &a, const AdjSmem &s, int layer, int64_t pos) {
+// Concrete bounds of hidden layer `layer` and the slope each neuron uses; the
+// layer's equations are kept when it is among the first nck.
+__device__ void concretize_layer(const AdjArgs &a, const Group &g, int layer) {
     const NetParams<float> &net = a.net;
     const int d = net.d, Q = d + 1, n = net.n[layer], H = a.H;
     const int off = hidden_offset(net, layer);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int it = threadIdx.x; it < g.nb * n; it += blockDim.x) {
+        const int q = it / n;
+        const int j = it - q * n;
+        const AdjSmem s = g.box(a, q);
+        const int64_t pos = g.pos0 + q;
         float su = 0.f, sl = 0.f;
         for (int c = 0; c < d; ++c) {
             su += fabsf(s.U[j * Q + c]);
@@ -187,27 +245,40 @@ __device__ void concretize_layer(const AdjArgs &a, const AdjSmem &s, int layer, 
         s.scal[3 * H + off + j] = uu;
         s.scal[4 * H + off + j] = al;
     }
+    if (layer <= a.nck) {
+        const int work = n * Q;
+        for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
+            const int q = it / work;
+            const int li = it - q * work;
+            const AdjSmem s = g.box(a, q);
+            chk_u(a, s, layer)[li] = s.U[li];
+            chk_l(a, s, layer)[li] = s.L[li];
+        }
+    }
 }
 
 // Recompute the pre-activation equations of hidden layer `layer` into (U, L)
 // from the nearest kept layer, with the scalars stored by the forward pass.
-__device__ void recompute(const AdjArgs &a, const AdjSmem &s, int layer) {
+__device__ void recompute(const AdjArgs &a, const Group &g, int layer) {
     int j = layer < a.nck ? layer : a.nck;
     if (j >= 1) {
-        const int PQ = a.net.n[j] * (a.net.d + 1);
-        for (int it = threadIdx.x; it < PQ; it += blockDim.x) {
-            s.U[it] = chk_u(a, s, j)[it];
-            s.L[it] = chk_l(a, s, j)[it];
+        const int work = a.net.n[j] * (a.net.d + 1);
+        for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
+            const int q = it / work;
+            const int li = it - q * work;
+            const AdjSmem s = g.box(a, q);
+            s.U[li] = chk_u(a, s, j)[li];
+            s.L[li] = chk_l(a, s, j)[li];
         }
     } else {
         j = 1;
-        build_layer1(a, s, s.U, s.L);
+        build_layer1(a, g);
     }
     __syncthreads();
     for (; j < layer; ++j) {
-        relax_layer(a, s, j, s.U, s.L);
+        relax_layer(a, g, j, false);
         __syncthreads();
-        contract(a, s, j, s.U, s.L);
+        contract(a, g, j);
         __syncthreads();
     }
 }
@@ -216,7 +287,7 @@ __device__ void recompute(const AdjArgs &a, const AdjSmem &s, int layer) {
 // (Sec. 3 check): SAFE needs every clause to have a row with hi < 0, so the
 // safe loss is sum_c max(0, min_{r in c} hi_r); UNSAFE needs some clause with
 // every lo_r >= 0, so the unsafe loss is min_c max(0, -min_{r in c} lo_r).
-// The direction is fixed at the first step.  Sets glo, ghi (thread 0).
+// The direction is fixed at the first step.  Sets glo, ghi.
 __device__ void decision_loss(const AdjArgs &a, const AdjSmem &s, int64_t pos) {
     const NetParams<float> &net = a.net;
     const int R = net.R;
@@ -261,23 +332,52 @@ __device__ void decision_loss(const AdjArgs &a, const AdjSmem &s, int64_t pos) {
     }
 }
 
+// Folded-layer weight gradients (R rows) of one box, unfolded with the
+// property rows: dW_K = C^T dW', db_K = C^T db'.
+__device__ void unfold_add(const AdjArgs &a, const AdjSmem &s, int n_in, float *dW, float *db, int lane, int nl) {
+    const int R = a.net.R, no = a.n_out, Q = a.net.d + 1;
+    for (int it = lane; it < no * n_in; it += nl) {
+        const int o = it / n_in;
+        const int i = it - o * n_in;
+        float v = 0.f;
+        for (int r = 0; r < R; ++r) v = fmaf(__ldg(a.Cprop + r * no + o), s.tmp[r * n_in + i], v);
+        atomicAdd(dW + it, v);
+    }
+    for (int o = lane; o < no; o += nl) {
+        float v = 0.f;
+        for (int r = 0; r < R; ++r) v = fmaf(__ldg(a.Cprop + r * no + o), s.gA[r * Q + a.net.d], v);
+        atomicAdd(db + o, v);
+    }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
     extern __shared__ __align__(16) float smem_adj[];
-    const AdjSmem s = carve_adj(smem_adj, a);
     const NetParams<float> &net = a.net;
     const int K = net.K, d = net.d, Q = d + 1, R = net.R, H = a.H;
+    const int B = a.boxes_per_cta;
+    const size_t stride = adj_box_floats(a);
 
     int64_t n = a.n;
     if (a.count != nullptr) {
         const int64_t c = (int64_t)*a.count;
         n = c < n ? c : n;
     }
-    for (int64_t pos = blockIdx.x; pos < n; pos += gridDim.x) {
-        // ---- the box: centre and radius (Sec. 2.2 bisection for path codes) ----
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    for (int64_t pos0 = (int64_t)blockIdx.x * B; pos0 < n; pos0 += (int64_t)gridDim.x * B) {
+        Group g;
+        g.base = smem_adj;
+        g.stride = stride;
+        g.pos0 = pos0;
+        g.nb = (int)((n - pos0) < B ? (n - pos0) : B);
+
+        // ---- the boxes: centre and radius (Sec. 2.2 bisection for path codes) ----
+        for (int it = threadIdx.x; it < g.nb * d; it += blockDim.x) {
+            const int q = it / d;
+            const int i = it - q * d;
+            const AdjSmem s = g.box(a, q);
             const BoxSource &src = a.src;
+            const int64_t pos = pos0 + q;
             const int64_t idx = src.index != nullptr ? src.index[pos] : pos;
             double m64, r64;
             if (src.mode == 0) {
@@ -296,31 +396,26 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             }
             s.m[i] = (float)m64;
             s.r[i] = (float)r64;
-            s.dm[i] = 0.f;
-            s.dr[i] = 0.f;
         }
         __syncthreads();
 
         // ---- forward: equations, concrete bounds and slopes of every layer ----
-        build_layer1(a, s, s.U, s.L);
+        build_layer1(a, g);
         __syncthreads();
         for (int k = 1; k < K; ++k) {
-            concretize_layer(a, s, k, pos);
-            if (k <= a.nck) {
-                const int PQ = net.n[k] * Q;
-                for (int it = threadIdx.x; it < PQ; it += blockDim.x) {
-                    chk_u(a, s, k)[it] = s.U[it];
-                    chk_l(a, s, k)[it] = s.L[it];
-                }
-            }
+            concretize_layer(a, g, k);
             __syncthreads();
-            relax_layer(a, s, k, s.U, s.L);
+            relax_layer(a, g, k, false);
             __syncthreads();
-            contract(a, s, k, s.U, s.L);
+            contract(a, g, k);
             __syncthreads();
         }
-        // row bounds of the folded last layer
-        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        // row bounds of the folded last layer and their upstream adjoints
+        for (int it = threadIdx.x; it < g.nb * R; it += blockDim.x) {
+            const int q = it / R;
+            const int r = it - q * R;
+            const AdjSmem s = g.box(a, q);
+            const int64_t pos = pos0 + q;
             float su = 0.f, sl = 0.f;
             for (int c = 0; c < d; ++c) {
                 su += fabsf(s.U[r * Q + c]);
@@ -339,36 +434,35 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
         }
         __syncthreads();
         if (a.g_lo == nullptr) {
-            if (threadIdx.x == 0) decision_loss(a, s, pos);
+            for (int q = threadIdx.x; q < g.nb; q += blockDim.x) decision_loss(a, g.box(a, q), pos0 + q);
             __syncthreads();
         }
         // d lo_r = d (L_r,d - sum |L_r,c|), d hi_r = d (U_r,d + sum |U_r,c|)
-        for (int it = threadIdx.x; it < R * Q; it += blockDim.x) {
-            const int r = it / Q;
-            const int c = it - r * Q;
-            s.gA[it] = c == d ? s.ghi[r] : s.ghi[r] * sgnf(s.U[it]);
-            s.gB[it] = c == d ? s.glo[r] : -s.glo[r] * sgnf(s.L[it]);
+        for (int it = threadIdx.x; it < g.nb * R * Q; it += blockDim.x) {
+            const int q = it / (R * Q);
+            const int li = it - q * R * Q;
+            const int r = li / Q;
+            const int c = li - r * Q;
+            const AdjSmem s = g.box(a, q);
+            s.gA[li] = c == d ? s.ghi[r] : s.ghi[r] * sgnf(s.U[li]);
+            s.gB[li] = c == d ? s.glo[r] : -s.glo[r] * sgnf(s.L[li]);
         }
         __syncthreads();
 
         // ---- backward sweep: contraction k maps hidden layer k to layer k + 1 ----
         for (int k = K - 1; k >= 1; --k) {
             const int n_in = net.n[k], n_out = net.n[k + 1];
-            const float *Uk, *Lk;
-            if (k <= a.nck) {
-                Uk = chk_u(a, s, k);
-                Lk = chk_l(a, s, k);
-            } else {
-                recompute(a, s, k);
-                Uk = s.U;
-                Lk = s.L;
-            }
-            relax_layer(a, s, k, Uk, Lk);
+            const bool kept = k <= a.nck;
+            if (!kept) recompute(a, g, k);
+            relax_layer(a, g, k, kept);
             // (gU', gL') -> (gC', gR') = (gU' + gL', gU' - gL')
-            for (int it = threadIdx.x; it < n_out * Q; it += blockDim.x) {
-                const float u = s.gA[it], l = s.gB[it];
-                s.gA[it] = u + l;
-                s.gB[it] = u - l;
+            for (int it = threadIdx.x; it < g.nb * n_out * Q; it += blockDim.x) {
+                const int q = it / (n_out * Q);
+                const int li = it - q * n_out * Q;
+                const AdjSmem s = g.box(a, q);
+                const float u = s.gA[li], l = s.gB[li];
+                s.gA[li] = u + l;
+                s.gB[li] = u - l;
             }
             __syncthreads();
             // weight and bias gradients: dW[p][i] = sum_c gC'[p,c] C[i,c] + sgn(W) gR'[p,c] Rr[i,c]
@@ -378,49 +472,74 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
                     const int p = it / n_in;
                     const int i = it - p * n_in;
                     const float sw = sgnf(weight(net, k, p, i));
-                    float v = 0.f;
-                    for (int c = 0; c < Q; ++c)
-                        v = fmaf(s.gA[p * Q + c], s.C[i * Q + c], fmaf(sw * s.gB[p * Q + c], s.Rr[i * Q + c], v));
-                    if (last) s.tmp[it] = v;
-                    else atomicAdd(a.dW[k] + it, v);
+                    float acc = 0.f;
+                    for (int q = 0; q < g.nb; ++q) {
+                        const AdjSmem s = g.box(a, q);
+                        float v = 0.f;
+                        for (int c = 0; c < Q; ++c)
+                            v = fmaf(s.gA[p * Q + c], s.C[i * Q + c], fmaf(sw * s.gB[p * Q + c], s.Rr[i * Q + c], v));
+                        if (last) s.tmp[it] = v;
+                        acc += v;
+                    }
+                    if (!last) atomicAdd(a.dW[k] + it, acc);
                 }
                 if (!last) {
-                    for (int p = threadIdx.x; p < n_out; p += blockDim.x) atomicAdd(a.db[k] + p, s.gA[p * Q + d]);
+                    for (int p = threadIdx.x; p < n_out; p += blockDim.x) {
+                        float acc = 0.f;
+                        for (int q = 0; q < g.nb; ++q) acc += g.box(a, q).gA[p * Q + d];
+                        atomicAdd(a.db[k] + p, acc);
+                    }
                 } else {
-                    // the folded rows are C W_K: dW_K = C^T dW', db_K = C^T db'
                     __syncthreads();
-                    const int no = a.n_out;
-                    for (int it = threadIdx.x; it < no * n_in; it += blockDim.x) {
-                        const int o = it / n_in;
-                        const int i = it - o * n_in;
-                        float v = 0.f;
-                        for (int r = 0; r < R; ++r) v = fmaf(__ldg(a.Cprop + r * no + o), s.tmp[r * n_in + i], v);
-                        atomicAdd(a.dW[k] + it, v);
-                    }
-                    for (int o = threadIdx.x; o < no; o += blockDim.x) {
-                        float v = 0.f;
-                        for (int r = 0; r < R; ++r) v = fmaf(__ldg(a.Cprop + r * no + o), s.gA[r * Q + d], v);
-                        atomicAdd(a.db[k] + o, v);
-                    }
+                    for (int q = 0; q < g.nb; ++q) unfold_add(a, g.box(a, q), n_in, a.dW[k], a.db[k], threadIdx.x,
+                                                              blockDim.x);
                 }
             }
             // adjoints of the post-relaxation pair: gU^ = (W^T gC' + |W|^T gR') / 2, gL^ = (W^T gC' - |W|^T gR') / 2
-            for (int it = threadIdx.x; it < n_in * Q; it += blockDim.x) {
-                const int i = it % n_in;
-                const int c = it / n_in;
-                float gc = 0.f, gr = 0.f;
+            const int nch = (Q + kAdjCols - 1) / kAdjCols;
+            for (int it = threadIdx.x; it < g.nb * n_in * nch; it += blockDim.x) {
+                const int q = it / (n_in * nch);
+                const int li = it - q * n_in * nch;
+                const int i = li % n_in;
+                const int c0 = (li / n_in) * kAdjCols;
+                const int nc = Q - c0 < kAdjCols ? Q - c0 : kAdjCols;
+                const AdjSmem s = g.box(a, q);
+                float gc[kAdjCols], gr[kAdjCols];
+#pragma unroll
+                for (int c = 0; c < kAdjCols; ++c) {
+                    gc[c] = 0.f;
+                    gr[c] = 0.f;
+                }
                 for (int p = 0; p < n_out; ++p) {
                     const float w = weight(net, k, p, i);
-                    gc = fmaf(w, s.gA[p * Q + c], gc);
-                    gr = fmaf(fabsf(w), s.gB[p * Q + c], gr);
+                    const float aw = fabsf(w);
+                    const float *ap = s.gA + p * Q + c0, *bp = s.gB + p * Q + c0;
+#pragma unroll
+                    for (int c = 0; c < kAdjCols; ++c) {
+                        if (c < nc) {
+                            gc[c] = fmaf(w, ap[c], gc[c]);
+                            gr[c] = fmaf(aw, bp[c], gr[c]);
+                        }
+                    }
                 }
-                s.gX[i * Q + c] = 0.5f * (gc + gr);
-                s.gY[i * Q + c] = 0.5f * (gc - gr);
+#pragma unroll
+                for (int c = 0; c < kAdjCols; ++c) {
+                    if (c < nc) {
+                        s.gX[i * Q + c0 + c] = 0.5f * (gc[c] + gr[c]);
+                        s.gY[i * Q + c0 + c] = 0.5f * (gc[c] - gr[c]);
+                    }
+                }
             }
             __syncthreads();
             // through the relaxation (Eq. 1) of hidden layer k, one neuron per thread
             const int off = hidden_offset(net, k);
-            for (int j = threadIdx.x; j < n_in; j += blockDim.x) {
+            for (int it = threadIdx.x; it < g.nb * n_in; it += blockDim.x) {
+                const int q = it / n_in;
+                const int j = it - q * n_in;
+                const AdjSmem s = g.box(a, q);
+                const int64_t pos = pos0 + q;
+                const float *Uk = kept ? chk_u(a, s, k) : s.U;
+                const float *Lk = kept ? chk_l(a, s, k) : s.L;
                 const float ll = s.scal[off + j], ul = s.scal[H + off + j];
                 const float lu = s.scal[2 * H + off + j], uu = s.scal[3 * H + off + j];
                 const float al = s.scal[4 * H + off + j];
@@ -488,42 +607,52 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
         }
 
         // ---- layer 1: U = L = [W_1 diag(r) | W_1 m + b_1] ----
-        for (int it = threadIdx.x; it < net.n[1] * Q; it += blockDim.x) s.gA[it] += s.gB[it];
-        __syncthreads();
         const int n1 = net.n[1];
+        for (int it = threadIdx.x; it < g.nb * n1 * Q; it += blockDim.x) {
+            const int q = it / (n1 * Q);
+            const int li = it - q * n1 * Q;
+            const AdjSmem s = g.box(a, q);
+            s.gA[li] += s.gB[li];
+        }
+        __syncthreads();
         if (a.dW[0] != nullptr) {
             if (K > 1) {
                 for (int it = threadIdx.x; it < n1 * d; it += blockDim.x) {
                     const int p = it / d;
                     const int i = it - p * d;
-                    atomicAdd(a.dW[0] + it, fmaf(s.gA[p * Q + i], s.r[i], s.gA[p * Q + d] * s.m[i]));
+                    float acc = 0.f;
+                    for (int q = 0; q < g.nb; ++q) {
+                        const AdjSmem s = g.box(a, q);
+                        acc += fmaf(s.gA[p * Q + i], s.r[i], s.gA[p * Q + d] * s.m[i]);
+                    }
+                    atomicAdd(a.dW[0] + it, acc);
                 }
-                for (int p = threadIdx.x; p < n1; p += blockDim.x) atomicAdd(a.db[0] + p, s.gA[p * Q + d]);
+                for (int p = threadIdx.x; p < n1; p += blockDim.x) {
+                    float acc = 0.f;
+                    for (int q = 0; q < g.nb; ++q) acc += g.box(a, q).gA[p * Q + d];
+                    atomicAdd(a.db[0] + p, acc);
+                }
             } else {
                 // a single affine layer is the folded one: unfold with the property rows
-                for (int it = threadIdx.x; it < R * d; it += blockDim.x) {
-                    const int r = it / d;
-                    const int i = it - r * d;
-                    s.tmp[it] = fmaf(s.gA[r * Q + i], s.r[i], s.gA[r * Q + d] * s.m[i]);
+                for (int q = 0; q < g.nb; ++q) {
+                    const AdjSmem s = g.box(a, q);
+                    for (int it = threadIdx.x; it < R * d; it += blockDim.x) {
+                        const int r = it / d;
+                        const int i = it - r * d;
+                        s.tmp[it] = fmaf(s.gA[r * Q + i], s.r[i], s.gA[r * Q + d] * s.m[i]);
+                    }
                 }
                 __syncthreads();
-                const int no = a.n_out;
-                for (int it = threadIdx.x; it < no * d; it += blockDim.x) {
-                    const int o = it / d;
-                    const int i = it - o * d;
-                    float v = 0.f;
-                    for (int r = 0; r < R; ++r) v = fmaf(__ldg(a.Cprop + r * no + o), s.tmp[r * d + i], v);
-                    atomicAdd(a.dW[0] + it, v);
-                }
-                for (int o = threadIdx.x; o < no; o += blockDim.x) {
-                    float v = 0.f;
-                    for (int r = 0; r < R; ++r) v = fmaf(__ldg(a.Cprop + r * no + o), s.gA[r * Q + d], v);
-                    atomicAdd(a.db[0] + o, v);
-                }
+                for (int q = 0; q < g.nb; ++q) unfold_add(a, g.box(a, q), d, a.dW[0], a.db[0], threadIdx.x,
+                                                          blockDim.x);
             }
         }
         if (a.d_lo != nullptr) {
-            for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            for (int it = threadIdx.x; it < g.nb * d; it += blockDim.x) {
+                const int q = it / d;
+                const int i = it - q * d;
+                const AdjSmem s = g.box(a, q);
+                const int64_t pos = pos0 + q;
                 float gr = 0.f, gm = 0.f;
                 for (int p = 0; p < n1; ++p) {
                     const float w = weight(net, 0, p, i);
@@ -601,12 +730,8 @@ __global__ void slr_gather_undecided_kernel(const uint8_t *cls, const unsigned l
     }
 }
 
-size_t adjoint_smem_bytes(const AdjArgs &a) {
-    const size_t PQ = (size_t)a.n_max * (a.net.d + 1);
-    const size_t tmp = (size_t)a.net.R * a.net.n[a.net.K - 1];
-    return sizeof(float) * (8 * PQ + 5 * (size_t)a.H + 2 * (size_t)a.nck * PQ + 4 * (size_t)a.net.d +
-                            4 * (size_t)a.net.R + tmp);
-}
+size_t adjoint_smem_bytes(const AdjArgs &a) { return sizeof(float) * adj_box_floats(a) * (size_t)a.boxes_per_cta; }
+
 
 cudaError_t launch_adjoint(const AdjArgs &a, int grid, cudaStream_t s) {
     const size_t smem = adjoint_smem_bytes(a);

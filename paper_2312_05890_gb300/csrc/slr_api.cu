@@ -87,7 +87,7 @@ struct slr_ctx {
     int tuned_T = 0, tuned_NT = 0;
     const float *dC = nullptr;            // property rows on the device (inside net_buf)
     int64_t H = 0;                        // hidden neurons (slope row length)
-    int adj_nck = 0, adj_grid = 0, adj_nmax = 0;
+    int adj_nck = 0, adj_grid = 0, adj_nmax = 0, adj_boxes = 1;
     size_t adj_smem = 0;
     void *alpha_buf = nullptr;            // slope optimisation during a count
     size_t alpha_buf_bytes = 0;
@@ -730,6 +730,9 @@ int prepare_device(slr_ctx *ctx) {
         for (int k = 1; k < ctx->K; ++k) a.H += ctx->widths[k];
         a.n_max = 0;
         for (int k = 1; k <= ctx->K; ++k) a.n_max = std::max(a.n_max, ctx->nf.n[k]);
+        // keep as many hidden layers' equations as fit 96 KB for one box, then
+        // put as many boxes in a CTA as fit about 110 KB (at most 8)
+        a.boxes_per_cta = 1;
         a.nck = 0;
         while (a.nck < ctx->K - 1) {
             a.nck += 1;
@@ -738,9 +741,12 @@ int prepare_device(slr_ctx *ctx) {
                 break;
             }
         }
+        const size_t one = slr::adjoint_smem_bytes(a);
+        a.boxes_per_cta = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(110 * 1024) / std::max<size_t>(1, one)));
         ctx->H = a.H;
         ctx->adj_nmax = a.n_max;
         ctx->adj_nck = a.nck;
+        ctx->adj_boxes = a.boxes_per_cta;
         ctx->adj_smem = slr::adjoint_smem_bytes(a);
         const int nb = ctx->adj_smem <= (size_t)kMaxSmem ? slr::adjoint_blocks_per_sm(ctx->adj_smem) : 0;
         ctx->adj_grid = nb * ctx->sm_count;
@@ -1855,6 +1861,7 @@ slr::AdjArgs adj_base(const slr_ctx *ctx) {
     a.H = ctx->H;
     a.n_max = ctx->adj_nmax;
     a.nck = ctx->adj_nck;
+    a.boxes_per_cta = ctx->adj_boxes;
     a.Cprop = ctx->dC;
     a.n_out = ctx->widths[ctx->K];
     a.lr = 0.f;
@@ -1942,7 +1949,8 @@ int optimise_slopes(slr_ctx *ctx, const slr::BoxSource &src, int64_t cap, const 
                                      steps == 0 ? cls_pos : nullptr, steps == 0 ? cls_idx : nullptr, src.index, 1,
                                      steps == 0 ? decided : nullptr, ctx->stream));
     *launches += 2;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, ctx->adj_grid));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((cap + ctx->adj_boxes - 1) / ctx->adj_boxes,
+                                                                 ctx->adj_grid));
     slr::AdjArgs a = adj_base(ctx);
     a.src = src;
     a.n = cap;
@@ -2117,7 +2125,7 @@ int slr_margin_backward(slr_ctx *ctx, int64_t n, const float *box_lo, const floa
             a.dW[k] = dW[k];
             a.db[k] = db[k];
         }
-        const int grid = (int)std::min<int64_t>(n, ctx->adj_grid);
+        const int grid = (int)std::min<int64_t>((n + ctx->adj_boxes - 1) / ctx->adj_boxes, ctx->adj_grid);
         CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
     }
     if (!on_device) {

@@ -63,6 +63,7 @@ struct AdjArgs {
     int64_t H;                      // hidden neurons (row length of the slope arrays)
     int n_max;                      // widest layer n[1..K]
     int nck;                        // hidden layers whose equations stay in shared memory
+    int boxes_per_cta;              // boxes a CTA works on together
     int alpha_mode;                 // kAlphaDefault: u/(u-l), differentiated through; kAlphaFree: read;
                                     // kAlphaInit: write u/(u-l) to alpha, then treat it as free
     float *alpha;                   // n x H
