@@ -389,7 +389,7 @@ int build_tc(slr_ctx *ctx, const HostLayers<float> &L) {
     for (int k = 1; k < K; ++k) tp.img[k] = (const unsigned char *)ctx->tc_buf + offs[k];
     // the most boxes per CTA whose B operand fits N <= 256 and shared memory
     ctx->T_tc = 0;
-    for (int T : slr::kTileSizes) {
+    for (int T : slr::kTcTileSizes) {
         slr::TcParams t2 = tp;
         t2.Npad = (tp.NCg * T + 15) & ~15;
         if (t2.Npad > 256) continue;

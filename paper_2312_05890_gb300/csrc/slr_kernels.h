@@ -10,6 +10,8 @@ namespace slr {
 
 // Tile sizes (boxes per CTA) the evaluation kernel is built for.
 constexpr int kTileSizes[] = {64, 32, 20, 16, 12, 8, 4};
+// Tile sizes of the tensor-core tile kernel.
+constexpr int kTcTileSizes[] = {64, 32, 16, 8, 4};
 constexpr int kThreadCounts[] = {256, 128};
 
 // Fused evaluation (kernel (b) plus its contraction); one instantiation per
