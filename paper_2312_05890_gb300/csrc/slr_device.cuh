@@ -187,6 +187,13 @@ struct BatchShape {
 // constant (hi), R coefficients, R constant, N, E, C constant (lo).
 __host__ __device__ inline int state_cols(int d) { return 2 * d + 5; }
 
+// Row stride of a tile's state: T (2d + 5) floats padded so that it is T modulo
+// 32, i.e. a warp's (row, box) items of consecutive rows fall in distinct banks.
+__host__ __device__ inline int state_stride(int T, int d) {
+    const int ns = T * state_cols(d);
+    return ns + (((T - ns) % 32) + 32) % 32;
+}
+
 // Contraction tiles (8 rows x 4 columns) per CTA of the fused kernel; each of
 // its threads holds at most two in registers, so this must not exceed 2 x 256.
 __host__ __device__ inline int eval_gemm_items(int T, int d, int n_max_pad) {
@@ -196,7 +203,7 @@ __host__ __device__ inline int eval_gemm_items(int T, int d, int n_max_pad) {
 // Shared-memory footprint of the fused evaluation kernel for a tile of T boxes.
 template <typename Real>
 __host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max_pad, int n_in_max) {
-    const int NS = T * state_cols(d);
+    const int NS = state_stride(T, d);
     size_t s = 0;
     s += (size_t)n_max_pad * NS * sizeof(Real);            // state, updated in place
     s += 3 * (size_t)n_max_pad * T * sizeof(Real);         // next layer's constants (hi, lo, error)

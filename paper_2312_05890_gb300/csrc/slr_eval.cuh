@@ -2,25 +2,26 @@
 //
 // One CTA takes a tile of T boxes and carries their symbolic state through all
 // layers without leaving the SM:
-//   decode     path code -> box centre m and radius r (outward to Real)
-//   layer 1    C = [W_1 diag(r) | W_1 m + b_1], R = [0 | rounding error]
+//   decode     path code -> box centre m (float-float) and radius r, outward
+//   layer 1    C = [W_1 diag(r) | W_1 m + b_1], R = 0, error E of the rounding
 //   per hidden layer k:
-//     widen    add the a-priori error of the contraction that produced it
+//     finish   constant and error of the contraction that produced the layer
 //     bounds   concrete bounds of both equations over the box (Sec. 2.2):
-//              max/min of (C +- R) = const +- sum_j |coeff_j|, directed rounding
+//              max/min of (C +- R) = const +- sum_j |coeff_j|, outward
 //     relax    ReLU relaxation, Eq. 1 (per-equation or one-pair reading)
+//     offsets  (float) the constant of every box as box 0's plus an offset
 //     contract C' = W C + b, R' = |W| R (the per-layer symbolic matrix product)
 //   last layer the property rows are folded into W_K; row bounds lo_r, hi_r
 //   classify  Sec. 3 containment check: UNSAFE / SAFE / UNDECIDED, and flag
 //              undecided boxes whose margins lie within the rounding budget.
 //
 // State layout in shared memory: element (row p, column c, box b) at
-// S[p * NS + c * T + b] with NS = T * (2d + 3).  Columns 0..d hold C (d
-// coefficients, then the constant), d+1..2d+1 hold R, 2d+2 holds the row
-// magnitude N = sum |C| + sum |R| (used by the next layer's error bound).
-// Boxes are the fastest index so that a warp reads one column of 32 boxes
-// (or 32/T rows of T boxes; NS/T = 2d+3 is odd, so those rows fall in distinct
-// banks) without bank conflicts.
+// S[p * NS + c * T + b], NS = state_stride(T, d) >= T (2d + 5).  Columns:
+// C coefficients (0..d-1), C constant (high part, d), R coefficients
+// (d+1..2d), R constant (2d+1), N = magnitude of the row's product columns
+// (2d+2), E = error bound (2d+3), C constant low part (2d+4).  Boxes are the
+// fastest index so that a warp reads one column of 32 boxes; NS is T modulo
+// 32, so a warp's items of consecutive rows fall in distinct banks.
 #pragma once
 
 #include "slr_device.cuh"
@@ -812,7 +813,7 @@ struct TileSmem {
 template <typename Real, int T>
 __device__ __forceinline__ TileSmem<Real> carve_smem(unsigned char *sp, int nmp, int d, int n_in_max, int R) {
     TileSmem<Real> m;
-    const int NS = T * state_cols(d);
+    const int NS = state_stride(T, d);
     m.sS = reinterpret_cast<Real *>(sp);
     sp += (size_t)nmp * NS * sizeof(Real);
     m.sConst = reinterpret_cast<Real *>(sp);
@@ -863,7 +864,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
     using Tile = EvalTile<Real, T, NT, KI>;
     const int d = net.d;
     const int R = net.R;
-    const int NS = T * state_cols(d);
+    const int NS = state_stride(T, d);
     Real *sS = sm.sS, *sConst = sm.sConst, *sW = sm.sW, *sMh = sm.sMh, *sMl = sm.sMl, *sR = sm.sR;
     Real *sLo = sm.sLo, *sHi = sm.sHi, *sErr = sm.sErr;
     int64_t *sIdx = sm.sIdx;
