@@ -40,9 +40,10 @@ L2_FLUSH_BYTES = 512 << 20          # written between timed steps (> 129 MB L2)
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 / BF16 tensor rates of GB300
 
 # DRAM bytes per box of the FP32 evaluation kernel from one ncu capture of the
-# kernel source hashed below (profiles/slr_eval_f32_acas.md); reported as
-# roofline.traffic only while the kernel source is unchanged.
-TRAFFIC = {"source_sha": "533f19481a9bfa0a", "bytes_per_box": 8.4}
+# kernel source hashed below (profiles/slr_eval_f32_acas_D20.md: levels 18 and
+# 19, 8.50 and 8.25 B per box); reported as roofline.traffic only while the
+# kernel source is unchanged.
+TRAFFIC = {"source_sha": "f91e5c12d95f0fc9", "bytes_per_box": 8.3}
 KERNEL_SOURCES = ["paper_2312_05890_gb300/csrc/slr_eval.cuh", "paper_2312_05890_gb300/csrc/slr_eval_f32.cu",
                   "paper_2312_05890_gb300/csrc/slr_device.cuh"]
 
