@@ -352,12 +352,17 @@ __device__ void unfold_add(const AdjArgs &a, const AdjSmem &s, int n_in, float *
 
 }  // namespace
 
+// kGlobal: the boxes' state in global memory (a.gscratch) instead of shared
+// memory; two instantiations so that the shared one keeps shared-memory
+// instructions.
+template <bool kGlobal>
 __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
     extern __shared__ __align__(16) float smem_adj[];
     const NetParams<float> &net = a.net;
     const int K = net.K, d = net.d, Q = d + 1, R = net.R, H = a.H;
     const int B = a.boxes_per_cta;
     const size_t stride = adj_box_floats(a);
+    float *const state = kGlobal ? a.gscratch + (size_t)blockIdx.x * B * stride : smem_adj;
 
     int64_t n = a.n;
     if (a.count != nullptr) {
@@ -366,7 +371,7 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
     }
     for (int64_t pos0 = (int64_t)blockIdx.x * B; pos0 < n; pos0 += (int64_t)gridDim.x * B) {
         Group g;
-        g.base = smem_adj;
+        g.base = state;
         g.stride = stride;
         g.pos0 = pos0;
         g.nb = (int)((n - pos0) < B ? (n - pos0) : B);
@@ -730,21 +735,31 @@ __global__ void slr_gather_undecided_kernel(const uint8_t *cls, const unsigned l
     }
 }
 
-size_t adjoint_smem_bytes(const AdjArgs &a) { return sizeof(float) * adj_box_floats(a) * (size_t)a.boxes_per_cta; }
+size_t adjoint_box_bytes(const AdjArgs &a) { return sizeof(float) * adj_box_floats(a); }
+
+size_t adjoint_smem_bytes(const AdjArgs &a) {
+    return a.gscratch != nullptr ? 0 : sizeof(float) * adj_box_floats(a) * (size_t)a.boxes_per_cta;
+}
 
 
 cudaError_t launch_adjoint(const AdjArgs &a, int grid, cudaStream_t s) {
+    if (a.gscratch != nullptr) {
+        slr_adjoint_kernel<true><<<grid, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const size_t smem = adjoint_smem_bytes(a);
-    cudaError_t e = cudaFuncSetAttribute(slr_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(slr_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    slr_adjoint_kernel<<<grid, 256, smem, s>>>(a);
+    slr_adjoint_kernel<false><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 int adjoint_blocks_per_sm(size_t smem) {
     int nb = 0;
-    cudaFuncSetAttribute(slr_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, slr_adjoint_kernel, 256, smem) != cudaSuccess) return 0;
+    cudaFuncSetAttribute(slr_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, slr_adjoint_kernel<false>, 256, smem) != cudaSuccess)
+        return 0;
     return nb;
 }
 

@@ -88,6 +88,9 @@ struct slr_ctx {
     const float *dC = nullptr;            // property rows on the device (inside net_buf)
     int64_t H = 0;                        // hidden neurons (slope row length)
     int adj_nck = 0, adj_grid = 0, adj_nmax = 0, adj_boxes = 1;
+    bool adj_gmem = false;                // adjoint state in global memory (wide networks)
+    void *adj_scratch = nullptr;
+    size_t adj_scratch_bytes = 0;
     size_t adj_smem = 0;
     void *alpha_buf = nullptr;            // slope optimisation during a count
     size_t alpha_buf_bytes = 0;
@@ -600,7 +603,8 @@ int run_wide(slr_ctx *ctx, const slr::BoxSource &src, int64_t n, const slr::Eval
         const int nb = (int)std::min<int64_t>((int64_t)bc, n - base);
         CK(ctx, slr::launch_wide_box(src, base, nb, d, mh, ml, rr, bidx, sms, ctx->stream));
         int cur = 0;
-        CK(ctx, slr::launch_wide_init(nf, ctx->w0t, nb, np, mh, ml, rr, Cb[cur], Rb[cur], Ch, Cl, ctx->stream));
+        CK(ctx, slr::launch_wide_init(nf, ctx->w0t, nb, np, mh, ml, rr, Cb[cur], Rb[cur], Ch, Cl, src.alpha,
+                                      src.alpha_ld, base, ctx->stream));
         *launches += 2;
         for (int k = 1; k < K; ++k) {
             const int nxt = cur ^ 1;
@@ -629,8 +633,8 @@ int run_wide(slr_ctx *ctx, const slr::BoxSource &src, int64_t n, const slr::Eval
             CK(ctx, slr::launch_wide_const(nf, k, nb, np, Ch, Cl, Rb[cur], Kh, Kl, Ke, sms, ctx->stream));
             const float g = slr::tc_gamma(ctx->w_Kpad[k]);
             if (k + 1 < K) {
-                CK(ctx, slr::launch_wide_hidden(nf, k + 1, nb, np, g, Cb[nxt], Rb[nxt], Ch, Cl, Kh, Kl, Ke,
-                                                ctx->stream));
+                CK(ctx, slr::launch_wide_hidden(nf, k + 1, nb, np, g, Cb[nxt], Rb[nxt], Ch, Cl, Kh, Kl, Ke, src.alpha,
+                                                src.alpha_ld, base, ctx->stream));
             } else {
                 CK(ctx, slr::launch_wide_final(nf, nb, np, g, Cb[nxt], Rb[nxt], Ch, Cl, Kh, Kl, Ke, lo, hi, er,
                                                ctx->stream));
@@ -688,7 +692,22 @@ int prepare_device(slr_ctx *ctx) {
         ctx->tc_ok = false;
         ctx->H = 0;
         for (int k = 1; k < ctx->K; ++k) ctx->H += ctx->widths[k];
-        ctx->adj_grid = 0;
+        // adjoint: one box per CTA, every hidden layer kept, state in global
+        // memory (up to about 4 GB of CTA slots)
+        slr::AdjArgs a{};
+        a.net = ctx->nf;
+        a.H = ctx->H;
+        a.n_max = 0;
+        for (int k = 1; k <= ctx->K; ++k) a.n_max = std::max(a.n_max, ctx->nf.n[k]);
+        a.nck = ctx->K - 1;
+        a.boxes_per_cta = 1;
+        const size_t box = slr::adjoint_box_bytes(a);
+        ctx->adj_nmax = a.n_max;
+        ctx->adj_nck = a.nck;
+        ctx->adj_boxes = 1;
+        ctx->adj_smem = 0;
+        ctx->adj_gmem = true;
+        ctx->adj_grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)2 * ctx->sm_count, ((size_t)4 << 30) / box));
         ctx->dev_dirty = false;
         return SLR_OK;
     }
@@ -747,6 +766,7 @@ int prepare_device(slr_ctx *ctx) {
         ctx->adj_nmax = a.n_max;
         ctx->adj_nck = a.nck;
         ctx->adj_boxes = a.boxes_per_cta;
+        ctx->adj_gmem = false;
         ctx->adj_smem = slr::adjoint_smem_bytes(a);
         const int nb = ctx->adj_smem <= (size_t)kMaxSmem ? slr::adjoint_blocks_per_sm(ctx->adj_smem) : 0;
         ctx->adj_grid = nb * ctx->sm_count;
@@ -958,6 +978,7 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->alpha_ctr);
     cudaFree(ctx->wide_img);
     cudaFree(ctx->wide_buf);
+    cudaFree(ctx->adj_scratch);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -1381,7 +1402,6 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
     o.status = ctx->status;
     CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
     if (ctx->wide) {
-        if (alpha) return fail(ctx, SLR_EUNSUPPORTED, "supplied slopes are not available on the wide path");
         int64_t launches = 0;
         if ((rc = run_wide(ctx, src, n, o, &launches))) return rc;
     } else if (ctx->opt.precision == SLR_PREC_TC_TF32 && ctx->tc_ok && alpha == nullptr) {
@@ -1862,6 +1882,7 @@ slr::AdjArgs adj_base(const slr_ctx *ctx) {
     a.n_max = ctx->adj_nmax;
     a.nck = ctx->adj_nck;
     a.boxes_per_cta = ctx->adj_boxes;
+    a.gscratch = ctx->adj_gmem ? (float *)ctx->adj_scratch : nullptr;
     a.Cprop = ctx->dC;
     a.n_out = ctx->widths[ctx->K];
     a.lr = 0.f;
@@ -1884,6 +1905,17 @@ int check_adjoint(slr_ctx *ctx) {
     if (ctx->adj_grid <= 0)
         return fail(ctx, SLR_EUNSUPPORTED, "network too large for the adjoint kernel (%zu bytes of shared memory)",
                     ctx->adj_smem);
+    if (ctx->adj_gmem) {
+        slr::AdjArgs a = adj_base(ctx);
+        const size_t need = slr::adjoint_box_bytes(a) * (size_t)ctx->adj_grid;
+        if (ctx->adj_scratch_bytes < need) {
+            cudaFree(ctx->adj_scratch);
+            ctx->adj_scratch = nullptr;
+            ctx->adj_scratch_bytes = 0;
+            CK(ctx, cudaMalloc(&ctx->adj_scratch, need));
+            ctx->adj_scratch_bytes = need;
+        }
+    }
     return SLR_OK;
 }
 
@@ -1929,6 +1961,20 @@ int eval_by_position(slr_ctx *ctx, slr::BoxSource src, const float *alpha, float
     o.row_hi = hi;
     o.by_position = 1;
     o.status = ctx->status;
+    if (ctx->wide) {
+        // the chunk loop needs the number of positions on the host
+        int64_t n = src.n_explicit;
+        if (src.index != nullptr || src.mode == 0) {
+            unsigned long long c = 0;
+            CK(ctx, cudaMemcpyAsync(&c, src.index != nullptr ? src.index_count : src.count, sizeof c,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            n = (int64_t)c;
+        }
+        n = std::min<int64_t>(n, src.cap);
+        int64_t launches = 0;
+        return n > 0 ? run_wide(ctx, src, n, o, &launches) : SLR_OK;
+    }
     const int64_t tiles = (n_hint + ctx->T32 - 1) / ctx->T32;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ctx->grid32));
     CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->NT32, grid, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));

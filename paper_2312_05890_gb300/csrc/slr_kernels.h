@@ -66,6 +66,9 @@ struct AdjArgs {
     int n_max;                      // widest layer n[1..K]
     int nck;                        // hidden layers whose equations stay in shared memory
     int boxes_per_cta;              // boxes a CTA works on together
+    float *gscratch;                // optional: per-CTA box state in global memory (networks whose
+                                    // state exceeds shared memory); CTA c uses boxes_per_cta slots
+                                    // from gscratch + c * boxes_per_cta * (floats per box)
     int alpha_mode;                 // kAlphaDefault: u/(u-l), differentiated through; kAlphaFree: read;
                                     // kAlphaInit: write u/(u-l) to alpha, then treat it as free
     float *alpha;                   // n x H
@@ -83,6 +86,7 @@ struct AdjArgs {
     float lr, beta1, beta2, eps, beta1_t, beta2_t;
 };
 size_t adjoint_smem_bytes(const AdjArgs &a);
+size_t adjoint_box_bytes(const AdjArgs &a);
 int adjoint_blocks_per_sm(size_t smem);
 cudaError_t launch_adjoint(const AdjArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_merge_bounds(const NetParams<float> &net, int64_t n, const unsigned long long *count,
@@ -107,12 +111,16 @@ size_t wide_gemm_smem_bytes();
 cudaError_t launch_wide_gemm(const WideGemmArgs &args, int nprob, cudaStream_t s);
 cudaError_t launch_wide_box(const BoxSource &src, int64_t base, int nb, int d, float *mh, float *ml, float *rr,
                             int64_t *bidx, int sms, cudaStream_t s);
+// Wide row kernels: `alpha` (nullable) holds the lower slopes of the chunk's
+// boxes, box b (0-based in the chunk) at row (base + b) * alpha_ld.
 cudaError_t launch_wide_init(const NetParams<float> &net, const float *W0t, int nb, int NP, const float *mh,
-                             const float *ml, const float *rr, float *C, float *Rr, float *Ch, float *Cl, cudaStream_t s);
+                             const float *ml, const float *rr, float *C, float *Rr, float *Ch, float *Cl,
+                             const float *alpha, int64_t alpha_ld, int64_t base, cudaStream_t s);
 cudaError_t launch_wide_const(const NetParams<float> &net, int k, int nb, int NP, const float *Ch, const float *Cl,
                               const float *Rr, float *Kh, float *Kl, float *Ke, int sms, cudaStream_t s);
 cudaError_t launch_wide_hidden(const NetParams<float> &net, int layer, int nb, int NP, float gcoef, float *C, float *Rr,
-                               float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke, cudaStream_t s);
+                               float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke,
+                               const float *alpha, int64_t alpha_ld, int64_t base, cudaStream_t s);
 cudaError_t launch_wide_final(const NetParams<float> &net, int nb, int NP, float gcoef, float *C, float *Rr, float *Ch,
                               float *Cl, const float *Kh, const float *Kl, const float *Ke, float *lo, float *hi,
                               float *err, cudaStream_t s);

@@ -111,7 +111,8 @@ constexpr int kRowsX = 32, kSlicesY = 16;
 // relaxation when it is a hidden layer.  W0t: W_1 transposed (d x n_1).
 __global__ void __launch_bounds__(kRowsX * kSlicesY)
 wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const float *mh, const float *ml,
-                 const float *rr, float *C, float *Rr, float *Ch, float *Cl) {
+                 const float *rr, float *C, float *Rr, float *Ch, float *Cl, const float *alpha, int64_t alpha_ld,
+                 int64_t base) {
     using A = Arith<float>;
     __shared__ RowBounds<float> part[kSlicesY][kRowsX];
     __shared__ RelaxPlan<float> plan[kRowsX];
@@ -176,7 +177,8 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
         pl.E = E;
         if (net.K > 1) {
             t.finish(chi, clo, 0.f);
-            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, E, nullptr);
+            const float *a_ptr = alpha != nullptr ? alpha + (base + b) * alpha_ld + p : nullptr;
+            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, E, a_ptr);
         }
         plan[lane] = pl;
     }
@@ -268,7 +270,8 @@ __device__ __forceinline__ void wide_finish(const WideRow &R, const float *Kh, c
 // Hidden layer `layer` after its product: error, bounds, ReLU relaxation in place.
 __global__ void __launch_bounds__(kRowsX * kSlicesY)
 wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, float *C, float *Rr, float *Ch,
-                   float *Cl, const float *Kh, const float *Kl, const float *Ke) {
+                   float *Cl, const float *Kh, const float *Kl, const float *Ke, const float *alpha, int64_t alpha_ld,
+                   int64_t base) {
     using A = Arith<float>;
     __shared__ RowBounds<float> part[kSlicesY][kRowsX];
     __shared__ RelaxPlan<float> plan[kRowsX];
@@ -293,7 +296,13 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
         wide_finish(R, Kh, Kl, Ke, NP, n_in, gcoef, chi, clo, E);
         const float rd = R(WTile::cRd(d));
         t.finish(chi, clo, rd);
-        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, nullptr);
+        const float *a_ptr = nullptr;
+        if (alpha != nullptr) {
+            int off = 0;
+            for (int j = 1; j < layer; ++j) off += net.n[j];
+            a_ptr = alpha + (base + b) * alpha_ld + off + p;
+        }
+        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, a_ptr);
     }
     __syncthreads();
     if (live) {
@@ -601,9 +610,10 @@ cudaError_t launch_wide_box(const BoxSource &src, int64_t base, int nb, int d, f
 }
 
 cudaError_t launch_wide_init(const NetParams<float> &net, const float *W0t, int nb, int NP, const float *mh,
-                             const float *ml, const float *rr, float *C, float *Rr, float *Ch, float *Cl, cudaStream_t s) {
+                             const float *ml, const float *rr, float *C, float *Rr, float *Ch, float *Cl,
+                             const float *alpha, int64_t alpha_ld, int64_t base, cudaStream_t s) {
     const dim3 grid((net.n[1] + kRowsX - 1) / kRowsX, nb), block(kRowsX, kSlicesY);
-    wide_init_kernel<<<grid, block, 0, s>>>(net, W0t, NP, mh, ml, rr, C, Rr, Ch, Cl);
+    wide_init_kernel<<<grid, block, 0, s>>>(net, W0t, NP, mh, ml, rr, C, Rr, Ch, Cl, alpha, alpha_ld, base);
     return cudaGetLastError();
 }
 
@@ -615,9 +625,10 @@ cudaError_t launch_wide_const(const NetParams<float> &net, int k, int nb, int NP
 }
 
 cudaError_t launch_wide_hidden(const NetParams<float> &net, int layer, int nb, int NP, float gcoef, float *C, float *Rr,
-                               float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke, cudaStream_t s) {
+                               float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke,
+                               const float *alpha, int64_t alpha_ld, int64_t base, cudaStream_t s) {
     const dim3 grid((net.n[layer] + kRowsX - 1) / kRowsX, nb), block(kRowsX, kSlicesY);
-    wide_hidden_kernel<<<grid, block, 0, s>>>(net, layer, NP, gcoef, C, Rr, Ch, Cl, Kh, Kl, Ke);
+    wide_hidden_kernel<<<grid, block, 0, s>>>(net, layer, NP, gcoef, C, Rr, Ch, Cl, Kh, Kl, Ke, alpha, alpha_ld, base);
     return cudaGetLastError();
 }
 

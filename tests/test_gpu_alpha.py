@@ -271,3 +271,79 @@ def test_autograd_function(pkg):
     assert np.allclose(A.grad.cpu().numpy(), ref["d_alpha"], rtol=1e-5, atol=1e-6)
     for k in range(len(W)):
         assert np.allclose(W[k].grad.cpu().numpy(), ref["d_W"][k], rtol=1e-4, atol=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# slopes on the wide path (per-box state in GPU memory; adjoint state in
+# global memory)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "acas"])
+def test_wide_bounds_at_given_slopes(pkg, name):
+    p = gen.make(name)
+    lo, hi = random_sub_boxes(p, 200, seed=21)
+    with _counter(pkg, p, wide=1) as c:
+        H = c.alpha_width()
+        A = np.random.default_rng(2).uniform(0, 1, size=(200, H)).astype(np.float32)
+        rl, rh, cls, err = c.bounds(lo, hi, want_err=True, alpha=A)
+    olo, ohi = _oracle_bounds_at(p, lo, hi, A)
+    scale = np.maximum(np.abs(olo), np.abs(ohi)) + (ohi - olo)
+    assert np.all(rl <= olo + 1e-12 * scale) and np.all(rh >= ohi - 1e-12 * scale)
+    elo, ehi, _ = bound_errors(rl.astype(np.float64) + err, rh.astype(np.float64) - err, olo, ohi)
+    assert elo.max() <= BOUND_RTOL and ehi.max() <= BOUND_RTOL
+
+
+@pytest.mark.parametrize("free", [True, False])
+def test_wide_adjoint_matches_tile_adjoint(pkg, free):
+    """The global-memory adjoint (wide path) computes what the shared-memory one does."""
+    p = gen.make("acas")
+    lo, hi = random_sub_boxes(p, 64, seed=8)
+    R = p.prop.C.shape[0]
+    rng = np.random.default_rng(3)
+    g_lo = rng.normal(size=(64, R)).astype(np.float32)
+    g_hi = rng.normal(size=(64, R)).astype(np.float32)
+    with _counter(pkg, p) as c:
+        H = c.alpha_width()
+        A = rng.uniform(0.05, 0.95, size=(64, H)).astype(np.float32) if free else None
+        a = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A, weights=True)
+    with _counter(pkg, p, wide=1) as c:
+        b = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A, weights=True)
+    for key in ("row_lo", "row_hi", "d_lo", "d_hi") + (("d_alpha",) if free else ()):
+        assert np.array_equal(a[key], b[key]), key
+    # weight gradients are sums over boxes in a different grouping and atomic order
+    for k in range(len(p.net.W)):
+        scale = np.abs(a["d_W"][k]).max() + 1e-6
+        assert np.abs(a["d_W"][k] - b["d_W"][k]).max() <= 1e-5 * scale
+
+
+def test_wide_slopes_mnist_shaped(pkg):
+    """784 -> 3x256 -> 10: optimised slopes give sound bounds no looser than the default."""
+    p = gen.make("mnist")
+    lo, hi = random_sub_boxes(p, 6, seed=5, min_frac=0.5)
+    with _counter(pkg, p) as c:
+        d_lo, d_hi, _ = c.bounds(lo, hi)
+        rl, rh, cls, A = c.optimize_alpha(lo, hi, steps=5, lr=0.1)
+        al, ah, _, aerr = c.bounds(lo, hi, want_err=True, alpha=A)
+    assert np.all(rl >= d_lo) and np.all(rh <= d_hi)
+    assert np.all(rl >= al) and np.all(rh <= ah)
+    olo, ohi = _oracle_bounds_at(p, lo, hi, A)
+    scale = np.maximum(np.abs(olo), np.abs(ohi)) + (ohi - olo)
+    assert np.all(al <= olo + 1e-12 * scale) and np.all(ah >= ohi - 1e-12 * scale)
+    elo, ehi, _ = bound_errors(al.astype(np.float64) + aerr, ah.astype(np.float64) - aerr, olo, ohi)
+    assert elo.max() <= BOUND_RTOL and ehi.max() <= BOUND_RTOL
+    rng = np.random.default_rng(0)
+    for b in range(len(lo)):
+        x = lo[b] + (hi[b] - lo[b]) * rng.random((500, p.d))
+        y = oracle.forward_points(p.net, x, p.prop)[0]
+        assert np.all(y >= rl[b]) and np.all(y <= rh[b])
+
+
+def test_wide_count_with_slopes_nests(pkg):
+    p = gen.make("acas")
+    D = 11
+    with _counter(pkg, p, wide=1) as c:
+        fixed = c.count(D)
+        c.set_options(wide=1, alpha_steps=10, alpha_lr=0.1)
+        opt = c.count(D)
+    assert fixed["unsafe_lo"] <= opt["unsafe_lo"] <= opt["unsafe_hi"] <= fixed["unsafe_hi"]
+    assert opt["alpha_boxes"] > 0
