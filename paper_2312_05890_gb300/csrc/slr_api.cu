@@ -83,6 +83,7 @@ struct slr_ctx {
     bool tc_ok = false;
     int64_t *near_list2 = nullptr;
     BatchState *batch = nullptr;
+    slr_ctx *wide_helper = nullptr;       // batched counts: problems too wide for a tile
     std::string tuned_key;                // network shape the FP32 tile choice was timed for
     int tuned_T = 0, tuned_NT = 0;
     const float *dC = nullptr;            // property rows on the device (inside net_buf)
@@ -979,6 +980,7 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->wide_img);
     cudaFree(ctx->wide_buf);
     cudaFree(ctx->adj_scratch);
+    if (ctx->wide_helper) slr_destroy(ctx->wide_helper);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -1533,9 +1535,10 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
-    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
-    if (n < 1 || n > 65535 || !problems || !results) return fail(ctx, SLR_EINVAL, "bad batch arguments");
+namespace {
+
+// The batched count of problems whose per-box state fits a shared-memory tile.
+int count_batch_tile(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
     CK(ctx, cudaSetDevice(ctx->device));
     const int P = n;
     std::vector<ProblemHost> ph(P);
@@ -1865,6 +1868,64 @@ extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems,
     }
     if (st & slr::kStatusOverflow) return fail(ctx, SLR_EOVERFLOW, "a problem's level exceeded its frontier capacity");
     if (st & slr::kStatusNearOverflow) return fail(ctx, SLR_EOVERFLOW, "an FP64 re-check list overflowed");
+    return SLR_OK;
+}
+
+}  // namespace
+
+// Whether a problem's per-box state fits the batched tile kernel (its
+// smallest tile, two product tiles per thread).
+static bool batch_tile_fits(const slr_problem &q) {
+    if (q.K < 1 || q.K > slr::kMaxLayers || !q.widths || !q.rows_per_clause) return true;   // validated later
+    int R = 0;
+    for (int c = 0; c < q.n_clauses; ++c) R += q.rows_per_clause[c];
+    int nmax = R, nin = 1;
+    for (int k = 1; k < q.K; ++k) {
+        nmax = std::max(nmax, q.widths[k]);
+        nin = std::max(nin, q.widths[k]);
+    }
+    const int nmp = (nmax + 7) & ~7;
+    const int d = q.widths[0];
+    return slr::eval_gemm_items(4, d, nmp) <= 2 * 256 &&
+           slr::eval_smem_bytes<float>(4, d, R, nmp, nin) + 1024 <= (size_t)kMaxSmem;
+}
+
+extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (n < 1 || n > 65535 || !problems || !results) return fail(ctx, SLR_EINVAL, "bad batch arguments");
+    std::vector<int> tile, wide;
+    for (int i = 0; i < n; ++i) (batch_tile_fits(problems[i]) ? tile : wide).push_back(i);
+    if (wide.empty()) return count_batch_tile(ctx, n, problems, results);
+    int rc;
+    // problems that fit a tile: one persistent launch per level step together
+    if (!tile.empty()) {
+        std::vector<slr_problem> sub(tile.size());
+        std::vector<slr_result> res(tile.size());
+        for (size_t j = 0; j < tile.size(); ++j) sub[j] = problems[tile[j]];
+        if ((rc = count_batch_tile(ctx, (int)sub.size(), sub.data(), res.data()))) return rc;
+        for (size_t j = 0; j < tile.size(); ++j) results[tile[j]] = res[j];
+    }
+    // wider problems: one wide-path count each, on a helper context sharing the stream
+    if (!ctx->wide_helper) {
+        if ((rc = slr_create(&ctx->wide_helper, ctx->device, ctx->stream)))
+            return fail(ctx, rc, "wide helper context: %s", slr_last_error(nullptr));
+    }
+    slr_ctx *h = ctx->wide_helper;
+    slr_options o = ctx->opt;
+    o.wide = 1;
+    o.alpha_steps = 0;
+    o.record_leaves = 0;
+    o.tile_boxes = o.tile_threads = 0;
+    if ((rc = slr_set_options(h, &o))) return fail(ctx, rc, "problem batch: %s", slr_last_error(h));
+    for (int i : wide) {
+        const slr_problem &q = problems[i];
+        int R = 0;
+        for (int c = 0; c < q.n_clauses; ++c) R += q.rows_per_clause ? q.rows_per_clause[c] : 0;
+        if ((rc = slr_load_network(h, q.K, q.widths, q.W, q.b)) || (rc = slr_set_box(h, q.widths[0], q.lo, q.hi)) ||
+            (rc = slr_set_property(h, q.n_clauses, q.rows_per_clause, q.widths[q.K], q.C, q.e, q.strict)) ||
+            (rc = slr_count(h, q.depth, &results[i])))
+            return fail(ctx, rc, "problem %d: %s", i, slr_last_error(h));
+    }
     return SLR_OK;
 }
 

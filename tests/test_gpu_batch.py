@@ -53,6 +53,9 @@ def test_batch_matches_oracle_on_small_problems(pkg):
     with pkg.Counter(0) as c:
         got = c.count_batch(probs, depths)
     for p, D, g in zip(probs, depths, got):
+        s = _single(pkg, p, D)
+        for k in KEYS:
+            assert np.array_equal(np.asarray(g[k]), np.asarray(s[k])), (p.name, k)
         w = oracle.count(p.net, p.lo, p.hi, p.prop, D)
         assert (g["unsafe_lo"], g["unsafe_hi"]) == (w.unsafe_lo, w.unsafe_hi), p.name
         assert g["level_boxes"] == [lv["boxes"] for lv in w.levels]
@@ -83,3 +86,23 @@ def test_batch_rejects_bad_problem(pkg):
         with pytest.raises(pkg.SlrError) as ei:
             c.count_batch([gen.tiny(1), p], [8, 8])
         assert ei.value.code == -1 and "problem 1" in str(ei.value)
+
+
+def test_batch_with_wide_members(pkg):
+    """256- and 512-wide members run on the wide path inside the same batched call."""
+    probs = [gen.tiny(0), gen.acas_shaped(0)]
+    depths = [12, 9]
+    probs += gen.batched_uneven(4, n_nets=2, props_per_net=2, depth_range=(6, 8), widths=(256, 512), tile_only=False)
+    depths += [p.depth for p in probs[2:]]
+    assert any(max(p.net.widths[1:-1]) >= 256 for p in probs)
+    with pkg.Counter(0) as c:
+        got = c.count_batch(probs, depths)
+    for p, D, g in zip(probs, depths, got):
+        s = _single(pkg, p, D)
+        for k in KEYS:
+            assert np.array_equal(np.asarray(g[k]), np.asarray(s[k])), (p.name, k)
+        w = oracle.count(p.net, p.lo, p.hi, p.prop, D)
+        if g["tie_leaves"] == 0:
+            assert (g["unsafe_lo"], g["unsafe_hi"]) == (w.unsafe_lo, w.unsafe_hi), p.name
+        else:
+            assert g["unsafe_lo"] <= w.unsafe_lo <= w.unsafe_hi <= g["unsafe_hi"], p.name

@@ -286,7 +286,7 @@ def _batch_member(rng, d, width, hidden, n_props, depth_range, seed):
 
 
 def batched_uneven(seed: int = 0, n_nets: int = 16, props_per_net: int = 16, depth_range=(12, 22),
-                   widths=(32, 64, 128)):
+                   widths=(32, 64, 128), tile_only=True):
     """Many (network, property) problems of uneven size (the batched workload).
 
     16 seeded networks with inputs d in {5, 8, 16, 32}, hidden widths from
@@ -294,15 +294,16 @@ def batched_uneven(seed: int = 0, n_nets: int = 16, props_per_net: int = 16, dep
     U(0.02, 0.2) inside [-0.5, 0.5]^d) with a one-clause property of 1-2 rows
     a y_i - a' y_j + e >= 0 (a, a' ~ U(0.5, 2), e ~ N(0, 0.1)), redrawn until
     the Monte-Carlo violation rate lies in [1 %, 99 %], and a depth cap
-    D ~ U{12..22}.  A width is kept only when its contraction tiles fit the
-    fused kernel: (2d + 3) * width / 8 <= 512.
+    D ~ U{12..22}.  With `tile_only` a width is kept only when its
+    contraction tiles fit the fused kernel, (2d + 3) * width / 8 <= 512;
+    otherwise wider networks run on the wide path inside the same call.
     """
     rng = np.random.default_rng(seed)
     probs = []
     ds = [5, 8, 16, 32]
     for k in range(n_nets):
         d = ds[k % len(ds)]
-        ok_w = [w for w in widths if (2 * d + 3) * ((w + 7) // 8) <= 512]
+        ok_w = [w for w in widths if not tile_only or (2 * d + 3) * ((w + 7) // 8) <= 512]
         width = int(rng.choice(ok_w))
         hidden = int(rng.integers(2, 9))
         probs += _batch_member(rng, d, width, hidden, props_per_net, depth_range, seed * 1000 + k)
