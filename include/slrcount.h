@@ -67,6 +67,21 @@ enum { SLR_RELAX_NEURIFY = 0, SLR_RELAX_PAPER_LITERAL = 1, SLR_RELAX_INTERVAL = 
  *   layer and the property at most 64 wide (SLR_EUNSUPPORTED otherwise). */
 enum { SLR_PREC_FP32 = 0, SLR_PREC_TC_TF32 = 1 };
 
+/* Which side an UNDECIDED box is bisected along (Sec. 2.2 splits a box into two
+ * halves of one input interval and leaves the dimension open).
+ * WIDEST: the widest side, ties to the lowest index.  All boxes of a level then
+ *   split the same dimension (one schedule, slr_schedule).
+ * GRADIENT: per box.  A split set S of at most 16 input dimensions is fixed at
+ *   the root: those with the largest |dM/dr_i| w_i, where M is the decision loss
+ *   of the slope optimisation at the fixed slopes u/(u-l), r the box radius and
+ *   w the root widths (ties to the lowest index).  Each UNDECIDED box then
+ *   splits the dimension of S with the largest |dM/dr_i| r_i for its own
+ *   radius, the gradient taken by the adjoint at the slopes of its bounds (the
+ *   optimised ones when alpha_steps > 0); ties go to the first in S.  Counts
+ *   to depth 12 at most; needs relax_mode NEURIFY and every UNDECIDED box of a
+ *   level within alpha_cap (SLR_EOVERFLOW otherwise).  slr_split_set returns S. */
+enum { SLR_SPLIT_WIDEST = 0, SLR_SPLIT_GRADIENT = 1 };
+
 typedef struct {
     int32_t precision;      /* SLR_PREC_*; default SLR_PREC_FP32 */
     int32_t relax_mode;     /* SLR_RELAX_*; default SLR_RELAX_NEURIFY */
@@ -74,7 +89,7 @@ typedef struct {
                                bounds would decide without their widening; default 1 */
     int32_t record_leaves;  /* 1: keep the leaves of the last count for slr_leaves(); default 0 */
     int32_t profile;        /* 1: time each kernel of a count with CUDA events (kernel_ms); default 0 */
-    int32_t reserved;       /* must be 0 */
+    int32_t split_rule;     /* SLR_SPLIT_*; default SLR_SPLIT_WIDEST */
     int64_t frontier_cap;   /* most boxes one level may hold; default 1<<24 */
     int64_t leaf_cap;       /* most leaves recorded when record_leaves; default 1<<22 */
     int32_t alpha_steps;    /* slr_count: projected-Adam steps on the lower ReLU slopes of the
@@ -229,6 +244,8 @@ int slr_optimize_alpha(slr_ctx *ctx, int64_t n, const float *box_lo, const float
 
 /* Leaves of the last slr_count when record_leaves was set: for each leaf its
  * path code (bit t-1-j = half taken at split j, 1 = upper), depth and class.
+ * Under SLR_SPLIT_GRADIENT the path takes the low 16 bits and bits 16+4j ..
+ * 19+4j hold the position in the split set of the dimension split j took.
  * Leaves are the SAFE and UNSAFE boxes of every level and the UNDECIDED boxes of
  * depth D, in no particular order.  Writes at most `cap` entries and sets *n to
  * the total number recorded (SLR_EOVERFLOW if leaf_cap was exceeded). */
@@ -236,8 +253,12 @@ int slr_leaves(slr_ctx *ctx, int64_t cap, uint64_t *codes, uint8_t *depth,
                uint8_t *cls, int64_t *n);
 
 /* The split dimension of each of the first D levels of the last count (the
- * widest-side schedule), D entries. */
+ * widest-side schedule), D entries.  SLR_ESTATE after a SLR_SPLIT_GRADIENT count. */
 int slr_schedule(slr_ctx *ctx, int D, int32_t *dims);
+
+/* The split set S of the last SLR_SPLIT_GRADIENT count, ascending: writes *n <= 16
+ * dimensions to dims (room for 16).  SLR_ESTATE after a widest-side count. */
+int slr_split_set(slr_ctx *ctx, int32_t *dims, int32_t *n);
 
 /* One problem of a batch: a network, an input box, a property (as in
  * slr_load_network, slr_set_box and slr_set_property) and its depth cap. */

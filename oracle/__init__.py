@@ -14,6 +14,8 @@ Modules
            count (Alg. 1 with a depth cap; Sec. 3 level-parallel BaB).
   grad     central finite differences of the row bounds with respect to the
            lower ReLU slopes, the box, the weights and the biases.
+  split    the gradient split rule (a split dimension per box from the
+           decision loss's radius gradient).
 
 Every function here is pinned by tests that do not re-use its own formulas
 (brute force over box vertices, closed forms, hand-worked examples, sampling).
@@ -24,3 +26,6 @@ from .slr import (  # noqa: F401
 )
 from .counter import split_schedule, decode, count, CountResult  # noqa: F401
 from .grad import objective, fd_gradients, default_alpha  # noqa: F401
+from .split import (  # noqa: F401
+    decision_weights, radius_gradient, split_set, root_scores, box_scores, gradient_split,
+)

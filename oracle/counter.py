@@ -13,6 +13,11 @@ together.  This module does exactly that, breadth-first, with a depth cap D:
   * an UNSAFE box at depth t adds 2^(D-t) units (one unit = 2^-D of the root
     volume); an UNDECIDED box at depth D adds one unit to the undecided
     count; the violation rate then lies in [lo, lo + und] / 2^D.
+
+With a ``split`` callable the dimension is chosen per box instead (e.g. the
+gradient rule of ``split.py``); each box then carries its own half indices
+k_i and split counts c_i, and spans [a_i + w_i k_i 2^-c_i, a_i + w_i (k_i+1) 2^-c_i]
+as before.
 """
 from __future__ import annotations
 
@@ -73,6 +78,7 @@ class CountResult:
     depth: int
     levels: list = field(default_factory=list)      # per level: dict(boxes, safe, unsafe, undecided)
     leaves: list = field(default_factory=list)      # (code, depth, class) when collected
+    leaf_boxes: list = field(default_factory=list)  # per-box splits: (lo, hi) of each collected leaf
 
     @property
     def boxes(self):
@@ -80,14 +86,19 @@ class CountResult:
 
 
 def count(net, a, b, prop, D, mode="neurify", bound="slr", collect_leaves=False,
-          batch=8192, max_boxes=None):
+          batch=8192, max_boxes=None, split=None):
     """Exact-count bracket [unsafe_lo, unsafe_hi] in units of 2^-D of the root box.
 
     bound='slr' uses symbolic linear relaxation; bound='interval' uses naive
     Moore intervals (the paper's Exact Count baseline).  ``max_boxes`` stops
     after that many box evaluations (a bounded sample used only for timing)
-    and returns the partial result.
+    and returns the partial result.  ``split``: None splits the widest side
+    (one schedule for every box of a level); a callable
+    split(t, paths, lo, hi) -> dims gives the dimension of each UNDECIDED box
+    of level t (paths: their path codes; lo, hi: float64 endpoints).
     """
+    if split is not None:
+        return _count_per_box(net, a, b, prop, D, mode, bound, collect_leaves, batch, split)
     sched = split_schedule(a, b, D)
     frontier = np.zeros(1, dtype=np.int64)
     lo = 0
@@ -132,5 +143,67 @@ def count(net, a, b, prop, D, mode="neurify", bound="slr", collect_leaves=False,
                 for _ in range(t + 1, D + 1):
                     res.levels.append(dict(boxes=0, safe=0, unsafe=0, undecided=0))
                 break
+    res.unsafe_lo, res.unsafe_hi = lo, lo + und
+    return res
+
+
+def _count_per_box(net, a, b, prop, D, mode, bound, collect_leaves, batch, split):
+    """``count`` with a split dimension chosen per box."""
+    a64 = np.asarray(a, dtype=np.float64)
+    w = np.asarray(b, dtype=np.float64) - a64
+    d = a64.shape[0]
+    paths = np.zeros(1, dtype=np.int64)
+    K = np.zeros((1, d), dtype=np.int64)      # half index along each dimension
+    C = np.zeros((1, d), dtype=np.int64)      # splits along each dimension
+    lo = 0
+    und = 0
+    res = CountResult(0, 0, D)
+    for t in range(D + 1):
+        nxt = []
+        lv = dict(boxes=int(paths.shape[0]), safe=0, unsafe=0, undecided=0)
+        for s in range(0, paths.shape[0], batch):
+            p, k, c = paths[s:s + batch], K[s:s + batch], C[s:s + batch]
+            scale = np.ldexp(1.0, -c)
+            blo = a64 + w * (k * scale)
+            bhi = a64 + w * ((k + 1) * scale)
+            if bound == "slr":
+                rlo, rhi, _ = slr_forward(net, blo, bhi, prop, mode=mode)
+            else:
+                rlo, rhi, _ = interval_forward(net, blo, bhi, prop)
+            cls = classify(rlo, rhi, prop)
+            n_uns = int(np.count_nonzero(cls == UNSAFE))
+            lv["unsafe"] += n_uns
+            lv["safe"] += int(np.count_nonzero(cls == SAFE))
+            u = cls == UNDECIDED
+            lv["undecided"] += int(np.count_nonzero(u))
+            lo += n_uns << (D - t)
+            if t < D:
+                if np.any(u):
+                    dims = np.asarray(split(t, p[u], blo[u], bhi[u]), dtype=np.int64)
+                    rows = np.arange(dims.shape[0])
+                    k0 = k[u].copy()
+                    c1 = c[u].copy()
+                    k0[rows, dims] *= 2
+                    c1[rows, dims] += 1
+                    k1 = k0.copy()
+                    k1[rows, dims] += 1
+                    nxt.append((2 * p[u], k0, c1))
+                    nxt.append((2 * p[u] + 1, k1, c1))
+            else:
+                und += int(np.count_nonzero(u))
+            if collect_leaves:
+                for j, (cd, cl) in enumerate(zip(p.tolist(), cls.tolist())):
+                    if cl != UNDECIDED or t == D:
+                        res.leaves.append((cd, t, cl))
+                        res.leaf_boxes.append((blo[j], bhi[j]))
+        res.levels.append(lv)
+        if t < D:
+            if not nxt:
+                for _ in range(t + 1, D + 1):
+                    res.levels.append(dict(boxes=0, safe=0, unsafe=0, undecided=0))
+                break
+            paths = np.concatenate([x[0] for x in nxt])
+            K = np.concatenate([x[1] for x in nxt])
+            C = np.concatenate([x[2] for x in nxt])
     res.unsafe_lo, res.unsafe_hi = lo, lo + und
     return res

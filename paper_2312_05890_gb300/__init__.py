@@ -23,12 +23,15 @@ SAFE, UNSAFE, UNDECIDED = 0, 1, 2
 RELAX_NEURIFY, RELAX_PAPER_LITERAL, RELAX_INTERVAL = 0, 1, 2
 PREC_FP32 = 0
 PREC_TC_TF32 = 1
+SPLIT_WIDEST = 0
+SPLIT_GRADIENT = 1
+SPLIT_PATH_BITS = 16     # SPLIT_GRADIENT codes: path below, one 4-bit split-set position per level above
 MAX_LEVELS = 63
 
 # Names the header declares (checked by the CPU test that loads the library).
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
-           "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
+           "slr_split_set", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
            "slr_optimize_alpha", "slr_last_error")
 
 
@@ -41,7 +44,7 @@ class SlrError(RuntimeError):
 class slr_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
                 ("fp64_recheck", ctypes.c_int32), ("record_leaves", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("split_rule", ctypes.c_int32),
                 ("frontier_cap", ctypes.c_int64), ("leaf_cap", ctypes.c_int64),
                 ("alpha_steps", ctypes.c_int32), ("alpha_lr", ctypes.c_float), ("alpha_cap", ctypes.c_int64),
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
@@ -115,6 +118,7 @@ def load_library(path: str = LIB_PATH):
                                               ctypes.c_int]),
         "slr_leaves": (ctypes.c_int, [P, i64, P, P, P, ctypes.POINTER(i64)]),
         "slr_schedule": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "slr_split_set": (ctypes.c_int, [P, P, ctypes.POINTER(i32)]),
         "slr_count_noalloc": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
         "slr_count_batch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_problem), ctypes.POINTER(slr_result)]),
         "slr_last_error": (ctypes.c_char_p, [P]),
@@ -327,6 +331,23 @@ def slr_schedule(ctx, D: int):
     return out
 
 
+def slr_split_set(ctx):
+    lib = load_library()
+    out = np.empty(16, dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(lib, ctx, lib.slr_split_set(ctx, _ptr(out), ctypes.byref(n)))
+    return out[:n.value].copy()
+
+
+def split_code_dims(code: int, depth: int, split_set):
+    """(path, dims) of a SPLIT_GRADIENT code: the halves taken (bit depth-1-j for
+    split j) and the input dimension of each split."""
+    code = int(code)
+    path = code & ((1 << SPLIT_PATH_BITS) - 1)
+    dims = [int(split_set[(code >> (SPLIT_PATH_BITS + 4 * j)) & 15]) for j in range(depth)]
+    return path, dims
+
+
 def slr_count_noalloc(ctx, D: int) -> dict:
     """slr_count without any GPU allocation (fixed scratch inside the library; see the header)."""
     lib = load_library()
@@ -445,3 +466,6 @@ class Counter:
 
     def schedule(self, D: int):
         return slr_schedule(self.ctx, D)
+
+    def split_set(self):
+        return slr_split_set(self.ctx)

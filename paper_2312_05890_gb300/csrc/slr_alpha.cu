@@ -313,10 +313,12 @@ __device__ void decision_loss(const AdjArgs &a, const AdjSmem &s, int64_t pos) {
         }
         r0 = r1;
     }
-    int8_t dir = a.alpha_mode == kAlphaInit ? 0 : a.dir[pos];
+    // direction: kept from the first step of an optimisation; chosen afresh
+    // (and not kept) without a direction array
+    int8_t dir = (a.alpha_mode == kAlphaInit || a.dir == nullptr) ? 0 : a.dir[pos];
     if (dir == 0) {
         dir = safe_gap <= unsafe_gap ? 1 : 2;
-        a.dir[pos] = dir;
+        if (a.dir != nullptr) a.dir[pos] = dir;
     }
     r0 = 0;
     for (int c = 0; c < net.n_clauses; ++c) {
@@ -386,10 +388,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             const int64_t idx = src.index != nullptr ? src.index[pos] : pos;
             double m64, r64;
             if (src.mode == 0) {
-                const unsigned long long code = src.codes[idx];
-                const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
-                const unsigned long long kk = pext64(code, mask);
-                const int c = __popcll(mask);
+                unsigned long long kk;
+                int c;
+                code_dim(src, src.codes[idx], i, kk, c);
                 const double w = src.root_w[i];
                 r64 = ldexp(w, -(c + 1));
                 m64 = src.root_lo[i] + w * ldexp((double)(2 * kk + 1), -(c + 1));
@@ -667,6 +668,39 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
                 // m = (lo + hi) / 2, r = (hi - lo) / 2
                 a.d_lo[pos * d + i] = 0.5f * (gm - gr);
                 a.d_hi[pos * d + i] = 0.5f * (gm + gr);
+            }
+        }
+        if (a.d_r != nullptr) {
+            for (int it = threadIdx.x; it < g.nb * d; it += blockDim.x) {
+                const int q = it / d;
+                const int i = it - q * d;
+                const AdjSmem s = g.box(a, q);
+                float gr = 0.f;
+                for (int p = 0; p < n1; ++p) gr = fmaf(s.gA[p * Q + i], weight(net, 0, p, i), gr);
+                a.d_r[(pos0 + q) * d + i] = gr;
+            }
+        }
+        if (a.split_codes != nullptr) {
+            // split the dimension whose halving is predicted to lower the loss
+            // most: the largest |dM/dr_i| r_i over the split set
+            for (int q = threadIdx.x; q < g.nb; q += blockDim.x) {
+                const int64_t pos = pos0 + q;
+                const int64_t idx = a.src.index != nullptr ? a.src.index[pos] : pos;
+                if (a.split_cls[idx] != kUndecided) continue;
+                const AdjSmem s = g.box(a, q);
+                int sel = 0;
+                float best = -1.f;
+                for (int j = 0; j < a.n_split; ++j) {
+                    const int i = a.split_dims[j];
+                    float gr = 0.f;
+                    for (int p = 0; p < n1; ++p) gr = fmaf(s.gA[p * Q + i], weight(net, 0, p, i), gr);
+                    const float score = fabsf(gr) * s.r[i];
+                    if (score > best) {
+                        best = score;
+                        sel = j;
+                    }
+                }
+                a.split_codes[idx] |= (unsigned long long)sel << (kSplitPathBits + 4 * a.src.t);
             }
         }
         __syncthreads();

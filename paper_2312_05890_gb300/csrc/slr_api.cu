@@ -1,5 +1,6 @@
 // C ABI of the SLR counter: context, validation, device copies of the
 // network and the level-by-level driver of the count (Alg. 1, Sec. 3).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -84,6 +85,8 @@ struct slr_ctx {
     int64_t *near_list2 = nullptr;
     BatchState *batch = nullptr;
     slr_ctx *wide_helper = nullptr;       // batched counts: problems too wide for a tile
+    void *split_buf = nullptr;            // gradient split rule: set, dimension map, root gradient
+    std::vector<int> split_set;           // split set of the last count (ascending); empty: widest side
     std::string tuned_key;                // network shape the FP32 tile choice was timed for
     int tuned_T = 0, tuned_NT = 0;
     const float *dC = nullptr;            // property rows on the device (inside net_buf)
@@ -880,6 +883,8 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
                     "slr_count_noalloc needs the network and property on the device: call slr_count (or "
                     "slr_bounds with n >= 1) once after setting them");
     if (ctx->wide) return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc does not run the wide path");
+    if (ctx->opt.split_rule != SLR_SPLIT_WIDEST)
+        return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc splits the widest side only");
     v->device = ctx->device;
     v->stream = ctx->stream;
     v->d = ctx->widths[0];
@@ -905,6 +910,8 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
 int slr_internal_fail(slr_ctx *ctx, int code, const char *msg) { return fail(ctx, code, "%s", msg); }
 
 int slr_internal_alpha_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t, int64_t *launches);
+int slr_internal_split_root(slr_ctx *ctx, const slr::BoxSource &root, int64_t *launches);
+int slr_internal_split_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t, bool slopes, int64_t *launches);
 namespace {
 int check_adjoint(slr_ctx *ctx);
 }
@@ -918,7 +925,7 @@ void slr_default_options(slr_options *opt) {
     opt->fp64_recheck = 1;
     opt->record_leaves = 0;
     opt->profile = 0;
-    opt->reserved = 0;
+    opt->split_rule = SLR_SPLIT_WIDEST;
     opt->frontier_cap = (int64_t)1 << 24;
     opt->leaf_cap = (int64_t)1 << 22;
     opt->alpha_steps = 0;
@@ -981,6 +988,7 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->wide_buf);
     cudaFree(ctx->adj_scratch);
     if (ctx->wide_helper) slr_destroy(ctx->wide_helper);
+    cudaFree(ctx->split_buf);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -1009,7 +1017,8 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
         return fail(ctx, SLR_EINVAL, "relax_mode %d unknown", opt->relax_mode);
     if (opt->frontier_cap < 2 || opt->frontier_cap > ((int64_t)1 << 34))
         return fail(ctx, SLR_EINVAL, "frontier_cap %lld out of range", (long long)opt->frontier_cap);
-    if (opt->reserved != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
+    if (opt->split_rule != SLR_SPLIT_WIDEST && opt->split_rule != SLR_SPLIT_GRADIENT)
+        return fail(ctx, SLR_EINVAL, "split_rule must be SLR_SPLIT_WIDEST or SLR_SPLIT_GRADIENT");
     if (opt->record_leaves && (opt->leaf_cap < 1 || opt->leaf_cap > ((int64_t)1 << 34)))
         return fail(ctx, SLR_EINVAL, "leaf_cap %lld out of range", (long long)opt->leaf_cap);
     if (opt->alpha_steps < 0 || opt->alpha_steps > 1000)
@@ -1104,6 +1113,9 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     if (rc) return rc;
     if (!out) return fail(ctx, SLR_EINVAL, "out is NULL");
     if (D < 0 || D > slr::kMaxDepth) return fail(ctx, SLR_EINVAL, "D=%d out of range [0, %d]", D, slr::kMaxDepth);
+    const bool grad_split = ctx->opt.split_rule == SLR_SPLIT_GRADIENT;
+    if (grad_split && D > slr::kSplitMaxDepth)
+        return fail(ctx, SLR_EINVAL, "the gradient split rule counts to depth %d at most (D=%d)", slr::kSplitMaxDepth, D);
     CK(ctx, cudaSetDevice(ctx->device));
     if ((rc = prepare_device(ctx))) return rc;
     if ((rc = ensure_count_buffers(ctx))) return rc;
@@ -1148,7 +1160,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     const bool leaves = ctx->opt.record_leaves != 0;
     const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0 && !ctx->wide;
     const bool slopes = ctx->opt.alpha_steps > 0;
-    if (slopes) {
+    if (slopes || grad_split) {
         if ((rc = check_adjoint(ctx))) return rc;
         if (!ctx->alpha_ctr)
             CK(ctx, cudaMalloc(&ctx->alpha_ctr, 2 * (slr::kMaxDepth + 2) * sizeof(unsigned long long)));
@@ -1170,8 +1182,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     ctx->gemm_ev_used = 0;
     ctx->gemm_launches = 0;
     ctx->gemm_flop = 0;
-    CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
-    for (int t = 0; t <= D; ++t) {
+    auto level_source = [&](int t) {
         slr::BoxSource src{};
         src.mode = 0;
         src.codes = ctx->codes[t & 1];
@@ -1182,6 +1193,19 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         src.root_lo = ctx->root;
         src.root_w = ctx->root + d;
         src.cap = ctx->cap;
+        return src;
+    };
+    ctx->split_set.clear();
+    if (grad_split) {
+        // the split set from the box gradient at the root (before the timed region)
+        if ((rc = slr_internal_split_root(ctx, level_source(0), &launches))) return rc;
+        launches = 1;
+    }
+    const uint64_t path_mask = grad_split ? (1ull << slr::kSplitPathBits) - 1ull : ~0ull;
+    CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+    for (int t = 0; t <= D; ++t) {
+        slr::BoxSource src = level_source(t);
+        if (grad_split) src.split_of = (const int8_t *)ctx->split_buf;
         slr::EvalOutputs o{};
         o.cls = ctx->cls;
         o.near_list = recheck ? ctx->near_list : nullptr;
@@ -1254,11 +1278,14 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
             // may decide boxes that would otherwise be split
             if ((rc = slr_internal_alpha_level(ctx, src, t, &launches))) return rc;
         }
+        if (grad_split && t < D) {
+            if ((rc = slr_internal_split_level(ctx, src, t, slopes, &launches))) return rc;
+        }
         CK(ctx, mark(t, 3));
         CK(ctx, mark(t, 4));
         CK(ctx, slr::launch_compact(ctx->codes[t & 1], ctx->cls, ctx->codes[(t + 1) & 1], ctx->ctr, ctx->status,
                                     ctx->cap, t, D, leaves ? ctx->leaf_codes : nullptr, ctx->leaf_depth,
-                                    ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream));
+                                    ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream, path_mask));
         CK(ctx, mark(t, 5));
         launches += 2;
     }
@@ -1266,9 +1293,17 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     CK(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
     unsigned long long h_alpha[2 * (slr::kMaxDepth + 2)] = {};
-    if (slopes)
+    if (slopes || grad_split)
         CK(ctx, cudaMemcpyAsync(h_alpha, ctx->alpha_ctr, sizeof h_alpha, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (grad_split) {
+        const int64_t list_cap = std::min<int64_t>(ctx->opt.alpha_cap, ctx->cap);
+        for (int t = 0; t < D; ++t)
+            if ((int64_t)h_alpha[2 * t] > list_cap)
+                return fail(ctx, SLR_EOVERFLOW,
+                            "level %d left %llu boxes UNDECIDED, more than alpha_cap=%lld boxes whose split the "
+                            "gradient rule can choose", t, h_alpha[2 * t], (long long)list_cap);
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
 
@@ -1450,9 +1485,19 @@ int slr_leaves(slr_ctx *ctx, int64_t cap, uint64_t *codes, uint8_t *depth, uint8
 
 int slr_schedule(slr_ctx *ctx, int D, int32_t *dims) {
     if (!ctx || !dims) return fail(ctx, SLR_EINVAL, "null argument");
+    if (!ctx->split_set.empty())
+        return fail(ctx, SLR_ESTATE, "the last count chose split dimensions per box (gradient split rule)");
     if (D < 0 || D > (int)ctx->sched.size())
         return fail(ctx, SLR_EINVAL, "D=%d exceeds the last count's depth %zu", D, ctx->sched.size());
     for (int t = 0; t < D; ++t) dims[t] = ctx->sched[t];
+    return SLR_OK;
+}
+
+int slr_split_set(slr_ctx *ctx, int32_t *dims, int32_t *n) {
+    if (!ctx || !dims || !n) return fail(ctx, SLR_EINVAL, "null argument");
+    if (ctx->split_set.empty()) return fail(ctx, SLR_ESTATE, "the last count did not use the gradient split rule");
+    for (size_t j = 0; j < ctx->split_set.size(); ++j) dims[j] = ctx->split_set[j];
+    *n = (int32_t)ctx->split_set.size();
     return SLR_OK;
 }
 
@@ -1893,6 +1938,8 @@ static bool batch_tile_fits(const slr_problem &q) {
 extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
     if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
     if (n < 1 || n > 65535 || !problems || !results) return fail(ctx, SLR_EINVAL, "bad batch arguments");
+    if (ctx->opt.split_rule != SLR_SPLIT_WIDEST)
+        return fail(ctx, SLR_EUNSUPPORTED, "batched counts split the widest side; the gradient rule runs in slr_count");
     std::vector<int> tile, wide;
     for (int i = 0; i < n; ++i) (batch_tile_fits(problems[i]) ? tile : wide).push_back(i);
     if (wide.empty()) return count_batch_tile(ctx, n, problems, results);
@@ -2115,6 +2162,92 @@ int slr_internal_alpha_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t
     src.cap = cap;
     return optimise_slopes(ctx, src, cap, list_n, b, ctx->opt.alpha_steps, ctx->opt.alpha_lr, nullptr, ctx->cls,
                            list_n + 1, false, launches);
+}
+
+// Gradient split rule, the split set: the (at most kSplitSetMax) input
+// dimensions with the largest |dM/dr_i| w_i at the root box, M the decision
+// loss at the fixed slopes u/(u-l), r the box radius and w the root widths;
+// ties go to the lowest index.  Kept in ascending order: a code's nibble is a
+// position in it.
+int slr_internal_split_root(slr_ctx *ctx, const slr::BoxSource &root, int64_t *launches) {
+    const int d = ctx->widths[0];
+    const size_t grad_off = align_up((size_t)d) + align_up(slr::kSplitSetMax * sizeof(int));
+    if (!ctx->split_buf) CK(ctx, cudaMalloc(&ctx->split_buf, grad_off + (size_t)d * sizeof(float)));
+    int8_t *split_of = (int8_t *)ctx->split_buf;
+    int *dims_dev = (int *)((unsigned char *)ctx->split_buf + align_up((size_t)d));
+    float *grad = (float *)((unsigned char *)ctx->split_buf + grad_off);
+    slr::AdjArgs a = adj_base(ctx);
+    a.src = root;
+    a.n = 1;
+    a.count = nullptr;
+    a.alpha_mode = slr::kAlphaDefault;
+    a.d_r = grad;
+    CK(ctx, slr::launch_adjoint(a, 1, ctx->stream));
+    *launches += 1;
+    std::vector<float> g(d);
+    CK(ctx, cudaMemcpyAsync(g.data(), grad, (size_t)d * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<int> order(d);
+    std::vector<double> score(d);
+    for (int i = 0; i < d; ++i) {
+        order[i] = i;
+        const double s = std::fabs((double)g[i]) * ((double)ctx->hi[i] - (double)ctx->lo[i]);
+        score[i] = std::isfinite(s) ? s : -1.0;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return score[x] > score[y]; });
+    const int ns = std::min(d, slr::kSplitSetMax);
+    std::vector<int> set(order.begin(), order.begin() + ns);
+    std::sort(set.begin(), set.end());
+    std::vector<int8_t> of(d, (int8_t)-1);
+    for (int j = 0; j < ns; ++j) of[set[j]] = (int8_t)j;
+    CK(ctx, cudaMemcpy(split_of, of.data(), (size_t)d, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(dims_dev, set.data(), (size_t)ns * sizeof(int), cudaMemcpyHostToDevice));
+    ctx->split_set = set;
+    return SLR_OK;
+}
+
+// Gradient split rule, one level: each box the level leaves UNDECIDED (after
+// any slope steps) takes the dimension of the split set with the largest
+// |dM/dr_i| r_i, the gradient taken at its final slopes; the choice goes into
+// the nibble of its code for this level.
+int slr_internal_split_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t, bool slopes, int64_t *launches) {
+    const int64_t cap = std::min<int64_t>(ctx->opt.alpha_cap, ctx->cap);
+    const int R = (int)ctx->e.size();
+    unsigned long long *list_n = ctx->alpha_ctr + 2 * t;
+    slr::AdjArgs a = adj_base(ctx);
+    int64_t *list;
+    if (slopes) {
+        // the boxes of the level's slope optimisation, their slopes and directions
+        const AlphaBuffers b = carve_alpha(ctx->alpha_buf, cap, ctx->H, R);
+        list = b.list;
+        a.alpha_mode = slr::kAlphaFree;
+        a.alpha = b.alpha;
+        a.dir = b.dir;
+    } else {
+        int rc = ensure_alpha_buf(ctx, align_up((size_t)cap * sizeof(int64_t)));
+        if (rc) return rc;
+        list = (int64_t *)ctx->alpha_buf;
+        CK(ctx, slr::launch_gather_undecided(ctx->cls, frontier.count, ctx->cap, list, list_n, cap,
+                                             std::max(1, ctx->sm_count * 4), ctx->stream));
+        *launches += 1;
+        a.alpha_mode = slr::kAlphaDefault;
+    }
+    slr::BoxSource src = frontier;
+    src.index = list;
+    src.index_count = list_n;
+    src.cap = cap;
+    a.src = src;
+    a.n = cap;
+    a.count = list_n;
+    a.split_codes = ctx->codes[t & 1];
+    a.split_cls = ctx->cls;
+    a.split_dims = (const int *)((unsigned char *)ctx->split_buf + align_up((size_t)ctx->widths[0]));
+    a.n_split = (int)ctx->split_set.size();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((cap + ctx->adj_boxes - 1) / ctx->adj_boxes,
+                                                                 ctx->adj_grid));
+    CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+    *launches += 1;
+    return SLR_OK;
 }
 
 extern "C" {

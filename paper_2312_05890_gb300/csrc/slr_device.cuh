@@ -31,6 +31,13 @@ constexpr int kMaxLayers = 16;
 constexpr int kMaxRows = 64;      // property rows
 constexpr int kMaxWidth = 1024;   // neurons per layer
 constexpr int kMaxDepth = 62;
+// Per-box split dimensions (gradient split rule): a path code keeps the halves
+// taken in its low kSplitPathBits bits (split j in bit t-1-j) and, above them,
+// one 4-bit position in the split set (at most kSplitSetMax dimensions) per
+// level, for at most kSplitMaxDepth levels.
+constexpr int kSplitPathBits = 16;
+constexpr int kSplitSetMax = 16;
+constexpr int kSplitMaxDepth = 12;
 
 enum : uint8_t { kSafe = 0, kUnsafe = 1, kUndecided = 2 };
 enum : int { kRelaxNeurify = 0, kRelaxPaperLiteral = 1, kRelaxInterval = 2 };
@@ -135,6 +142,8 @@ struct BoxSource {
     int t;                            // depth of the codes
     int D;                            // depth cap (mask shift)
     const unsigned long long *dim_mask;  // per input dim: bits of the splits on it, full depth D
+    const int8_t *split_of;           // per input dim: position in the split set, or -1; non-null
+                                      // for per-box split dimensions carried in the codes
     const double *root_lo;            // float64 root box
     const double *root_w;             // float64 root widths
     int64_t cap;                      // upper bound on n (buffer capacity)

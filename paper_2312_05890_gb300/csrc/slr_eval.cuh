@@ -62,6 +62,31 @@ __device__ __forceinline__ unsigned long long pext64(unsigned long long x, unsig
     return res;
 }
 
+// Half index k and split count c of input dimension i in the depth-t box with
+// path code `code` (Sec. 2.2 bisection): dimension i spans
+// [a_i + w_i k 2^-c, a_i + w_i (k + 1) 2^-c].  Widest-side schedule: the splits
+// on i are the code bits dim_mask[i].  Per-box split dimensions: split j took
+// the upper half when bit t-1-j is set and dimension split_set[nibble j].
+__device__ __forceinline__ void code_dim(const BoxSource &src, unsigned long long code, int i,
+                                         unsigned long long &k, int &c) {
+    if (src.split_of == nullptr) {
+        const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
+        k = pext64(code, mask);
+        c = __popcll(mask);
+        return;
+    }
+    k = 0ull;
+    c = 0;
+    const int s = src.split_of[i];
+    if (s < 0) return;
+    for (int j = 0; j < src.t; ++j) {
+        if ((int)((code >> (kSplitPathBits + 4 * j)) & 15ull) == s) {
+            k = 2ull * k + ((code >> (src.t - 1 - j)) & 1ull);
+            ++c;
+        }
+    }
+}
+
 // Centre m64 as a pair hi + lo in Real and radius r rounded up so that
 // [hi + lo - r, hi + lo + r] covers [m64 - r64, m64 + r64] plus `pad` (the
 // float64 error of computing m64 and r64).
@@ -883,10 +908,9 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         double m64, r64, pad;
         if (src.mode == 0) {
             // Sec. 2.2 bisection: dimension i split c times, half index k
-            const unsigned long long code = src.codes[idx];
-            const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
-            const unsigned long long k = pext64(code, mask);
-            const int c = __popcll(mask);
+            unsigned long long k;
+            int c;
+            code_dim(src, src.codes[idx], i, k, c);
             const double w = src.root_w[i];
             const double a = src.root_lo[i];
             r64 = ldexp(w, -(c + 1));

@@ -177,10 +177,9 @@ slr_eval_tc_kernel(const NetParams<float> net, const TcParams tc, const BoxSourc
             const int64_t idx = sIdx[b];
             double m64, r64, pad;
             if (src.mode == 0) {
-                const unsigned long long code = src.codes[idx];
-                const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
-                const unsigned long long kk = pext64(code, mask);
-                const int c = __popcll(mask);
+                unsigned long long kk;
+                int c;
+                code_dim(src, src.codes[idx], i, kk, c);
                 const double w = src.root_w[i];
                 const double a = src.root_lo[i];
                 r64 = ldexp(w, -(c + 1));

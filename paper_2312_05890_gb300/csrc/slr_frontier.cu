@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256)
 compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
                uint64_t *__restrict__ codes_out, LevelCounters *ctr, unsigned int *status,
                int64_t cap, int t, int D, uint64_t *leaf_codes, uint8_t *leaf_depth,
-               uint8_t *leaf_cls, int64_t leaf_cap) {
+               uint8_t *leaf_cls, int64_t leaf_cap, uint64_t path_mask) {
     __shared__ unsigned sh[8];
     __shared__ unsigned long long s_off;
     const unsigned long long n_raw = ctr->frontier_n[t];
@@ -205,8 +205,10 @@ compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict_
         if (t < D && und) {
             const int64_t pos = 2 * (int64_t)(off + wbefore + __popc(m_und & lt_mask));
             if (pos + 1 < cap) {
-                codes_out[pos] = code << 1;
-                codes_out[pos + 1] = (code << 1) | 1ull;
+                // children: the path bits (those under path_mask) shifted up by one
+                const uint64_t child = code + (code & path_mask);
+                codes_out[pos] = child;
+                codes_out[pos + 1] = child | 1ull;
             }
         }
         off += ctot;
@@ -314,11 +316,11 @@ cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
                            uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
-                           int64_t leaf_cap, int grid, cudaStream_t s) {
+                           int64_t leaf_cap, int grid, cudaStream_t s, uint64_t path_mask) {
     (void)grid;
     compact_count_kernel<<<kCompactBlocks, 256, 0, s>>>(cls, ctr, cap, t);
     compact_kernel<<<kCompactBlocks, 256, 0, s>>>(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes,
-                                                  leaf_depth, leaf_cls, leaf_cap);
+                                                  leaf_depth, leaf_cls, leaf_cap, path_mask);
     return cudaGetLastError();
 }
 

@@ -84,6 +84,15 @@ struct AdjArgs {
     int adam_t;                     // > 0: take Adam step t on the slopes
     float *adam_m, *adam_v;         // n x H
     float lr, beta1, beta2, eps, beta1_t, beta2_t;
+    float *d_r;                     // optional n x d: gradient with respect to the box radius
+    // gradient split rule: for each position whose box split_cls (indexed like
+    // the source) still holds UNDECIDED, store in the box's code in split_codes
+    // the position in split_dims of the dimension i with the largest
+    // |dM/dr_i| r_i (the first on ties); split_codes null: no choice
+    uint64_t *split_codes;
+    const uint8_t *split_cls;
+    const int *split_dims;
+    int n_split;
 };
 size_t adjoint_smem_bytes(const AdjArgs &a);
 size_t adjoint_box_bytes(const AdjArgs &a);
@@ -132,6 +141,6 @@ cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
                            uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
-                           int64_t leaf_cap, int grid, cudaStream_t s);
+                           int64_t leaf_cap, int grid, cudaStream_t s, uint64_t path_mask = ~0ull);
 
 }  // namespace slr

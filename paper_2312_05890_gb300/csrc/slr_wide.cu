@@ -73,10 +73,9 @@ __global__ void wide_box_kernel(const BoxSource src, int64_t base, int nb, int d
         const int64_t idx = src.index != nullptr ? src.index[k] : k;
         double m64, r64, pad;
         if (src.mode == 0) {
-            const unsigned long long code = src.codes[idx];
-            const unsigned long long mask = src.dim_mask[i] >> (src.D - src.t);
-            const unsigned long long kk = pext64(code, mask);
-            const int c = __popcll(mask);
+            unsigned long long kk;
+            int c;
+            code_dim(src, src.codes[idx], i, kk, c);
             const double w = src.root_w[i];
             const double a = src.root_lo[i];
             r64 = ldexp(w, -(c + 1));
