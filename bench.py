@@ -195,6 +195,9 @@ def main():
                     help="boxes x threads per CTA of the FP32 evaluation kernel, e.g. 16x256 (default: timed choice)")
     ap.add_argument("--alpha-cap", type=int, default=1 << 20,
                     help="most undecided boxes per level whose slopes are optimised")
+    ap.add_argument("--split", default="widest", choices=["widest", "gradient"],
+                    help="bisect the widest side, or per box the dimension of the 16-dimension split set "
+                         "with the largest |dM/dr| r (adjoint gradient of the decision loss)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -213,6 +216,8 @@ def main():
               "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}"}
     if args.alpha_steps:
         config["slopes"] = f"{args.alpha_steps} projected-Adam steps (lr {args.alpha_lr}) per undecided box"
+    if args.split == "gradient":
+        config["split"] = "per box: largest |dM/dr_i| r_i over the 16 dimensions of largest |dM/dr_i| w_i at the root"
 
     if args.impl == "reference":
         if rank != 0:
@@ -260,14 +265,21 @@ def main():
     if args.precision == "tf32":
         tile["precision"] = pkg.PREC_TC_TF32
         config["precision"] = "split-TF32 tensor-core contraction (tcgen05), FP32 re-bound and FP64 re-check"
-    fixed = None
-    if args.alpha_steps:
+    fixed = fixed_split = None
+    if args.alpha_steps or args.split == "gradient":
+        # the plain path (fixed slopes, widest side), for the comparison below
         c.set_options(**tile)
-        fixed = c.count(D)      # the fixed-slope count, for the comparison below
+        fixed = c.count(D)
+    if args.split == "gradient":
+        tile["split_rule"] = pkg.SPLIT_GRADIENT
+        if args.alpha_steps:
+            c.set_options(alpha_cap=args.alpha_cap, **tile)
+            fixed_split = c.count(D)     # fixed slopes, gradient split
+    if args.alpha_steps:
         c.set_options(profile=1, alpha_steps=args.alpha_steps, alpha_lr=args.alpha_lr, alpha_cap=args.alpha_cap,
                       **tile)
     else:
-        c.set_options(profile=1, **tile)
+        c.set_options(profile=1, alpha_cap=args.alpha_cap, **tile)
     for _ in range(args.warmup):
         c.count(D)
 
@@ -373,13 +385,16 @@ def main():
             "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks,
         }
+        def summary(x):
+            return {"unsafe_lo": x["unsafe_lo"], "unsafe_hi": x["unsafe_hi"], "boxes": x["boxes"],
+                    "device_ms": x["device_ms"], "boxes_per_s": x["boxes"] / (x["device_ms"] / 1e3)}
         if fixed is not None:
             line["slope_opt"] = {
                 "alpha_boxes": last["alpha_boxes"], "alpha_decided": last["alpha_decided"],
                 "alpha_ms_per_step": alpha_ms / args.steps,
-                "fixed_slopes": {"unsafe_lo": fixed["unsafe_lo"], "unsafe_hi": fixed["unsafe_hi"],
-                                 "boxes": fixed["boxes"], "device_ms": fixed["device_ms"],
-                                 "boxes_per_s": fixed["boxes"] / (fixed["device_ms"] / 1e3)}}
+                "fixed_slopes": summary(fixed)}
+            if fixed_split is not None:
+                line["slope_opt"]["fixed_slopes_gradient_split"] = summary(fixed_split)
         print(json.dumps(line))
     c.close()
     if dist is not None:
