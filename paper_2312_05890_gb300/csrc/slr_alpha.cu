@@ -20,12 +20,11 @@
 
 #include "slr_kernels.h"
 #include "slr_eval.cuh"
+#include "slr_adj_common.cuh"
 
 namespace slr {
 
 namespace {
-
-__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
 struct AdjSmem {
     float *U, *L;        // pre-activation equations of the current layer, n x Q (Q = d + 1)
@@ -283,55 +282,13 @@ __device__ void recompute(const AdjArgs &a, const Group &g, int layer) {
     }
 }
 
-// In-kernel loss on the row bounds of one box, towards the nearer decision
-// (Sec. 3 check): SAFE needs every clause to have a row with hi < 0, so the
-// safe loss is sum_c max(0, min_{r in c} hi_r); UNSAFE needs some clause with
-// every lo_r >= 0, so the unsafe loss is min_c max(0, -min_{r in c} lo_r).
-// The direction is fixed at the first step.  Sets glo, ghi.
+// The decision loss of one box (decision_grad).  The direction is kept from
+// the first step of an optimisation; without a direction array it is chosen
+// afresh and not kept.
 __device__ void decision_loss(const AdjArgs &a, const AdjSmem &s, int64_t pos) {
-    const NetParams<float> &net = a.net;
-    const int R = net.R;
-    for (int r = 0; r < R; ++r) {
-        s.glo[r] = 0.f;
-        s.ghi[r] = 0.f;
-    }
-    float safe_gap = 0.f, unsafe_gap = INFINITY;
-    int best_c = -1;
-    int r0 = 0;
-    for (int c = 0; c < net.n_clauses; ++c) {
-        const int r1 = net.clause_end[c];
-        float mh = INFINITY, ml = INFINITY;
-        for (int r = r0; r < r1; ++r) {
-            mh = fminf(mh, s.hi[r]);
-            ml = fminf(ml, s.lo[r]);
-        }
-        safe_gap += fmaxf(mh, 0.f);
-        const float ug = fmaxf(-ml, 0.f);
-        if (ug < unsafe_gap) {
-            unsafe_gap = ug;
-            best_c = c;
-        }
-        r0 = r1;
-    }
-    // direction: kept from the first step of an optimisation; chosen afresh
-    // (and not kept) without a direction array
-    int8_t dir = (a.alpha_mode == kAlphaInit || a.dir == nullptr) ? 0 : a.dir[pos];
-    if (dir == 0) {
-        dir = safe_gap <= unsafe_gap ? 1 : 2;
-        if (a.dir != nullptr) a.dir[pos] = dir;
-    }
-    r0 = 0;
-    for (int c = 0; c < net.n_clauses; ++c) {
-        const int r1 = net.clause_end[c];
-        int rh = r0, rl = r0;
-        for (int r = r0; r < r1; ++r) {
-            if (s.hi[r] < s.hi[rh]) rh = r;
-            if (s.lo[r] < s.lo[rl]) rl = r;
-        }
-        if (dir == 1 && s.hi[rh] > 0.f) s.ghi[rh] += 1.f;
-        if (dir == 2 && c == best_c && s.lo[rl] < 0.f) s.glo[rl] = -1.f;
-        r0 = r1;
-    }
+    const int8_t dir = (a.alpha_mode == kAlphaInit || a.dir == nullptr) ? 0 : a.dir[pos];
+    const int8_t got = decision_grad(a.net, s.lo, s.hi, s.glo, s.ghi, dir);
+    if (dir == 0 && a.dir != nullptr) a.dir[pos] = got;
 }
 
 // Folded-layer weight gradients (R rows) of one box, unfolded with the
@@ -595,19 +552,7 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
                 }
                 const int64_t ai = pos * H + off + j;
                 if (a.d_alpha != nullptr) a.d_alpha[ai] = g_alpha;
-                if (a.adam_t > 0 && a.alpha_mode != kAlphaDefault) {
-                    // projected Adam on the loss: descend, then clip to [0, 1]
-                    const float m0 = a.adam_t == 1 ? 0.f : a.adam_m[ai];
-                    const float v0 = a.adam_t == 1 ? 0.f : a.adam_v[ai];
-                    const float mm = a.beta1 * m0 + (1.f - a.beta1) * g_alpha;
-                    const float vv = a.beta2 * v0 + (1.f - a.beta2) * g_alpha * g_alpha;
-                    a.adam_m[ai] = mm;
-                    a.adam_v[ai] = vv;
-                    const float mh = mm / (1.f - a.beta1_t);
-                    const float vh = vv / (1.f - a.beta2_t);
-                    const float nv = al - a.lr * mh / (sqrtf(vh) + a.eps);
-                    a.alpha[ai] = fminf(fmaxf(nv, 0.f), 1.f);
-                }
+                if (a.adam_t > 0 && a.alpha_mode != kAlphaDefault) a.alpha[ai] = adam_slope(a, ai, al, g_alpha);
             }
             __syncthreads();
         }

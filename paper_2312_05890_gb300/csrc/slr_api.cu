@@ -106,6 +106,13 @@ struct slr_ctx {
     const float *wa_hi[slr::kMaxLayers] = {}, *wa_lo[slr::kMaxLayers] = {};
     const float *w0t = nullptr;           // layer 1 transposed (d x n_1)
     int w_Kpad[slr::kMaxLayers] = {};
+    // transposed pieces (W_k^T, |W_k|^T) for the adjoint's backward products
+    const float *wt_hi[slr::kMaxLayers] = {}, *wt_lo[slr::kMaxLayers] = {};
+    const float *wta_hi[slr::kMaxLayers] = {}, *wta_lo[slr::kMaxLayers] = {};
+    int wt_Kpad[slr::kMaxLayers] = {};
+    void *wadj_buf = nullptr;             // the wide adjoint's chunk state
+    size_t wadj_bytes = 0;
+    int wadj_Bc = 0;
     void *wide_buf = nullptr;             // chunk state
     size_t wide_buf_bytes = 0;
     std::vector<cudaEvent_t> gemm_ev;     // profile: a pair around each product launch
@@ -507,13 +514,17 @@ int build_wide(slr_ctx *ctx, const HostLayers<float> &L) {
     int np = 32;
     for (int k = 1; k <= K; ++k) np = std::max(np, (nf.n[k] + 31) & ~31);
     ctx->wide_NP = np;
-    std::vector<size_t> offs(K, 0);
+    std::vector<size_t> offs(K, 0), offs_t(K, 0);
     size_t total = align_up((size_t)d * nf.n[1] * sizeof(float));   // W_1 transposed first
     for (int k = 1; k < K; ++k) {
         const int Mpad = (nf.n[k + 1] + 127) & ~127, Kpad = (nf.n[k] + 31) & ~31;
         ctx->w_Kpad[k] = Kpad;
         offs[k] = total;
         total += 4 * align_up((size_t)Mpad * Kpad * sizeof(float));
+        const int MpadT = (nf.n[k] + 127) & ~127, KpadT = (nf.n[k + 1] + 31) & ~31;
+        ctx->wt_Kpad[k] = KpadT;
+        offs_t[k] = total;
+        total += 4 * align_up((size_t)MpadT * KpadT * sizeof(float));
     }
     if (ctx->wide_img) cudaFree(ctx->wide_img);
     ctx->wide_img = nullptr;
@@ -530,6 +541,12 @@ int build_wide(slr_ctx *ctx, const HostLayers<float> &L) {
             float *lo = (float *)(host.data() + offs[k] + one);
             float *ahi = (float *)(host.data() + offs[k] + 2 * one);
             float *alo = (float *)(host.data() + offs[k] + 3 * one);
+            const int KpadT = ctx->wt_Kpad[k];
+            const size_t oneT = align_up((size_t)((n_in + 127) & ~127) * KpadT * sizeof(float));
+            float *thi = (float *)(host.data() + offs_t[k]);
+            float *tlo = (float *)(host.data() + offs_t[k] + oneT);
+            float *tahi = (float *)(host.data() + offs_t[k] + 2 * oneT);
+            float *talo = (float *)(host.data() + offs_t[k] + 3 * oneT);
             for (int p = 0; p < n_out; ++p) {
                 for (int i = 0; i < n_in; ++i) {
                     const float v = L.W[k][(size_t)i * n_out + p];   // transposed float weights
@@ -540,6 +557,11 @@ int build_wide(slr_ctx *ctx, const HostLayers<float> &L) {
                     lo[o] = l;
                     ahi[o] = std::fabs(h);
                     alo[o] = v >= 0.f ? l : -l;
+                    const size_t ot = (size_t)i * KpadT + p;
+                    thi[ot] = h;
+                    tlo[ot] = l;
+                    tahi[ot] = std::fabs(h);
+                    talo[ot] = v >= 0.f ? l : -l;
                 }
             }
         }
@@ -555,6 +577,12 @@ int build_wide(slr_ctx *ctx, const HostLayers<float> &L) {
             ctx->w_lo[k] = (const float *)(b + one);
             ctx->wa_hi[k] = (const float *)(b + 2 * one);
             ctx->wa_lo[k] = (const float *)(b + 3 * one);
+            const size_t oneT = align_up((size_t)((nf.n[k] + 127) & ~127) * ctx->wt_Kpad[k] * sizeof(float));
+            const unsigned char *bt = (const unsigned char *)ctx->wide_img + offs_t[k];
+            ctx->wt_hi[k] = (const float *)bt;
+            ctx->wt_lo[k] = (const float *)(bt + oneT);
+            ctx->wta_hi[k] = (const float *)(bt + 2 * oneT);
+            ctx->wta_lo[k] = (const float *)(bt + 3 * oneT);
         }
     }
     // chunk: the boxes whose state fits about 3 GB
@@ -654,6 +682,109 @@ int run_wide(slr_ctx *ctx, const slr::BoxSource &src, int64_t n, const slr::Eval
         CK(ctx, slr::launch_wide_classify(nf, nb, base, lo, hi, er, bidx, out, sms, ctx->stream));
         *launches += 1;
     }
+    return SLR_OK;
+}
+
+// The adjoint on the wide path for positions [0, n) of a.src (the device count
+// when a.count is set): per chunk, the forward products keeping each hidden
+// layer's pre-activation equations, the rows and their adjoints, the backward
+// products through W^T and |W|^T with the relaxations between them, and the
+// box gradient and split choice.
+int run_wide_adjoint(slr_ctx *ctx, const slr::AdjArgs &a, int64_t *launches) {
+    const slr::NetParams<float> &nf = ctx->nf;
+    const int K = nf.K, d = nf.d, Q = d + 1, np = ctx->wide_NP, sms = ctx->sm_count;
+    int64_t n = a.n;
+    if (a.count != nullptr) {
+        unsigned long long c = 0;
+        CK(ctx, cudaMemcpyAsync(&c, a.count, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        n = std::min<int64_t>(n, (int64_t)c);
+    }
+    if (n <= 0) return SLR_OK;
+    // chunk: the boxes whose state fits about 6 GB
+    const size_t eq = (size_t)Q * np;
+    const size_t per_box = sizeof(float) * (eq * (size_t)(2 * (K - 1) - 1 + 6) + 5 * (size_t)(K - 1) * np +
+                                            3 * (size_t)d) + 64 * 16;
+    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(((size_t)6 << 30) / per_box)));
+    const size_t need = per_box * (size_t)bc + ((size_t)64 << 10);
+    if (ctx->wadj_bytes < need) {
+        cudaFree(ctx->wadj_buf);
+        ctx->wadj_buf = nullptr;
+        ctx->wadj_bytes = 0;
+        CK(ctx, cudaMalloc(&ctx->wadj_buf, need));
+        ctx->wadj_bytes = need;
+    }
+    unsigned char *p = (unsigned char *)ctx->wadj_buf;
+    auto take = [&](size_t floats) {
+        float *q = (float *)p;
+        p += align_up(floats * sizeof(float));
+        return q;
+    };
+    float *m = take((size_t)bc * d), *r = take((size_t)bc * d), *gr = take((size_t)bc * d);
+    float *Cl[slr::kMaxLayers] = {}, *Rl[slr::kMaxLayers] = {};
+    for (int k = 1; k < K; ++k) {
+        Cl[k] = take((size_t)bc * eq);
+        Rl[k] = k > 1 ? take((size_t)bc * eq) : nullptr;   // layer 1: U = L
+    }
+    float *Cf = take((size_t)bc * eq), *Rf = take((size_t)bc * eq);
+    float *Pc = take((size_t)bc * eq), *Pr = take((size_t)bc * eq);
+    float *gC = take((size_t)bc * eq), *gR = take((size_t)bc * eq);
+    const int64_t sstride = bc * np;
+    float *sc = take((size_t)5 * (K - 1) * sstride);
+    for (int64_t pos0 = 0; pos0 < n; pos0 += bc) {
+        const int nb = (int)std::min<int64_t>(bc, n - pos0);
+        CK(ctx, slr::launch_wadj_box(a.src, pos0, nb, d, m, r, sms, ctx->stream));
+        CK(ctx, slr::launch_wadj_layer1(nf, ctx->w0t, nb, np, m, r, Cl[1], ctx->stream));
+        *launches += 2;
+        for (int k = 1; k < K; ++k) {
+            float *sck = sc + (size_t)(k - 1) * 5 * sstride;
+            CK(ctx, slr::launch_wadj_fwd(a, k, pos0, nb, np, Cl[k], Rl[k], k > 1 ? nf.b[k - 1] : nullptr, sck,
+                                         sstride, Pc, Pr, ctx->stream));
+            slr::WideGemmArgs ga{};
+            ga.status = ctx->status;
+            float *oc = k + 1 < K ? Cl[k + 1] : Cf, *orr = k + 1 < K ? Rl[k + 1] : Rf;
+            ga.g[0] = slr::WideGemm{ctx->w_hi[k], ctx->w_lo[k], Pc, oc, nf.n[k + 1], nf.n[k], ctx->w_Kpad[k],
+                                    nb * Q, np, np};
+            ga.g[1] = slr::WideGemm{ctx->wa_hi[k], ctx->wa_lo[k], Pr, orr, nf.n[k + 1], nf.n[k], ctx->w_Kpad[k],
+                                    nb * Q, np, np};
+            CK(ctx, slr::launch_wide_gemm(ga, 2, ctx->stream));
+            *launches += 2;
+        }
+        CK(ctx, slr::launch_wadj_rows(a, pos0, nb, np, Cf, Rf, nf.b[K - 1], gC, gR, ctx->stream));
+        *launches += 1;
+        for (int k = K - 1; k >= 1; --k) {
+            slr::WideGemmArgs ga{};
+            ga.status = ctx->status;
+            ga.g[0] = slr::WideGemm{ctx->wt_hi[k], ctx->wt_lo[k], gC, Pc, nf.n[k], nf.n[k + 1], ctx->wt_Kpad[k],
+                                    nb * Q, np, np};
+            ga.g[1] = slr::WideGemm{ctx->wta_hi[k], ctx->wta_lo[k], gR, Pr, nf.n[k], nf.n[k + 1], ctx->wt_Kpad[k],
+                                    nb * Q, np, np};
+            CK(ctx, slr::launch_wide_gemm(ga, 2, ctx->stream));
+            const float *sck = sc + (size_t)(k - 1) * 5 * sstride;
+            CK(ctx, slr::launch_wadj_bwd(a, k, pos0, nb, np, Cl[k], Rl[k], sck, sstride, Pc, Pr, gC,
+                                         k > 1 ? gR : nullptr, ctx->stream));
+            *launches += 2;
+        }
+        if (a.d_lo != nullptr || a.d_r != nullptr || a.split_codes != nullptr) {
+            CK(ctx, slr::launch_wadj_boxgrad(a, pos0, nb, np, ctx->w0t, gC, gr, sms, ctx->stream));
+            *launches += 1;
+            if (a.split_codes != nullptr) {
+                CK(ctx, slr::launch_wadj_split(a, pos0, nb, gr, r, sms, ctx->stream));
+                *launches += 1;
+            }
+        }
+    }
+    return SLR_OK;
+}
+
+// The adjoint of `a`: on the wide path by per-layer products (no weight
+// gradients there), else the one-box-per-CTA kernel.
+int run_adjoint(slr_ctx *ctx, const slr::AdjArgs &a, int grid, int64_t *launches) {
+    bool weights = false;
+    for (int k = 0; k < ctx->nf.K; ++k) weights = weights || a.dW[k] != nullptr || a.db[k] != nullptr;
+    if (ctx->wide && ctx->nf.K > 1 && !weights) return run_wide_adjoint(ctx, a, launches);
+    CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+    *launches += 1;
     return SLR_OK;
 }
 
@@ -989,6 +1120,7 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->adj_scratch);
     if (ctx->wide_helper) slr_destroy(ctx->wide_helper);
     cudaFree(ctx->split_buf);
+    cudaFree(ctx->wadj_buf);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -2115,13 +2247,12 @@ int optimise_slopes(slr_ctx *ctx, const slr::BoxSource &src, int64_t cap, const 
     a.adam_v = b.v;
     if (steps == 0 && want_alpha) {
         a.alpha_mode = slr::kAlphaInit;
-        CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
-        *launches += 1;
+        if ((rc = run_adjoint(ctx, a, grid, launches))) return rc;
     }
     for (int t = 1; t <= steps; ++t) {
         a.alpha_mode = t == 1 ? slr::kAlphaInit : slr::kAlphaFree;
         adam_step(a, t, lr);
-        CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+        if ((rc = run_adjoint(ctx, a, grid, launches))) return rc;
         if ((rc = eval_by_position(ctx, src, b.alpha, b.lo_new, b.hi_new, cap))) return rc;
         const bool last = t == steps;
         CK(ctx, slr::launch_merge_bounds(ctx->nf, cap, count, b.lo_new, b.hi_new, b.lo_best, b.hi_best,
@@ -2182,8 +2313,8 @@ int slr_internal_split_root(slr_ctx *ctx, const slr::BoxSource &root, int64_t *l
     a.count = nullptr;
     a.alpha_mode = slr::kAlphaDefault;
     a.d_r = grad;
-    CK(ctx, slr::launch_adjoint(a, 1, ctx->stream));
-    *launches += 1;
+    int rc = run_adjoint(ctx, a, 1, launches);
+    if (rc) return rc;
     std::vector<float> g(d);
     CK(ctx, cudaMemcpyAsync(g.data(), grad, (size_t)d * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -2245,9 +2376,7 @@ int slr_internal_split_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t
     a.n_split = (int)ctx->split_set.size();
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((cap + ctx->adj_boxes - 1) / ctx->adj_boxes,
                                                                  ctx->adj_grid));
-    CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
-    *launches += 1;
-    return SLR_OK;
+    return run_adjoint(ctx, a, grid, launches);
 }
 
 extern "C" {
@@ -2366,7 +2495,9 @@ int slr_margin_backward(slr_ctx *ctx, int64_t n, const float *box_lo, const floa
             a.db[k] = db[k];
         }
         const int grid = (int)std::min<int64_t>((n + ctx->adj_boxes - 1) / ctx->adj_boxes, ctx->adj_grid);
-        CK(ctx, slr::launch_adjoint(a, grid, ctx->stream));
+        int64_t nl = 0;
+        int rc2 = run_adjoint(ctx, a, grid, &nl);
+        if (rc2) return rc2;
     }
     if (!on_device) {
         auto back = [&](float *host, const float *dev, size_t count) -> int {

@@ -98,6 +98,22 @@ size_t adjoint_smem_bytes(const AdjArgs &a);
 size_t adjoint_box_bytes(const AdjArgs &a);
 int adjoint_blocks_per_sm(size_t smem);
 cudaError_t launch_adjoint(const AdjArgs &a, int grid, cudaStream_t s);
+// The adjoint on the wide path (per-layer tensor-core products; slr_wide_adj.cu).
+cudaError_t launch_wadj_box(const BoxSource &src, int64_t pos0, int nb, int d, float *m, float *r, int sms,
+                            cudaStream_t s);
+cudaError_t launch_wadj_layer1(const NetParams<float> &net, const float *W0t, int nb, int NP, const float *m,
+                               const float *r, float *C, cudaStream_t s);
+cudaError_t launch_wadj_fwd(const AdjArgs &a, int layer, int64_t pos0, int nb, int NP, float *C, const float *R,
+                            const float *bias, float *sc, int64_t sstride, float *Pc, float *Pr, cudaStream_t s);
+cudaError_t launch_wadj_rows(const AdjArgs &a, int64_t pos0, int nb, int NP, const float *C, const float *R,
+                             const float *bias, float *gC, float *gR, cudaStream_t s);
+cudaError_t launch_wadj_bwd(const AdjArgs &a, int layer, int64_t pos0, int nb, int NP, const float *C, const float *R,
+                            const float *sc, int64_t sstride, const float *gPc, const float *gPr, float *gC, float *gR,
+                            cudaStream_t s);
+cudaError_t launch_wadj_boxgrad(const AdjArgs &a, int64_t pos0, int nb, int NP, const float *W0t, const float *gC1,
+                                float *gr, int sms, cudaStream_t s);
+cudaError_t launch_wadj_split(const AdjArgs &a, int64_t pos0, int nb, const float *gr, const float *r, int sms,
+                              cudaStream_t s);
 cudaError_t launch_merge_bounds(const NetParams<float> &net, int64_t n, const unsigned long long *count,
                                 const float *lo_new, const float *hi_new, float *lo_best, float *hi_best,
                                 uint8_t *cls_pos, uint8_t *cls_idx, const int64_t *index, int first,

@@ -316,6 +316,60 @@ def test_wide_adjoint_matches_tile_adjoint(pkg, free):
         assert np.abs(a["d_W"][k] - b["d_W"][k]).max() <= 1e-5 * scale
 
 
+def _boxes_differing(a, b, keys, n, rtol):
+    """Boxes where some array of `keys` differs by more than rtol of that box's scale."""
+    bad = set()
+    for key in keys:
+        x = np.asarray(a[key], np.float64).reshape(n, -1)
+        y = np.asarray(b[key], np.float64).reshape(n, -1)
+        scale = np.abs(x).max(axis=1, keepdims=True) + 1e-6
+        bad |= set(np.nonzero((np.abs(x - y) / scale).max(axis=1) > rtol)[0].tolist())
+    return bad
+
+
+@pytest.mark.parametrize("free", [True, False])
+def test_wide_product_adjoint_matches_tile_adjoint(pkg, free):
+    """Without weight gradients the wide path runs the adjoint as per-layer
+    tensor-core products (three-term TF32); it agrees with the one-box kernel
+    to float rounding (at most one box may sit on a ReLU case boundary that
+    the two summation orders resolve differently)."""
+    p = gen.make("acas")
+    n = 64
+    lo, hi = random_sub_boxes(p, n, seed=9)
+    R = p.prop.C.shape[0]
+    rng = np.random.default_rng(4)
+    g_lo = rng.normal(size=(n, R)).astype(np.float32)
+    g_hi = rng.normal(size=(n, R)).astype(np.float32)
+    with _counter(pkg, p) as c:
+        H = c.alpha_width()
+        A = rng.uniform(0.05, 0.95, size=(n, H)).astype(np.float32) if free else None
+        a = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A)
+    with _counter(pkg, p, wide=1) as c:
+        b = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A)
+    keys = ("row_lo", "row_hi", "d_lo", "d_hi") + (("d_alpha",) if free else ())
+    assert len(_boxes_differing(a, b, keys, n, 1e-4)) <= 1
+
+
+def test_wide_product_adjoint_mnist_shaped(pkg):
+    """784 -> 3x256 -> 10: the per-layer product adjoint against the one-box
+    global-memory kernel (which the weight gradients select), slopes free and
+    default."""
+    p = gen.make("mnist")
+    n = 6
+    lo, hi = random_sub_boxes(p, n, seed=6, min_frac=0.5)
+    R = p.prop.C.shape[0]
+    rng = np.random.default_rng(5)
+    g_lo = rng.normal(size=(n, R)).astype(np.float32)
+    g_hi = rng.normal(size=(n, R)).astype(np.float32)
+    with _counter(pkg, p) as c:
+        H = c.alpha_width()
+        for A in (None, rng.uniform(0.05, 0.95, size=(n, H)).astype(np.float32)):
+            fast = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A)
+            slow = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A, weights=True)
+            keys = ("row_lo", "row_hi", "d_lo", "d_hi") + (("d_alpha",) if A is not None else ())
+            assert len(_boxes_differing(fast, slow, keys, n, 1e-4)) <= 1
+
+
 def test_wide_slopes_mnist_shaped(pkg):
     """784 -> 3x256 -> 10: optimised slopes give sound bounds no looser than the default."""
     p = gen.make("mnist")
