@@ -725,15 +725,18 @@ struct EvalTile {
         const int QW = (d + 1) * T / 4;       // quads of C coefficient columns and the constant column
         const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
         const int Q = QW + QA;
-        const int total = (Mpad / 8) * Q;
+        const int G = Mpad / 8;               // groups of 8 output rows
+        const int total = G * Q;
+        // items column-quad-major: the lanes of a warp share the quad's kind
+        // (W or |W| products), so the branch below is uniform in all but one warp
         const int n_const = delta ? net.n[layer + 1] : ((net.n[layer + 1] + 1) / 2) * T;
         Real acc[kItems][8][4];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const int item = threadIdx.x + it * NT;
             if (item < total) {
-                const int g = item / Q;
-                const int q = item - g * Q;
+                const int q = item / G;
+                const int g = item - q * G;
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
                 tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
@@ -753,8 +756,8 @@ struct EvalTile {
         for (int it = 0; it < kItems; ++it) {
             const int item = threadIdx.x + it * NT;
             if (item < total) {
-                const int g = item / Q;
-                const int q = item - g * Q;
+                const int q = item / G;
+                const int g = item - q * G;
                 const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) V4<Real>::st(S + (g * 8 + r) * NS + j0, acc[it][r]);
