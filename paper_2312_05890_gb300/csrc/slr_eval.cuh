@@ -674,6 +674,19 @@ struct EvalTile {
     // then, after a barrier, overwrites the rows.
     static constexpr int kItems = KI;
 
+    // Row group g and column quad q (q < QW: W products, else |W|) of product tile `item`.
+    static __device__ __forceinline__ void item_tile(int item, int G, int QW, int QA, int &g, int &q) {
+        const int nW = G * QW;
+        if (item < nW) {
+            g = item / QW;
+            q = item - g * QW;
+        } else {
+            const int k = item - nW;
+            g = k / QA;
+            q = QW + (k - g * QA);
+        }
+    }
+
     static __device__ __forceinline__ void tile_mac(const Real *wp, const Real *xp, int n_in, int Mpad, int NS,
                                                     bool is_abs, Real (&acc)[8][4]) {
 #pragma unroll
@@ -727,16 +740,17 @@ struct EvalTile {
         const int Q = QW + QA;
         const int G = Mpad / 8;               // groups of 8 output rows
         const int total = G * Q;
-        // items column-quad-major: the lanes of a warp share the quad's kind
-        // (W or |W| products), so the branch below is uniform in all but one warp
+        // items: first every W product tile, then every |W| one, each row-group
+        // major, so that the branch below diverges in one warp only and a warp's
+        // lanes share their weights and write neighbouring columns
         const int n_const = delta ? net.n[layer + 1] : ((net.n[layer + 1] + 1) / 2) * T;
         Real acc[kItems][8][4];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const int item = threadIdx.x + it * NT;
             if (item < total) {
-                const int q = item / G;
-                const int g = item - q * G;
+                int g, q;
+                item_tile(item, G, QW, QA, g, q);
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
                 tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
@@ -756,8 +770,8 @@ struct EvalTile {
         for (int it = 0; it < kItems; ++it) {
             const int item = threadIdx.x + it * NT;
             if (item < total) {
-                const int q = item / G;
-                const int g = item - q * G;
+                int g, q;
+                item_tile(item, G, QW, QA, g, q);
                 const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) V4<Real>::st(S + (g * 8 + r) * NS + j0, acc[it][r]);
