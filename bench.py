@@ -200,16 +200,15 @@ def main():
                          "with the largest |dM/dr| r (adjoint gradient of the decision loss)")
     args = ap.parse_args()
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2312_05890_gb300 import multirank
+    world, rank, local_rank = multirank.rank_env()
     procs = os.cpu_count() or 1
 
     from workloads import generators as gen
     if args.workload == "batch":
         return bench_batch(args, world, rank, local_rank)
     # weak scaling: rank r counts its own problem of the same shape (seed + r)
-    p = gen.make(args.workload, args.seed + rank)
+    p = gen.make(args.workload, multirank.weak_seed(args.seed, rank))
     D = args.depth or p.depth
     workload = f"{p.name} D={D} seed={args.seed}"
     config = {"workload": workload, "widths": p.net.widths, "depth": D, "rows": p.prop.R,
@@ -243,17 +242,13 @@ def main():
         return
 
     import torch
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local_rank)
+    dist = multirank.init(world)
     import paper_2312_05890_gb300 as pkg
     pkg.load_library()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        multirank.barrier(dist)
 
     flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device="cuda")
     c = pkg.Counter(local_rank)
@@ -311,14 +306,7 @@ def main():
     clocks = sampler.stop()
     last = r
 
-    tot_ms = sum(dev_ms)
-    stats = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-    tot_boxes = torch.tensor([boxes], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(stats, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot_boxes, op=dist.ReduceOp.SUM)
-    max_ms = float(stats.item())
-    value = float(tot_boxes.item()) / (max_ms / 1e3)
+    max_ms, _, value = multirank.job_rate(sum(dev_ms), boxes, dist)
 
     # ---- e2e: upload network, box and property from host memory every step ------
     e2e_s = []
@@ -397,8 +385,7 @@ def main():
                 line["slope_opt"]["fixed_slopes_gradient_split"] = summary(fixed_split)
         print(json.dumps(line))
     c.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    multirank.finish(dist)
 
 
 def bench_batch(args, world, rank, local_rank):
@@ -406,14 +393,17 @@ def bench_batch(args, world, rank, local_rank):
     import torch
 
     import paper_2312_05890_gb300 as pkg
+    from paper_2312_05890_gb300 import multirank
     from workloads import generators as gen
     torch.cuda.set_device(local_rank)
-    probs = gen.batched_uneven(args.seed + rank)
+    dist = multirank.init(world)
+    probs = gen.batched_uneven(multirank.weak_seed(args.seed, rank))
     flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device="cuda")
     c = pkg.Counter(local_rank)
     for _ in range(args.warmup):
         c.count_batch(probs)
     torch.cuda.synchronize()
+    multirank.barrier(dist)
     sampler = ClockSampler(local_rank)
     sampler.start()
     ms, boxes, e2e = [], 0, []
@@ -425,11 +415,14 @@ def bench_batch(args, world, rank, local_rank):
         e2e.append(time.perf_counter() - t0)
         ms.append(res[0]["device_ms"])
         boxes += sum(r["boxes"] for r in res)
+    torch.cuda.synchronize()
+    multirank.barrier(dist)
     clocks = sampler.stop()
     per_boxes = sorted(r["boxes"] for r in res)
     levels = sorted(r["levels"] for r in res)
-    tot_s = sum(ms) / 1e3
-    value = boxes / tot_s
+    max_ms, tot_boxes, value = multirank.job_rate(sum(ms), boxes, dist)
+    tot_s = max_ms / 1e3
+    _, _, e2e_value = multirank.job_rate(1e3 * sum(e2e), boxes, dist)
     if rank == 0:
         print(json.dumps({
             "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
@@ -441,11 +434,12 @@ def bench_batch(args, world, rank, local_rank):
                        "tile_boxes": res[0]["tile"][0], "launches_per_step": res[0]["launches"]},
             "per_problem": {"boxes_min_median_max": [per_boxes[0], per_boxes[len(per_boxes) // 2], per_boxes[-1]],
                             "levels_min_max": [levels[0], levels[-1]]},
-            "e2e": {"value": boxes / sum(e2e), "unit": "boxes/s", "h2d_bytes_per_step": res[0]["h2d_bytes"],
+            "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": res[0]["h2d_bytes"],
                     "d2h_bytes_per_step": res[0]["d2h_bytes"]},
             "gpu_launches": res[0]["launches"] * args.steps, "clocks": clocks,
         }))
     c.close()
+    multirank.finish(dist)
 
 
 if __name__ == "__main__":
