@@ -126,6 +126,7 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
     RowBounds<float> bd;
     bd.reset();
     if (live) {
+#pragma unroll 4
         for (int j = sl; j < d; j += kSlicesY) {
             const float c = A::mul_rn(W0t[(size_t)j * n1 + p], rb[j]);
             R(j) = c;
@@ -185,7 +186,8 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
     if (live) {
         const RelaxPlan<float> pl = plan[lane];
         if (pl.kind != 0) {
-            for (int j = sl; j < d; j += kSlicesY) {
+    #pragma unroll 4
+        for (int j = sl; j < d; j += kSlicesY) {
                 float c = R(j), r = R(WTile::cR(d) + j);
                 WTile::apply_plan(pl, c, r);
                 R(j) = c;
@@ -285,6 +287,7 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
     RowBounds<float> bd;
     bd.reset();
     if (live)
+#pragma unroll 4
         for (int j = sl; j < d; j += kSlicesY) bd.add(R(j), R(WTile::cR(d) + j));
     part[sl][lane] = bd;
     __syncthreads();
@@ -307,7 +310,8 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
     if (live) {
         const RelaxPlan<float> pl = plan[lane];
         if (pl.kind != 0) {
-            for (int j = sl; j < d; j += kSlicesY) {
+    #pragma unroll 4
+        for (int j = sl; j < d; j += kSlicesY) {
                 float c = R(j), r = R(WTile::cR(d) + j);
                 WTile::apply_plan(pl, c, r);
                 R(j) = c;
@@ -341,6 +345,7 @@ wide_final_kernel(const NetParams<float> net, int NP, float gcoef, float *C, flo
     RowBounds<float> bd;
     bd.reset();
     if (live)
+#pragma unroll 4
         for (int j = sl; j < d; j += kSlicesY) bd.add(Rw(j), Rw(WTile::cR(d) + j));
     part[sl][lane] = bd;
     __syncthreads();
