@@ -260,6 +260,14 @@ int slr_schedule(slr_ctx *ctx, int D, int32_t *dims);
  * dimensions to dims (room for 16).  SLR_ESTATE after a widest-side count. */
 int slr_split_set(slr_ctx *ctx, int32_t *dims, int32_t *n);
 
+/* Failure detection check (no paper counterpart): runs, on the context's
+ * device and stream, the bounded wait that the tensor-core kernels use, on a
+ * barrier phase that nothing completes, giving up after `limit` polls
+ * (1..2^20).  Returns SLR_ETIMEOUT, as every count does when one of its waits
+ * gives up, and leaves the context usable; SLR_OK would mean the wait did not
+ * give up. */
+int slr_wait_selfcheck(slr_ctx *ctx, int32_t limit);
+
 /* One problem of a batch: a network, an input box, a property (as in
  * slr_load_network, slr_set_box and slr_set_property) and its depth cap. */
 typedef struct {

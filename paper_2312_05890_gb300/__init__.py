@@ -31,7 +31,7 @@ MAX_LEVELS = 63
 # Names the header declares (checked by the CPU test that loads the library).
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
-           "slr_split_set", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
+           "slr_split_set", "slr_wait_selfcheck", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
            "slr_optimize_alpha", "slr_last_error")
 
 
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
         "slr_leaves": (ctypes.c_int, [P, i64, P, P, P, ctypes.POINTER(i64)]),
         "slr_schedule": (ctypes.c_int, [P, ctypes.c_int, P]),
         "slr_split_set": (ctypes.c_int, [P, P, ctypes.POINTER(i32)]),
+        "slr_wait_selfcheck": (ctypes.c_int, [P, ctypes.c_int32]),
         "slr_count_noalloc": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
         "slr_count_batch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_problem), ctypes.POINTER(slr_result)]),
         "slr_last_error": (ctypes.c_char_p, [P]),
@@ -339,6 +340,12 @@ def slr_split_set(ctx):
     return out[:n.value].copy()
 
 
+def slr_wait_selfcheck(ctx, limit: int = 4096):
+    """A bounded device wait on a barrier nothing completes; raises SlrError (SLR_ETIMEOUT)."""
+    lib = load_library()
+    _check(lib, ctx, lib.slr_wait_selfcheck(ctx, int(limit)))
+
+
 def split_code_dims(code: int, depth: int, split_set):
     """(path, dims) of a SPLIT_GRADIENT code: the halves taken (bit depth-1-j for
     split j) and the input dimension of each split."""
@@ -469,3 +476,6 @@ class Counter:
 
     def split_set(self):
         return slr_split_set(self.ctx)
+
+    def wait_selfcheck(self, limit: int = 4096):
+        return slr_wait_selfcheck(self.ctx, limit)

@@ -1625,6 +1625,24 @@ int slr_schedule(slr_ctx *ctx, int D, int32_t *dims) {
     return SLR_OK;
 }
 
+int slr_wait_selfcheck(slr_ctx *ctx, int32_t limit) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (limit < 1 || limit > (1 << 20)) return fail(ctx, SLR_EINVAL, "limit %d out of range [1, 2^20]", limit);
+    CK(ctx, cudaSetDevice(ctx->device));
+    unsigned int *d_status = nullptr;
+    CK(ctx, cudaMalloc(&d_status, sizeof(unsigned int)));
+    unsigned int st = 0;
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof st, ctx->stream);
+    if (e == cudaSuccess) e = slr::launch_wait_selfcheck(d_status, limit, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d_status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d_status);
+    if (e != cudaSuccess) return fail(ctx, SLR_ECUDA, "%s", cudaGetErrorString(e));
+    if (st & slr::kStatusTimeout)
+        return fail(ctx, SLR_ETIMEOUT, "a bounded device wait gave up after %d polls", limit);
+    return SLR_OK;
+}
+
 int slr_split_set(slr_ctx *ctx, int32_t *dims, int32_t *n) {
     if (!ctx || !dims || !n) return fail(ctx, SLR_EINVAL, "null argument");
     if (ctx->split_set.empty()) return fail(ctx, SLR_ESTATE, "the last count did not use the gradient split rule");

@@ -598,6 +598,18 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmA
 
 size_t wide_gemm_smem_bytes() { return 2 * (size_t)kWStage + 64; }
 
+// The bounded wait of the tensor-core kernels on a barrier whose phase nothing
+// completes: it must give up after `limit` polls and report kStatusTimeout.
+__global__ void wait_selfcheck_kernel(unsigned int *status, int limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0u, limit)) atomicOr(status, kStatusTimeout);
+}
+
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
@@ -648,6 +660,11 @@ cudaError_t launch_wide_classify(const NetParams<float> &net, int nb, int64_t ba
                                  const float *err, const int64_t *bidx, const EvalOutputs &out, int sms,
                                  cudaStream_t s) {
     wide_classify_kernel<<<grid_for(nb, sms), 256, 0, s>>>(net, nb, base, lo, hi, err, bidx, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selfcheck(unsigned int *status, int limit, cudaStream_t s) {
+    wait_selfcheck_kernel<<<1, 32, 0, s>>>(status, limit);
     return cudaGetLastError();
 }
 

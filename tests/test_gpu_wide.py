@@ -99,3 +99,17 @@ def test_mnist_shaped_count_small_depth(pkg):
     ref = oracle.count(p.net, p.lo, p.hi, p.prop, 4)
     assert r["unsafe_lo"] <= ref.unsafe_lo <= ref.unsafe_hi <= r["unsafe_hi"]
     assert r["boxes"] >= ref.boxes
+
+
+def test_bounded_wait_gives_up_and_context_survives(pkg):
+    """Failure detection: the tensor-core kernels' bounded wait, on a barrier
+    nothing completes, returns SLR_ETIMEOUT; the context then counts correctly."""
+    p = gen.make("tiny")
+    with _counter(pkg, p) as c:
+        with pytest.raises(pkg.SlrError, match="ETIMEOUT"):
+            c.wait_selfcheck(4096)
+        with pytest.raises(pkg.SlrError, match="EINVAL"):
+            c.wait_selfcheck(0)
+        r = c.count(10)
+    ref = oracle.count(p.net, p.lo, p.hi, p.prop, 10)
+    assert (r["unsafe_lo"], r["unsafe_hi"]) == (ref.unsafe_lo, ref.unsafe_hi)
