@@ -423,6 +423,29 @@ def bench_batch(args, world, rank, local_rank):
     max_ms, tot_boxes, value = multirank.job_rate(sum(ms), boxes, dist)
     tot_s = max_ms / 1e3
     _, _, e2e_value = multirank.job_rate(1e3 * sum(e2e), boxes, dist)
+    # roofline: the algorithmic FLOPs of every problem's boxes over the whole
+    # step's device time (evaluation, re-check and compaction together)
+    flops = sum(algorithmic_flops_per_box(p.net.widths, p.prop.R) * r["boxes"] for p, r in zip(probs, res))
+    clk = clocks.get("sm_mhz") or 2070.0
+    peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    achieved = flops * args.steps / (sum(ms) / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "slr_eval_batch_kernel<float>",
+                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk:.0f} MHz (sampled median)",
+                "time_basis": "whole step (all kernels), so a lower bound on the kernel's own rate"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        cb = 0
+        for p in probs:
+            cb += oracle.count(p.net, p.lo, p.hi, p.prop, p.depth, max_boxes=4096).boxes
+            if time.perf_counter() - t0 > args.cpu_budget:
+                break
+        cs = time.perf_counter() - t0
+        cpu = {"value": cb / cs, "unit": "boxes/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first levels (at most 4096 boxes) of the batch's problems in order, {cb} boxes, "
+                         f"{cs:.1f} s, one process"}
     if rank == 0:
         print(json.dumps({
             "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
@@ -434,6 +457,7 @@ def bench_batch(args, world, rank, local_rank):
                        "tile_boxes": res[0]["tile"][0], "launches_per_step": res[0]["launches"]},
             "per_problem": {"boxes_min_median_max": [per_boxes[0], per_boxes[len(per_boxes) // 2], per_boxes[-1]],
                             "levels_min_max": [levels[0], levels[-1]]},
+            "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": res[0]["h2d_bytes"],
                     "d2h_bytes_per_step": res[0]["d2h_bytes"]},
             "gpu_launches": res[0]["launches"] * args.steps, "clocks": clocks,
