@@ -745,27 +745,63 @@ struct EvalTile {
         // lanes share their weights and write neighbouring columns
         const int n_const = delta ? net.n[layer + 1] : ((net.n[layer + 1] + 1) / 2) * T;
         Real acc[kItems][8][4];
+        // few tiles (the property rows): each tile's inputs in two halves on a
+        // pair of neighbouring lanes, added in a fixed order after the products
+        const bool split = 2 * total <= NT && n_in >= 8;
+        const int busy = split ? 2 * total : total;   // threads busy with products
+        if (split) {
+            const int item = (int)threadIdx.x >> 1, half = (int)threadIdx.x & 1;
 #pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            const int item = threadIdx.x + it * NT;
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[0][r][c] = 0;
             if (item < total) {
                 int g, q;
                 item_tile(item, G, QW, QA, g, q);
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-                tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
+                const int i0 = half ? n_in / 2 : 0;
+                tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, half ? n_in - n_in / 2 : n_in / 2, Mpad, NS,
+                         is_abs, acc[0]);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[0][r][c] += __shfl_xor_sync(0xffffffffu, acc[0][r][c], 1);
+        } else {
+#pragma unroll
+            for (int it = 0; it < kItems; ++it) {
+                const int item = threadIdx.x + it * NT;
+                if (item < total) {
+                    int g, q;
+                    item_tile(item, G, QW, QA, g, q);
+                    const bool is_abs = q >= QW;
+                    const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
+                    tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
+                }
             }
         }
-        // combined index space [0, total + n_const): indices past `total` are constants
+        // combined index space [0, busy + n_const): indices past `busy` are constants
         {
-            int idx = threadIdx.x + ((total - (int)threadIdx.x + NT - 1) / NT) * NT;
-            if (idx < total) idx += NT;
-            for (; idx < total + n_const; idx += NT) {
-                if (delta) ref_item(sConst, sRef, sW, Mpad, net, layer, idx - total);
-                else const_item(lay, sConst, sW, Mpad, net, layer, idx - total);
+            int idx = threadIdx.x + ((busy - (int)threadIdx.x + NT - 1) / NT) * NT;
+            if (idx < busy) idx += NT;
+            for (; idx < busy + n_const; idx += NT) {
+                if (delta) ref_item(sConst, sRef, sW, Mpad, net, layer, idx - busy);
+                else const_item(lay, sConst, sW, Mpad, net, layer, idx - busy);
             }
         }
         __syncthreads();
+        if (split) {
+            const int item = (int)threadIdx.x >> 1;
+            if ((threadIdx.x & 1) == 0 && item < total) {
+                int g, q;
+                item_tile(item, G, QW, QA, g, q);
+                const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) V4<Real>::st(S + (g * 8 + r) * NS + j0, acc[0][r]);
+            }
+            return;
+        }
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const int item = threadIdx.x + it * NT;

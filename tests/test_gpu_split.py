@@ -207,3 +207,15 @@ def test_split_rule_errors(pkg):
         c.set_options(split_rule=pkg.SPLIT_GRADIENT, relax_mode=pkg.RELAX_PAPER_LITERAL)
         with pytest.raises(pkg.SlrError, match="EUNSUPPORTED"):
             c.count(6)
+
+
+def test_gradient_rule_tensor_core_path_matches(pkg):
+    """The tensor-core tile path decodes the per-box split dimensions the same
+    way: with its FP32 and FP64 re-checks it gives the FP32 path's count."""
+    p = _shrunk("acas", 0.1)
+    D = 10
+    a, ca, da, ka, Sa = _gpu_count(pkg, p, D)
+    b, cb, db, kb, Sb = _gpu_count(pkg, p, D, precision=pkg.PREC_TC_TF32)
+    assert list(Sa) == list(Sb)
+    assert (a["unsafe_lo"], a["unsafe_hi"], a["boxes"]) == (b["unsafe_lo"], b["unsafe_hi"], b["boxes"])
+    assert sorted(zip(ca.tolist(), da.tolist(), ka.tolist())) == sorted(zip(cb.tolist(), db.tolist(), kb.tolist()))
