@@ -864,11 +864,13 @@ int prepare_device(slr_ctx *ctx) {
     ctx->NT32 = best.NT;
     ctx->smem32 = best.smem;
     ctx->grid32 = best.blocks * ctx->sm_count;
-    // FP64 re-check: short lists, so the smallest tiles spread them over the most SMs
+    // FP64 re-check: short lists, so the smallest tiles spread them over the
+    // most SMs, with the most threads (a tile's products then split their
+    // inputs over lane pairs: the per-level latency is what counts)
     const std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
     ctx->T64 = 0;
     for (const TileChoice &c : c64) {
-        if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT < ctx->NT64)) {
+        if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT > ctx->NT64)) {
             ctx->T64 = c.T;
             ctx->NT64 = c.NT;
             ctx->smem64 = c.smem;
