@@ -867,7 +867,17 @@ int prepare_device(slr_ctx *ctx) {
     // FP64 re-check: short lists, so the smallest tiles spread them over the
     // most SMs, with the most threads (a tile's products then split their
     // inputs over lane pairs: the per-level latency is what counts)
-    const std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
+    std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
+    if (slr::eval_f64_pair_tile_ok(ctx->nd.d)) {
+        TileChoice c;
+        c.T = 2;
+        c.NT = 256;
+        c.smem = slr::eval_smem_bytes<double>(2, ctx->nd.d, ctx->nd.R, ctx->nd.n_max_pad, ctx->nd.n_in_max);
+        if (c.smem <= (size_t)kMaxSmem && slr::eval_gemm_items(2, ctx->nd.d, ctx->nd.n_max_pad) <= 2 * 256) {
+            c.blocks = slr::eval_blocks_per_sm_f64(2, 256, c.smem);
+            if (c.blocks > 0) c64.push_back(c);
+        }
+    }
     ctx->T64 = 0;
     for (const TileChoice &c : c64) {
         if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT > ctx->NT64)) {

@@ -745,12 +745,14 @@ struct EvalTile {
         // lanes share their weights and write neighbouring columns
         const int n_const = delta ? net.n[layer + 1] : ((net.n[layer + 1] + 1) / 2) * T;
         Real acc[kItems][8][4];
-        // few tiles (the property rows): each tile's inputs in two halves on a
-        // pair of neighbouring lanes, added in a fixed order after the products
-        const bool split = 2 * total <= NT && n_in >= 8;
-        const int busy = split ? 2 * total : total;   // threads busy with products
+        // few tiles (the property rows; the re-check's small tiles): each
+        // tile's inputs in 2 or 4 parts on neighbouring lanes, added in a fixed
+        // order ((p0 + p1) + (p2 + p3)) after the products
+        const int parts = (4 * total <= NT && n_in >= 16) ? 4 : ((2 * total <= NT && n_in >= 8) ? 2 : 1);
+        const bool split = parts > 1;
+        const int busy = parts * total;   // threads busy with products
         if (split) {
-            const int item = (int)threadIdx.x >> 1, half = (int)threadIdx.x & 1;
+            const int item = (int)threadIdx.x / parts, part = (int)threadIdx.x % parts;
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -760,14 +762,16 @@ struct EvalTile {
                 item_tile(item, G, QW, QA, g, q);
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-                const int i0 = half ? n_in / 2 : 0;
-                tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, half ? n_in - n_in / 2 : n_in / 2, Mpad, NS,
-                         is_abs, acc[0]);
+                const int i0 = part * n_in / parts, i1 = (part + 1) * n_in / parts;
+                tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, i1 - i0, Mpad, NS, is_abs, acc[0]);
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[0][r][c] += __shfl_xor_sync(0xffffffffu, acc[0][r][c], 1);
+                for (int c = 0; c < 4; ++c) {
+                    acc[0][r][c] += __shfl_xor_sync(0xffffffffu, acc[0][r][c], 1);
+                    if (parts == 4) acc[0][r][c] += __shfl_xor_sync(0xffffffffu, acc[0][r][c], 2);
+                }
         } else {
 #pragma unroll
             for (int it = 0; it < kItems; ++it) {
@@ -792,8 +796,8 @@ struct EvalTile {
         }
         __syncthreads();
         if (split) {
-            const int item = (int)threadIdx.x >> 1;
-            if ((threadIdx.x & 1) == 0 && item < total) {
+            const int item = (int)threadIdx.x / parts;
+            if ((int)threadIdx.x % parts == 0 && item < total) {
                 int g, q;
                 item_tile(item, G, QW, QA, g, q);
                 const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;

@@ -33,10 +33,16 @@ static int occ_t(size_t smem) {
         default: break;                   \
     }
 
+// Two-box tiles for the short re-check lists (odd input counts only: the
+// products take the columns four at a time, (d + 1) T and (d + 3) T must be
+// multiples of 4, and a row of the state must start on 16 bytes).
+static bool f64_pair_tile_ok(int d) { return d % 2 == 1; }
+
 cudaError_t launch_eval_f64(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass) {
     if (NT == 256) {
         SLR_DISPATCH(256, launch_t)
+        if (T == 2 && f64_pair_tile_ok(net.d)) return launch_t<2, 256>(grid, smem, s, net, src, out, pass);
     } else if (NT == 128) {
         SLR_DISPATCH(128, launch_t)
     }
@@ -55,9 +61,12 @@ int eval_blocks_per_sm_f64(int T, int NT, size_t smem) {
         case 12816: return occ_t<16, 128>(smem);
         case 12808: return occ_t<8, 128>(smem);
         case 12804: return occ_t<4, 128>(smem);
+        case 25602: return occ_t<2, 256>(smem);
         default: return 0;
     }
 }
+
+int eval_f64_pair_tile_ok(int d) { return f64_pair_tile_ok(d) ? 1 : 0; }
 
 
 template <int T>

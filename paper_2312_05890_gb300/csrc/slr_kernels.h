@@ -26,6 +26,8 @@ cudaError_t launch_eval_f64(int T, int NT, int grid, size_t smem, cudaStream_t s
 // one-product-tile-per-thread instantiation where it fits).
 int eval_blocks_per_sm_f32(int T, int NT, size_t smem, int items);
 int eval_blocks_per_sm_f64(int T, int NT, size_t smem);
+// 1 when the FP64 kernel can take tiles of two boxes for d inputs.
+int eval_f64_pair_tile_ok(int d);
 
 // Tensor-core evaluation (FP32 state, split-TF32 contraction on tcgen05).
 size_t eval_tc_smem_bytes(int T, const NetParams<float> &net, const TcParams &tc);
