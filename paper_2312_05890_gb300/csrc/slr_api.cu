@@ -51,6 +51,7 @@ struct BatchState {
     std::vector<int64_t> near_cap;
     int64_t launches = 0;
     int T32 = 0, T64 = 0;
+    std::vector<int> tile_of;            // per problem: boxes per tile of its class
 };
 
 struct slr_ctx {
@@ -1745,7 +1746,60 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 namespace {
 
 // The batched count of problems whose per-box state fits a shared-memory tile.
+// Problem shape as the fused kernel sees it: inputs, rows, widest layer
+// (padded to 8, the property rows counted) and widest layer input.
+struct TileShape {
+    int d, R, nmp, n_in;
+};
+
+TileShape problem_shape(const ProblemHost &h) {
+    TileShape s{h.widths[0], (int)h.e.size(), 0, 0};
+    int m = s.R;
+    for (int k = 1; k < h.K; ++k) m = std::max(m, h.widths[k]);
+    s.nmp = (m + 7) & ~7;
+    for (int k = 0; k < h.K; ++k) s.n_in = std::max(s.n_in, h.widths[k]);
+    return s;
+}
+
+// Boxes per tile of the batched kernel that fit one problem: the largest of
+// 32, 16, 8, 4 whose product tiles fit two per thread and whose shared memory
+// fits next to a problem's shared copies.
+constexpr int kBatchTiles[] = {32, 16, 8, 4};
+constexpr size_t kBatchStatic = 4096;
+int batch_tile_for(const TileShape &s) {
+    for (int t : kBatchTiles)
+        if (slr::eval_gemm_items(t, s.d, s.nmp) <= 2 * 256 &&
+            slr::eval_smem_bytes<float>(t, s.d, s.R, s.nmp, s.n_in) + kBatchStatic <= (size_t)kMaxSmem)
+            return t;
+    return 0;
+}
+
+int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results);
+
+// Problems grouped by the tile size that fits them (one persistent launch per
+// group and level step): sorted by group, counted, results put back in order.
 int count_batch_tile(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
+    std::vector<int> tile(n);
+    for (int i = 0; i < n; ++i) {
+        ProblemHost h;
+        int rc = read_problem(ctx, i, problems[i], ctx->opt.relax_mode, h);
+        if (rc) return rc;
+        tile[i] = batch_tile_for(problem_shape(h));
+        if (!tile[i]) return fail(ctx, SLR_EUNSUPPORTED, "problem %d is too large for the fused kernel", i);
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return tile[a] > tile[b]; });
+    std::vector<slr_problem> sorted(n);
+    std::vector<slr_result> res(n);
+    for (int j = 0; j < n; ++j) sorted[j] = problems[ord[j]];
+    const int rc = count_batch_sorted(ctx, n, sorted.data(), res.data());
+    for (int j = 0; j < n; ++j) results[ord[j]] = res[j];
+    return rc;
+}
+
+// The batch with problems sorted by tile size (runs of equal size are the groups).
+int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
     CK(ctx, cudaSetDevice(ctx->device));
     const int P = n;
     std::vector<ProblemHost> ph(P);
@@ -1833,7 +1887,7 @@ int count_batch_tile(slr_ctx *ctx, int n, const slr_problem *problems, slr_resul
         const size_t o_ca = off;
         off += al(2 * (size_t)P * sizeof(slr::CompactArgs));
         const size_t o_pm = off;
-        off += al(((size_t)P + 1) * sizeof(long long));
+        off += al(((size_t)P + 4) * sizeof(long long));   // one prefix per group (at most 4 groups)
         const size_t o_pr = off;
         off += al(((size_t)P + 1) * sizeof(long long));
         CK(ctx, cudaMalloc(&bs->arena, off));
@@ -1887,12 +1941,49 @@ int count_batch_tile(slr_ctx *ctx, int n, const slr_problem *problems, slr_resul
                 }
             }
         };
-        int T32 = 0, T64 = 0, g32 = 0, g64 = 0;
-        size_t sm32 = 0, sm64 = 0;
-        pick(false, T32, sm32, g32);
+        int T64 = 0, g64 = 0;
+        size_t sm64 = 0;
         pick(true, T64, sm64, g64);
-        if (!T32) return fail(ctx, SLR_EUNSUPPORTED, "a problem of the batch is too large for the fused kernel");
-        bs->T32 = T32;
+        // FP32 groups: runs of problems with the same tile size, each launched
+        // with the shared memory and occupancy of its own largest shape
+        struct Group {
+            int p0, p1, T, grid;
+            size_t smem;
+            slr::BatchShape sh;
+        };
+        std::vector<Group> groups;
+        bs->tile_of.assign(P, 0);
+        for (int i = 0; i < P;) {
+            const int t = batch_tile_for(problem_shape(ph[i]));
+            int j = i;
+            slr::BatchShape sh{0, 0, 0, 0};
+            while (j < P && batch_tile_for(problem_shape(ph[j])) == t) {
+                sh.nmp = std::max(sh.nmp, n32[j].n_max_pad);
+                sh.d = std::max(sh.d, n32[j].d);
+                sh.n_in_max = std::max(sh.n_in_max, n32[j].n_in_max);
+                sh.R = std::max(sh.R, n32[j].R);
+                ++j;
+            }
+            Group gr{i, j, 0, 0, 0, sh};
+            // the group's combined shape may need a smaller tile than each member alone
+            for (int tt : kBatchTiles) {
+                if (tt > t) continue;
+                const size_t sm = slr::eval_smem_bytes<float>(tt, sh.d, sh.R, sh.nmp, sh.n_in_max);
+                if (sm + kStatic > (size_t)kMaxSmem) continue;
+                const int nb = slr::eval_batch_blocks_per_sm_f32(tt, sm);
+                if (nb <= 0) continue;
+                gr.T = tt;
+                gr.smem = sm;
+                gr.grid = nb * ctx->sm_count;
+                break;
+            }
+            if (!gr.T) return fail(ctx, SLR_EUNSUPPORTED, "a problem of the batch is too large for the fused kernel");
+            for (int k = i; k < j; ++k) bs->tile_of[k] = gr.T;
+            groups.push_back(gr);
+            i = j;
+        }
+        if (groups.size() > 4) return fail(ctx, SLR_EUNSUPPORTED, "more than four tile groups");
+        bs->T32 = groups[0].T;
         bs->T64 = T64;
         const bool rch = recheck && T64 > 0;
 
@@ -1969,10 +2060,15 @@ int count_batch_tile(slr_ctx *ctx, int n, const slr_problem *problems, slr_resul
             const slr::BoxSource *s_r = (const slr::BoxSource *)(A + o_sr) + t * P;
             const slr::EvalOutputs *o_m = (const slr::EvalOutputs *)(A + o_om) + t * P;
             const slr::EvalOutputs *o_r = (const slr::EvalOutputs *)(A + o_or) + t * P;
-            ce = slr::launch_tile_prefix(s_m, P, T32, pm, ctx->stream);
-            if (ce == cudaSuccess)
-                ce = slr::launch_eval_batch_f32(T32, g32, sm32, ctx->stream, dn32, s_m, o_m, P, pm, sh32, 0);
-            L += 2;
+            for (size_t gi = 0; gi < groups.size() && ce == cudaSuccess; ++gi) {
+                const Group &gr = groups[gi];
+                long long *pg = pm + gr.p0 + gi;
+                ce = slr::launch_tile_prefix(s_m + gr.p0, gr.p1 - gr.p0, gr.T, pg, ctx->stream);
+                if (ce == cudaSuccess)
+                    ce = slr::launch_eval_batch_f32(gr.T, gr.grid, gr.smem, ctx->stream, dn32 + gr.p0, s_m + gr.p0,
+                                                    o_m + gr.p0, gr.p1 - gr.p0, pg, gr.sh, 0);
+                L += 2;
+            }
             if (rch && ce == cudaSuccess) {
                 ce = slr::launch_tile_prefix(s_r, P, T64, pr, ctx->stream);
                 if (ce == cudaSuccess)
@@ -2070,7 +2166,7 @@ int count_batch_tile(slr_ctx *ctx, int n, const slr_problem *problems, slr_resul
         out.launches = bs->launches;
         out.h2d_bytes = (int64_t)bs->upload_bytes;
         out.d2h_bytes = (int64_t)((size_t)P * sizeof(slr::LevelCounters) + sizeof st);
-        out.tile_boxes = bs->T32;
+        out.tile_boxes = bs->tile_of[i];
         out.tile_threads = 256;
     }
     if (st & slr::kStatusOverflow) return fail(ctx, SLR_EOVERFLOW, "a problem's level exceeded its frontier capacity");
@@ -2086,15 +2182,15 @@ static bool batch_tile_fits(const slr_problem &q) {
     if (q.K < 1 || q.K > slr::kMaxLayers || !q.widths || !q.rows_per_clause) return true;   // validated later
     int R = 0;
     for (int c = 0; c < q.n_clauses; ++c) R += q.rows_per_clause[c];
-    int nmax = R, nin = 1;
+    const int d = q.widths[0];
+    int nmax = R, nin = d;
     for (int k = 1; k < q.K; ++k) {
         nmax = std::max(nmax, q.widths[k]);
         nin = std::max(nin, q.widths[k]);
     }
     const int nmp = (nmax + 7) & ~7;
-    const int d = q.widths[0];
     return slr::eval_gemm_items(4, d, nmp) <= 2 * 256 &&
-           slr::eval_smem_bytes<float>(4, d, R, nmp, nin) + 1024 <= (size_t)kMaxSmem;
+           slr::eval_smem_bytes<float>(4, d, R, nmp, nin) + kBatchStatic <= (size_t)kMaxSmem;
 }
 
 extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results) {
