@@ -1078,7 +1078,7 @@ slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutput
 // shared memory when the problem changes.
 // ---------------------------------------------------------------------------
 template <typename Real, int T, int NT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, (eval_min_blocks<Real, NT, 2>()))
 slr_eval_batch_kernel(const NetParams<Real> *__restrict__ nets, const BoxSource *__restrict__ srcs,
                       const EvalOutputs *__restrict__ outs, const int P, const long long *__restrict__ tile_prefix,
                       const BatchShape shape, const int pass) {
