@@ -569,17 +569,23 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmA
         const int quad = warp & 3;
         const int half = warp >> 2;
         const int m = m0 + quad * 32 + lane;
-        for (int cc = 0; cc < kWN / 2; cc += 8) {
-            uint32_t r[8];
+        // 32 accumulator columns per read, one wait per read
+        for (int cc = 0; cc < kWN / 2; cc += 32) {
+            uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * (kWN / 2) + cc);
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (m < G.M) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < 32; ++j) {
                     const int col = n0 + half * (kWN / 2) + cc + j;
                     if (col < G.ncols) G.D[(size_t)col * G.ldd + m] = __uint_as_float(r[j]);
                 }
