@@ -641,6 +641,21 @@ int run_wide(slr_ctx *ctx, const slr::BoxSource &src, int64_t n, const slr::Eval
         *launches += 2;
         for (int k = 1; k < K; ++k) {
             const int nxt = cur ^ 1;
+            if (k + 1 == K && nf.R <= 16) {
+                // the property layer: a few rows, on the CUDA cores (FP32 FMA
+                // chains, rounding bound gamma_{n_in} like the tile kernel's)
+                CK(ctx, slr::launch_wide_rows_product(nf.Wt[k], nf.n[k], nf.R, Cb[cur], np, Cb[nxt], np,
+                                                      (int64_t)nb * d, false, sms, ctx->stream));
+                CK(ctx, slr::launch_wide_rows_product(nf.Wt[k], nf.n[k], nf.R, Rb[cur], np, Rb[nxt], np,
+                                                      (int64_t)nb * (d + 3), true, sms, ctx->stream));
+                CK(ctx, slr::launch_wide_const(nf, k, nb, np, Ch, Cl, Rb[cur], Kh, Kl, Ke, sms, ctx->stream));
+                const float gf = (float)(nf.n[k] + 2) * 0x1p-24f;
+                CK(ctx, slr::launch_wide_final(nf, nb, np, gf, Cb[nxt], Rb[nxt], Ch, Cl, Kh, Kl, Ke, lo, hi, er,
+                                               ctx->stream));
+                *launches += 4;
+                cur = nxt;
+                continue;
+            }
             slr::WideGemmArgs ga{};
             ga.status = out.status;
             ga.g[0] = slr::WideGemm{ctx->w_hi[k], ctx->w_lo[k], Cb[cur], Cb[nxt], nf.n[k + 1], nf.n[k], ctx->w_Kpad[k],

@@ -137,6 +137,9 @@ struct WideGemmArgs {
 size_t wide_gemm_smem_bytes();
 cudaError_t launch_wide_gemm(const WideGemmArgs &args, int nprob, cudaStream_t s);
 cudaError_t launch_wait_selfcheck(unsigned int *status, int limit, cudaStream_t s);
+// The property layer (R <= 16 rows) of the wide path on the CUDA cores.
+cudaError_t launch_wide_rows_product(const float *Wt, int n_in, int R, const float *B, int ldb, float *D, int ldd,
+                                     int64_t ncols, bool abs_w, int sms, cudaStream_t s);
 cudaError_t launch_wide_box(const BoxSource &src, int64_t base, int nb, int d, float *mh, float *ml, float *rr,
                             int64_t *bidx, int sms, cudaStream_t s);
 // Wide row kernels: `alpha` (nullable) holds the lower slopes of the chunk's

@@ -604,6 +604,46 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmA
 
 size_t wide_gemm_smem_bytes() { return 2 * (size_t)kWStage + 64; }
 
+// The property layer's products on the CUDA cores: with at most 16 rows a
+// tensor-core tile (M = 128) would be mostly padding.  Column `col` of B (the
+// n_in values at B + col * ldb) times the weights (Wt: n_in x R, input-major;
+// |W| when abs_w) into D[col * ldd + r], r < R, each a plain FP32 FMA chain
+// over the inputs in order (rounding within gamma_{n_in} of sum |W| |x|).
+template <int RM>
+__global__ void __launch_bounds__(256)
+wide_rows_product_kernel(const float *__restrict__ Wt, int n_in, int R, const float *__restrict__ B, int ldb,
+                         float *__restrict__ D, int ldd, int64_t ncols, int abs_w) {
+    extern __shared__ float sWt[];   // n_in x RM, zero beyond R
+    for (int q = threadIdx.x; q < n_in * RM; q += blockDim.x) {
+        const int i = q / RM, r = q - i * RM;
+        const float w = r < R ? Wt[(size_t)i * R + r] : 0.f;
+        sWt[q] = abs_w ? fabsf(w) : w;
+    }
+    __syncthreads();
+    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < ncols;
+         col += (int64_t)gridDim.x * blockDim.x) {
+        float acc[RM];
+#pragma unroll
+        for (int r = 0; r < RM; ++r) acc[r] = 0.f;
+        const float *x = B + (size_t)col * ldb;
+        int i = 0;
+        for (; i + 4 <= n_in; i += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(x + i);
+            const float xv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int r = 0; r < RM; ++r) acc[r] = fmaf(sWt[(i + u) * RM + r], xv[u], acc[r]);
+        }
+        for (; i < n_in; ++i)
+#pragma unroll
+            for (int r = 0; r < RM; ++r) acc[r] = fmaf(sWt[i * RM + r], x[i], acc[r]);
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+            if (r < R) D[(size_t)col * ldd + r] = acc[r];
+    }
+}
+
 // The bounded wait of the tensor-core kernels on a barrier whose phase nothing
 // completes: it must give up after `limit` polls and report kStatusTimeout.
 __global__ void wait_selfcheck_kernel(unsigned int *status, int limit) {
@@ -666,6 +706,24 @@ cudaError_t launch_wide_classify(const NetParams<float> &net, int nb, int64_t ba
                                  const float *err, const int64_t *bidx, const EvalOutputs &out, int sms,
                                  cudaStream_t s) {
     wide_classify_kernel<<<grid_for(nb, sms), 256, 0, s>>>(net, nb, base, lo, hi, err, bidx, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_rows_product(const float *Wt, int n_in, int R, const float *B, int ldb, float *D, int ldd,
+                                     int64_t ncols, bool abs_w, int sms, cudaStream_t s) {
+    const int grid = grid_for(ncols, sms);
+    if (R <= 4) {
+        wide_rows_product_kernel<4><<<grid, 256, (size_t)n_in * 4 * sizeof(float), s>>>(Wt, n_in, R, B, ldb, D, ldd,
+                                                                                       ncols, abs_w ? 1 : 0);
+    } else if (R <= 8) {
+        wide_rows_product_kernel<8><<<grid, 256, (size_t)n_in * 8 * sizeof(float), s>>>(Wt, n_in, R, B, ldb, D, ldd,
+                                                                                       ncols, abs_w ? 1 : 0);
+    } else if (R <= 16) {
+        wide_rows_product_kernel<16><<<grid, 256, (size_t)n_in * 16 * sizeof(float), s>>>(Wt, n_in, R, B, ldb, D,
+                                                                                         ldd, ncols, abs_w ? 1 : 0);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
