@@ -756,9 +756,18 @@ int run_wide_adjoint(slr_ctx *ctx, const slr::AdjArgs &a, int64_t *launches) {
             float *sck = sc + (size_t)(k - 1) * 5 * sstride;
             CK(ctx, slr::launch_wadj_fwd(a, k, pos0, nb, np, Cl[k], Rl[k], k > 1 ? nf.b[k - 1] : nullptr, sck,
                                          sstride, Pc, Pr, ctx->stream));
+            float *oc = k + 1 < K ? Cl[k + 1] : Cf, *orr = k + 1 < K ? Rl[k + 1] : Rf;
+            if (k + 1 == K && nf.R <= 16) {
+                // the property layer's few rows on the CUDA cores
+                CK(ctx, slr::launch_wide_rows_product(nf.Wt[k], nf.n[k], nf.R, Pc, np, oc, np, (int64_t)nb * Q, false,
+                                                      sms, ctx->stream));
+                CK(ctx, slr::launch_wide_rows_product(nf.Wt[k], nf.n[k], nf.R, Pr, np, orr, np, (int64_t)nb * Q, true,
+                                                      sms, ctx->stream));
+                *launches += 3;
+                continue;
+            }
             slr::WideGemmArgs ga{};
             ga.status = ctx->status;
-            float *oc = k + 1 < K ? Cl[k + 1] : Cf, *orr = k + 1 < K ? Rl[k + 1] : Rf;
             ga.g[0] = slr::WideGemm{ctx->w_hi[k], ctx->w_lo[k], Pc, oc, nf.n[k + 1], nf.n[k], ctx->w_Kpad[k],
                                     nb * Q, np, np};
             ga.g[1] = slr::WideGemm{ctx->wa_hi[k], ctx->wa_lo[k], Pr, orr, nf.n[k + 1], nf.n[k], ctx->w_Kpad[k],
