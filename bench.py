@@ -210,7 +210,8 @@ def main():
     # weak scaling: rank r counts its own problem of the same shape (seed + r)
     p = gen.make(args.workload, multirank.weak_seed(args.seed, rank))
     D = args.depth or p.depth
-    workload = f"{p.name} D={D} seed={args.seed}"
+    # the seed filter maps the requested base seed to the first accepted one
+    workload = f"{p.name} D={D} seed={p.seed}"
     config = {"workload": workload, "widths": p.net.widths, "depth": D, "rows": p.prop.R,
               "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}"}
     if args.alpha_steps:
