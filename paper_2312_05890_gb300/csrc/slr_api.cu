@@ -87,6 +87,10 @@ struct slr_ctx {
     BatchState *batch = nullptr;
     slr_ctx *wide_helper = nullptr;       // batched counts: problems too wide for a tile
     void *split_buf = nullptr;            // gradient split rule: set, dimension map, root gradient
+    uint64_t dev_version = 0;             // bumped whenever the device images of the problem are rebuilt
+    cudaGraphExec_t count_graph = nullptr;  // the tile path's level loop, captured once per configuration
+    std::string count_graph_key;
+    int64_t count_graph_launches = 0;
     std::vector<int> split_set;           // split set of the last count (ascending); empty: widest side
     std::string tuned_key;                // network shape the FP32 tile choice was timed for
     int tuned_T = 0, tuned_NT = 0;
@@ -869,6 +873,7 @@ int prepare_device(slr_ctx *ctx) {
         ctx->adj_gmem = true;
         ctx->adj_grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)2 * ctx->sm_count, ((size_t)4 << 30) / box));
         ctx->dev_dirty = false;
+        ++ctx->dev_version;
         return SLR_OK;
     }
     TileChoice best = c32[0];
@@ -949,6 +954,7 @@ int prepare_device(slr_ctx *ctx) {
         ctx->tc_ok = false;
     }
     ctx->dev_dirty = false;
+    ++ctx->dev_version;
     return SLR_OK;
 }
 
@@ -1158,6 +1164,7 @@ int slr_destroy(slr_ctx *ctx) {
     if (ctx->wide_helper) slr_destroy(ctx->wide_helper);
     cudaFree(ctx->split_buf);
     cudaFree(ctx->wadj_buf);
+    if (ctx->count_graph) cudaGraphExecDestroy(ctx->count_graph);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -1344,8 +1351,14 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         CK(ctx, cudaEventCreate(&e));
         ctx->prof_ev.push_back(e);
     }
+    // while the level loop is captured as a graph, the timing events become
+    // event-record nodes of the graph (an ordinary record there is only an edge)
+    bool capturing = false;
     auto mark = [&](int t, int slot) -> cudaError_t {
-        return prof ? cudaEventRecord(ctx->prof_ev[(size_t)t * 6 + slot], ctx->stream) : cudaSuccess;
+        if (!prof) return cudaSuccess;
+        cudaEvent_t e = ctx->prof_ev[(size_t)t * 6 + slot];
+        return capturing ? cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal)
+                         : cudaEventRecord(e, ctx->stream);
     };
     int64_t launches = 1;
     ctx->gemm_ev_used = 0;
@@ -1371,7 +1384,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         launches = 1;
     }
     const uint64_t path_mask = grad_split ? (1ull << slr::kSplitPathBits) - 1ull : ~0ull;
-    CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+    auto run_levels = [&]() -> int {
     for (int t = 0; t <= D; ++t) {
         slr::BoxSource src = level_source(t);
         if (grad_split) src.split_of = (const int8_t *)ctx->split_buf;
@@ -1458,6 +1471,54 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         CK(ctx, mark(t, 5));
         launches += 2;
     }
+    return SLR_OK;
+    };
+    // The tile path reads no count on the host between levels: its level loop
+    // is captured as a CUDA graph once per configuration and buffer set, and
+    // replayed (fewer launch gaps between the small kernels of a level).
+    const bool graphable = !ctx->wide && !slopes && !grad_split;
+    if (graphable) {
+        char key[512];
+        std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%llu|%p|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%lld|%lld|%d|%d|%d|%d|%d|%d",
+                      D, leaves ? 1 : 0, recheck ? 1 : 0, use_tc ? 1 : 0, prof ? 1 : 0,
+                      (unsigned long long)ctx->dev_version, (void *)ctx->codes[0], (void *)ctx->codes[1],
+                      (void *)ctx->cls, (void *)ctx->ctr, (void *)ctx->near_list, (void *)ctx->near_list2,
+                      (void *)ctx->leaf_codes, (void *)ctx->masks, (void *)ctx->root, (long long)ctx->cap,
+                      (long long)ctx->near_cap, (long long)ctx->opt.leaf_cap, ctx->T32, ctx->NT32, ctx->T64,
+                      ctx->NT64, ctx->grid32, ctx->grid64);
+        if (!ctx->count_graph || ctx->count_graph_key != key) {
+            if (ctx->count_graph) cudaGraphExecDestroy(ctx->count_graph);
+            ctx->count_graph = nullptr;
+            ctx->count_graph_key.clear();
+            CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t l0 = launches;
+            capturing = true;
+            const int rcap = run_levels();
+            capturing = false;
+            cudaGraph_t g = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
+            if (rcap) {
+                if (ee == cudaSuccess && g) cudaGraphDestroy(g);
+                return rcap;
+            }
+            if (ee != cudaSuccess) return cuda_fail(ctx, ee, "capturing the level loop");
+            const cudaError_t ie = cudaGraphInstantiate(&ctx->count_graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                ctx->count_graph = nullptr;
+                return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+            }
+            ctx->count_graph_key = key;
+            ctx->count_graph_launches = launches - l0;
+            launches = l0;
+        }
+        CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+        CK(ctx, cudaGraphLaunch(ctx->count_graph, ctx->stream));
+        launches += ctx->count_graph_launches;
+    } else {
+        CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+        if ((rc = run_levels())) return rc;
+    }
     CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(slr::LevelCounters), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1523,6 +1584,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
             out->kernel_ms[1] += b;
             out->kernel_ms[2] += c2;
         }
+        (void)cudaGetLastError();   // a timing read that failed must not surface at the next launch
     }
     out->gemm_launches = ctx->gemm_launches;
     out->gemm_flop = ctx->gemm_flop;
