@@ -229,3 +229,45 @@ def test_call_order_and_arguments(pkg):
         c.count(4)
     assert ei.value.code == -1
     c.close()
+
+
+def test_replayed_level_loop_follows_changes(pkg):
+    """The level loop is replayed from a captured graph: counts after a new box,
+    a new property, new options and a new network equal fresh contexts' counts."""
+    import copy
+    p = gen.make("acas")
+    q = copy.deepcopy(p)
+    m = 0.5 * (p.lo.astype(np.float64) + p.hi)
+    r = 0.25 * (p.hi.astype(np.float64) - p.lo)
+    q.lo, q.hi = (m - r).astype(np.float32), (m + r).astype(np.float32)
+    t = gen.make("acas", 10)
+    D = 12
+
+    def fresh(prob, **opt):
+        with pkg.Counter(0) as c:
+            c.set_problem(prob)
+            if opt:
+                c.set_options(**opt)
+            return c.count(D)
+
+    keys = ("unsafe_lo", "unsafe_hi", "boxes", "level_boxes", "level_undecided")
+    with pkg.Counter(0) as c:
+        c.set_problem(p)
+        a1 = c.count(D)
+        a2 = c.count(D)
+        c.set_box(q.lo, q.hi)
+        b = c.count(D)
+        c.set_property(t.prop.rows_per_clause, t.prop.C, t.prop.e, t.prop.strict)
+        qt = copy.deepcopy(q)
+        qt.prop = t.prop
+        e = c.count(D)
+        c.set_options(record_leaves=1)
+        f = c.count(D)
+        c.set_problem(t)
+        g = c.count(D)
+    for k in keys:
+        assert a1[k] == a2[k]
+    want = [(b, fresh(q)), (e, fresh(qt)), (f, fresh(qt, record_leaves=1)), (g, fresh(t))]
+    for got, ref in want:
+        for k in keys:
+            assert got[k] == ref[k], k
