@@ -287,15 +287,20 @@ typedef struct {
 
 /* Count n problems of uneven size together (Alg. 1 for each, Sec. 3 level
  * evaluation across all of them): every level step bounds the current level
- * of every unfinished problem in one persistent launch, tiles never mixing
- * problems; problems with smaller depth caps simply finish earlier.  The step
- * loop is captured once as a CUDA graph and replayed while later calls keep
- * the batch's shape (same widths, rows, clauses and depths; weights, boxes
- * and properties may change).  results[i] receives problem i's count as
- * slr_count would return it (device_ms is the time of the whole batch).
+ * of every unfinished problem, tiles never mixing problems; problems with
+ * smaller depth caps simply finish earlier.  Problems are grouped by the
+ * largest tile (32, 16, 8 or 4 boxes) their shape fits, one persistent launch
+ * per group and step.  The step loop is captured once as a CUDA graph and
+ * replayed while later calls keep the batch's shape (same widths, rows,
+ * clauses and depths; weights, boxes and properties may change).  Problems
+ * too wide for any tile are counted one by one on the wide path in the same
+ * call.  results[i] receives problem i's count as slr_count would return it
+ * (device_ms is the time of the whole batch; tile_boxes the problem's tile).
  * Inputs are copied.  Each problem's frontier holds up to min(2^depth,
  * frontier_cap) boxes (SLR_EOVERFLOW beyond).  Uses the context's options
- * (relax_mode, fp64_recheck, frontier_cap) and stream; FP32 arithmetic. */
+ * (relax_mode, fp64_recheck, frontier_cap) and stream; FP32 arithmetic with
+ * the FP64 re-check; the widest-side split rule only (SLR_EUNSUPPORTED under
+ * SLR_SPLIT_GRADIENT). */
 int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result *results);
 
 /* slr_count for callers that cannot allocate GPU memory.  The paper has no
