@@ -104,6 +104,13 @@ typedef struct {
                                layer one tensor-core product, no FP64 re-check); 0 (default):
                                only for networks whose per-box state does not fit the fused
                                shared-memory kernel */
+    int32_t shard_count;    /* N > 1: this context counts one of N shards of the tree (default 1) */
+    int32_t shard_index;    /* which shard, 0..N-1: the level-g boxes whose frontier position
+                               is congruent to it modulo N, and everything below them */
+    int32_t shard_level;    /* g: every shard evaluates levels 0..g-1 in full, then keeps its
+                               share of level g (0 <= g <= D); the unsafe volume of levels
+                               below g is added by shard 0 only, so the sums of unsafe_lo and
+                               of unsafe_hi over the N shards are the whole count's */
     int32_t reserved2;      /* must be 0 */
 } slr_options;
 

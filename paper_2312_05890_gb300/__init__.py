@@ -48,7 +48,8 @@ class slr_options(ctypes.Structure):
                 ("frontier_cap", ctypes.c_int64), ("leaf_cap", ctypes.c_int64),
                 ("alpha_steps", ctypes.c_int32), ("alpha_lr", ctypes.c_float), ("alpha_cap", ctypes.c_int64),
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
-                ("wide", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("wide", ctypes.c_int32), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
+                ("shard_level", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 _U64A = ctypes.c_uint64 * (MAX_LEVELS + 1)

@@ -1059,6 +1059,7 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
     if (ctx->wide) return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc does not run the wide path");
     if (ctx->opt.split_rule != SLR_SPLIT_WIDEST)
         return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc splits the widest side only");
+    if (ctx->opt.shard_count > 1) return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc does not shard");
     v->device = ctx->device;
     v->stream = ctx->stream;
     v->d = ctx->widths[0];
@@ -1108,6 +1109,9 @@ void slr_default_options(slr_options *opt) {
     opt->tile_boxes = 0;
     opt->tile_threads = 0;
     opt->wide = 0;
+    opt->shard_count = 1;
+    opt->shard_index = 0;
+    opt->shard_level = 0;
     opt->reserved2 = 0;
 }
 
@@ -1208,6 +1212,10 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
             return fail(ctx, SLR_EUNSUPPORTED, "slope optimisation needs relax mode NEURIFY");
     }
     if (opt->reserved2 != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
+    if (opt->shard_count < 1 || opt->shard_index < 0 || opt->shard_index >= opt->shard_count ||
+        opt->shard_level < 0 || opt->shard_level > slr::kMaxDepth)
+        return fail(ctx, SLR_EINVAL, "shard %d of %d at level %d is not valid", opt->shard_index, opt->shard_count,
+                    opt->shard_level);
     if (opt->wide != 0 && opt->wide != 1) return fail(ctx, SLR_EINVAL, "wide must be 0 or 1");
     if ((opt->tile_boxes == 0) != (opt->tile_threads == 0))
         return fail(ctx, SLR_EINVAL, "tile_boxes and tile_threads are set together");
@@ -1292,6 +1300,10 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     const bool grad_split = ctx->opt.split_rule == SLR_SPLIT_GRADIENT;
     if (grad_split && D > slr::kSplitMaxDepth)
         return fail(ctx, SLR_EINVAL, "the gradient split rule counts to depth %d at most (D=%d)", slr::kSplitMaxDepth, D);
+    const bool sharded = ctx->opt.shard_count > 1;
+    const int shard_g = ctx->opt.shard_level;
+    if (sharded && shard_g > D)
+        return fail(ctx, SLR_EINVAL, "shard level %d is below the depth cap D=%d", shard_g, D);
     CK(ctx, cudaSetDevice(ctx->device));
     if ((rc = prepare_device(ctx))) return rc;
     if ((rc = ensure_count_buffers(ctx))) return rc;
@@ -1386,6 +1398,13 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     const uint64_t path_mask = grad_split ? (1ull << slr::kSplitPathBits) - 1ull : ~0ull;
     auto run_levels = [&]() -> int {
     for (int t = 0; t <= D; ++t) {
+        if (sharded && t == shard_g) {
+            // this shard's subtrees: every shard_count-th box of level g
+            CK(ctx, slr::launch_shard_level(ctx->codes[t & 1], ctx->codes[(t + 1) & 1], ctx->ctr, t,
+                                            ctx->opt.shard_count, ctx->opt.shard_index, ctx->cap, ctx->sm_count,
+                                            ctx->stream));
+            launches += 3;
+        }
         slr::BoxSource src = level_source(t);
         if (grad_split) src.split_of = (const int8_t *)ctx->split_buf;
         slr::EvalOutputs o{};
@@ -1467,7 +1486,8 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         CK(ctx, mark(t, 4));
         CK(ctx, slr::launch_compact(ctx->codes[t & 1], ctx->cls, ctx->codes[(t + 1) & 1], ctx->ctr, ctx->status,
                                     ctx->cap, t, D, leaves ? ctx->leaf_codes : nullptr, ctx->leaf_depth,
-                                    ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream, path_mask));
+                                    ctx->leaf_cls, ctx->opt.leaf_cap, compact_grid, ctx->stream, path_mask,
+                                    !sharded || ctx->opt.shard_index == 0 || t >= shard_g));
         CK(ctx, mark(t, 5));
         launches += 2;
     }
@@ -1479,8 +1499,10 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     const bool graphable = !ctx->wide && !slopes && !grad_split;
     if (graphable) {
         char key[512];
-        std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%llu|%p|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%lld|%lld|%d|%d|%d|%d|%d|%d",
-                      D, leaves ? 1 : 0, recheck ? 1 : 0, use_tc ? 1 : 0, prof ? 1 : 0,
+        std::snprintf(key, sizeof key,
+                      "%d|%d|%d|%d|%d|%d|%d|%d|%llu|%p|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%lld|%lld|%d|%d|%d|%d|%d|%d",
+                      D, leaves ? 1 : 0, recheck ? 1 : 0, use_tc ? 1 : 0, prof ? 1 : 0, ctx->opt.shard_count,
+                      ctx->opt.shard_index, shard_g,
                       (unsigned long long)ctx->dev_version, (void *)ctx->codes[0], (void *)ctx->codes[1],
                       (void *)ctx->cls, (void *)ctx->ctr, (void *)ctx->near_list, (void *)ctx->near_list2,
                       (void *)ctx->leaf_codes, (void *)ctx->masks, (void *)ctx->root, (long long)ctx->cap,
@@ -2284,6 +2306,7 @@ extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems,
     if (n < 1 || n > 65535 || !problems || !results) return fail(ctx, SLR_EINVAL, "bad batch arguments");
     if (ctx->opt.split_rule != SLR_SPLIT_WIDEST)
         return fail(ctx, SLR_EUNSUPPORTED, "batched counts split the widest side; the gradient rule runs in slr_count");
+    if (ctx->opt.shard_count > 1) return fail(ctx, SLR_EUNSUPPORTED, "batched counts are not sharded");
     std::vector<int> tile, wide;
     for (int i = 0; i < n; ++i) (batch_tile_fits(problems[i]) ? tile : wide).push_back(i);
     if (wide.empty()) return count_batch_tile(ctx, n, problems, results);

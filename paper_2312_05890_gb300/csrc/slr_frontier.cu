@@ -9,6 +9,8 @@
 // The single-problem count keeps the frontier's order (two passes, below);
 // the batched count appends with one atomic per warp (ballot + popc).
 // Integer sums make the volumes independent of order either way.
+#include <algorithm>
+
 #include "slr_eval.cuh"
 #include "slr_kernels.h"
 
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256)
 compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict__ cls,
                uint64_t *__restrict__ codes_out, LevelCounters *ctr, unsigned int *status,
                int64_t cap, int t, int D, uint64_t *leaf_codes, uint8_t *leaf_depth,
-               uint8_t *leaf_cls, int64_t leaf_cap, uint64_t path_mask) {
+               uint8_t *leaf_cls, int64_t leaf_cap, uint64_t path_mask, int add_volume) {
     __shared__ unsigned sh[8];
     __shared__ unsigned long long s_off;
     const unsigned long long n_raw = ctr->frontier_n[t];
@@ -233,7 +235,7 @@ compact_kernel(const uint64_t *__restrict__ codes_in, const uint8_t *__restrict_
     if (lane == 0) {
         if (n_unsafe) {
             atomicAdd(&ctr->level_unsafe[t], n_unsafe);
-            atomicAdd(&ctr->unsafe_lo, n_unsafe << (D - t));
+            if (add_volume) atomicAdd(&ctr->unsafe_lo, n_unsafe << (D - t));
         }
         if (n_safe) atomicAdd(&ctr->level_safe[t], n_safe);
         if (n_und) {
@@ -316,11 +318,47 @@ cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
                            uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
-                           int64_t leaf_cap, int grid, cudaStream_t s, uint64_t path_mask) {
+                           int64_t leaf_cap, int grid, cudaStream_t s, uint64_t path_mask, bool add_volume) {
     (void)grid;
     compact_count_kernel<<<kCompactBlocks, 256, 0, s>>>(cls, ctr, cap, t);
     compact_kernel<<<kCompactBlocks, 256, 0, s>>>(codes_in, cls, codes_out, ctr, status, cap, t, D, leaf_codes,
-                                                  leaf_depth, leaf_cls, leaf_cap, path_mask);
+                                                  leaf_depth, leaf_cls, leaf_cap, path_mask, add_volume ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// One shard of a count: of level t keep the boxes at frontier positions
+// index, index + count, index + 2 count, ... (each the root of a subtree), in
+// order.  Copied out, copied back, then the level's size set.
+__device__ __forceinline__ int64_t shard_size(const LevelCounters *ctr, int t, int count, int index, int64_t cap) {
+    int64_t n = (int64_t)ctr->frontier_n[t];
+    n = n < cap ? n : cap;
+    return n > index ? (n - index + count - 1) / count : 0;
+}
+
+__global__ void shard_gather_kernel(const uint64_t *__restrict__ codes, uint64_t *__restrict__ scratch,
+                                    const LevelCounters *ctr, int t, int count, int index, int64_t cap) {
+    const int64_t m = shard_size(ctr, t, count, index, cap);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        scratch[j] = codes[index + j * count];
+}
+
+__global__ void shard_back_kernel(const uint64_t *__restrict__ scratch, uint64_t *__restrict__ codes,
+                                  const LevelCounters *ctr, int t, int count, int index, int64_t cap) {
+    const int64_t m = shard_size(ctr, t, count, index, cap);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        codes[j] = scratch[j];
+}
+
+__global__ void shard_size_kernel(LevelCounters *ctr, int t, int count, int index, int64_t cap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctr->frontier_n[t] = (unsigned long long)shard_size(ctr, t, count, index, cap);
+}
+
+cudaError_t launch_shard_level(uint64_t *codes, uint64_t *scratch, LevelCounters *ctr, int t, int count, int index,
+                               int64_t cap, int sms, cudaStream_t s) {
+    const int grid = std::max(1, sms * 4);
+    shard_gather_kernel<<<grid, 256, 0, s>>>(codes, scratch, ctr, t, count, index, cap);
+    shard_back_kernel<<<grid, 256, 0, s>>>(scratch, codes, ctr, t, count, index, cap);
+    shard_size_kernel<<<1, 32, 0, s>>>(ctr, t, count, index, cap);
     return cudaGetLastError();
 }
 

@@ -163,6 +163,10 @@ cudaError_t launch_init_count(uint64_t *codes0, LevelCounters *ctr, cudaStream_t
 cudaError_t launch_compact(const uint64_t *codes_in, const uint8_t *cls, uint64_t *codes_out,
                            LevelCounters *ctr, unsigned int *status, int64_t cap, int t, int D,
                            uint64_t *leaf_codes, uint8_t *leaf_depth, uint8_t *leaf_cls,
-                           int64_t leaf_cap, int grid, cudaStream_t s, uint64_t path_mask = ~0ull);
+                           int64_t leaf_cap, int grid, cudaStream_t s, uint64_t path_mask = ~0ull,
+                           bool add_volume = true);
+// Keep shard `index` of `count` of level t's frontier (every count-th box from index).
+cudaError_t launch_shard_level(uint64_t *codes, uint64_t *scratch, LevelCounters *ctr, int t, int count, int index,
+                               int64_t cap, int sms, cudaStream_t s);
 
 }  // namespace slr

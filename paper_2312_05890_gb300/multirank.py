@@ -1,10 +1,12 @@
 """Runs over several GPUs of one node, one process per GPU (host side only).
 
-The count partitions, it does not exchange: every rank counts problems of its
-own (weak scaling: rank r takes the workload's seed + r), so no collective
-touches the data path.  The only collectives are the barriers around a timed
-region and the reduction of its timings and unit counts at the end: the job
-took as long as its slowest rank and processed the units of every rank.
+The count partitions, it does not exchange.  Weak scaling: every rank counts
+a problem of its own (rank r takes the workload's seed + r).  Strong
+scaling: the ranks share one count, rank r taking shard r of the tree (the
+`shard_*` options: every N-th subtree below a level g), and the whole count's
+bracket is the sum of the shards' brackets (`sum_counts`).  Either way the
+only collectives are the barriers around a timed region and the reductions
+of its timings, unit counts and the two volume counters at the end.
 """
 from __future__ import annotations
 
@@ -52,6 +54,16 @@ def job_rate(local_ms: float, local_units: float, dist=None):
     max_ms = float(t.item())
     total = float(u.item())
     return max_ms, total, total / (max_ms / 1e3)
+
+
+def sum_counts(unsafe_lo: int, unsafe_hi: int, dist=None):
+    """The whole count's bracket from the shards' (unsafe_lo, unsafe_hi): sums."""
+    import torch
+    dev = "cuda" if dist is not None and dist.get_backend() == "nccl" else "cpu"
+    v = torch.tensor([int(unsafe_lo), int(unsafe_hi)], dtype=torch.int64, device=dev)
+    if dist is not None:
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return int(v[0].item()), int(v[1].item())
 
 
 def finish(dist) -> None:

@@ -23,9 +23,11 @@ def _rank_main(rank, world, port, out_dir):
     # rank r: (10 (r + 1)) ms for 100 (r + 1) units
     res = multirank.job_rate(10.0 * (r + 1), 100 * (r + 1), dist)
     seed = multirank.weak_seed(7, r)
+    # shard brackets beyond 2^32: the sums stay exact
+    counts = multirank.sum_counts((1 << 40) + r, (1 << 41) + 3 * r, dist)
     multirank.finish(dist)
     with open(os.path.join(out_dir, f"rank{r}.json"), "w") as f:
-        json.dump({"env": [w, r, lr], "rate": res, "seed": seed}, f)
+        json.dump({"env": [w, r, lr], "rate": res, "seed": seed, "counts": counts}, f)
 
 
 @pytest.mark.timeout(120)
@@ -40,6 +42,7 @@ def test_two_gloo_ranks_reduce_time_and_units(tmp_path):
         assert max_ms == 20.0 and total == 300.0
         assert rate == pytest.approx(300.0 / 0.020)
         assert g["seed"] == 7 + r
+        assert g["counts"] == [(1 << 41) + 1, (1 << 42) + 3]
     assert got[0]["seed"] != got[1]["seed"]
 
 
