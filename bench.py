@@ -195,6 +195,9 @@ def main():
                     help="boxes x threads per CTA of the FP32 evaluation kernel, e.g. 16x256 (default: timed choice)")
     ap.add_argument("--alpha-cap", type=int, default=1 << 20,
                     help="most undecided boxes per level whose slopes are optimised")
+    ap.add_argument("--shard-level", type=int, default=-1,
+                    help="strong scaling: the ranks share one count, rank r taking every N-th subtree below this "
+                         "level (default: weak scaling, a problem per rank)")
     ap.add_argument("--split", default="widest", choices=["widest", "gradient"],
                     help="bisect the widest side, or per box the dimension of the 16-dimension split set "
                          "with the largest |dM/dr| r (adjoint gradient of the decision loss)")
@@ -207,8 +210,10 @@ def main():
     from workloads import generators as gen
     if args.workload == "batch":
         return bench_batch(args, world, rank, local_rank)
-    # weak scaling: rank r counts its own problem of the same shape (seed + r)
-    p = gen.make(args.workload, multirank.weak_seed(args.seed, rank))
+    # weak scaling: rank r counts its own problem of the same shape (seed + r);
+    # strong scaling (--shard-level): every rank takes a shard of one count
+    strong = args.shard_level >= 0
+    p = gen.make(args.workload, args.seed if strong else multirank.weak_seed(args.seed, rank))
     D = args.depth or p.depth
     # the seed filter maps the requested base seed to the first accepted one
     workload = f"{p.name} D={D} seed={p.seed}"
@@ -218,6 +223,8 @@ def main():
         config["slopes"] = f"{args.alpha_steps} projected-Adam steps (lr {args.alpha_lr}) per undecided box"
     if args.split == "gradient":
         config["split"] = "per box: largest |dM/dr_i| r_i over the 16 dimensions of largest |dM/dr_i| w_i at the root"
+    if strong:
+        config["parallelism"] = f"strong x{world}: shard r of {world} = every {world}-th subtree below level {args.shard_level}"
 
     if args.impl == "reference":
         if rank != 0:
@@ -258,6 +265,8 @@ def main():
     if args.tile:
         tb, tt = (int(x) for x in args.tile.lower().split("x"))
         tile = {"tile_boxes": tb, "tile_threads": tt}
+    if strong:
+        tile.update(shard_count=world, shard_index=rank, shard_level=args.shard_level)
     if args.precision == "tf32":
         tile["precision"] = pkg.PREC_TC_TF32
         config["precision"] = "split-TF32 tensor-core contraction (tcgen05), FP32 re-bound and FP64 re-check"
@@ -308,6 +317,7 @@ def main():
     last = r
 
     max_ms, _, value = multirank.job_rate(sum(dev_ms), boxes, dist)
+    job_lo, job_hi = multirank.sum_counts(last["unsafe_lo"], last["unsafe_hi"], dist) if strong else (None, None)
 
     # ---- e2e: upload network, box and property from host memory every step ------
     e2e_s = []
@@ -362,9 +372,10 @@ def main():
         line = {
             "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config,
-            "count": {"unsafe_lo": last["unsafe_lo"], "unsafe_hi": last["unsafe_hi"], "boxes": last["boxes"],
+            "higher_is_better": True, "scaling": "strong" if strong else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config,
+            "count": {"unsafe_lo": job_lo if strong else last["unsafe_lo"],
+                      "unsafe_hi": job_hi if strong else last["unsafe_hi"], "boxes": last["boxes"],
                       "rechecked": last["rechecked"], "tie_leaves": last["tie_leaves"],
                       "tile_boxes_threads": last["tile"]},
             "kernel_ms_per_step": {"eval_f32": kern[0] / args.steps, "recheck_f64": kern[1] / args.steps,
