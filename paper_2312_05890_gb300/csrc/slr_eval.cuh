@@ -819,11 +819,23 @@ struct EvalTile {
         }
     }
 
+    // Rows of the transposed weights, NT / Mpad rows per pass (one division
+    // per thread, not one per element).
     static __device__ void stage_weights(Real *sW, const Real *Wt, int n_in, int n_out, int Mpad) {
-        for (int idx = threadIdx.x; idx < n_in * Mpad; idx += NT) {
-            const int i = idx / Mpad;
-            const int p = idx - i * Mpad;
-            sW[idx] = p < n_out ? Wt[(size_t)i * n_out + p] : (Real)0;
+        const int per = NT / Mpad;
+        if (per >= 1) {
+            const int r0 = (int)threadIdx.x / Mpad;
+            const int p = (int)threadIdx.x - r0 * Mpad;
+            if (r0 < per) {
+                const bool live = p < n_out;
+                for (int i = r0; i < n_in; i += per) sW[i * Mpad + p] = live ? Wt[(size_t)i * n_out + p] : (Real)0;
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < n_in * Mpad; idx += NT) {
+                const int i = idx / Mpad;
+                const int p = idx - i * Mpad;
+                sW[idx] = p < n_out ? Wt[(size_t)i * n_out + p] : (Real)0;
+            }
         }
     }
 
