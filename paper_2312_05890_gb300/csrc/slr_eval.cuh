@@ -674,15 +674,20 @@ struct EvalTile {
     // then, after a barrier, overwrites the rows.
     static constexpr int kItems = KI;
 
-    // Row group g and column quad q (q < QW: W products, else |W|) of product tile `item`.
-    static __device__ __forceinline__ void item_tile(int item, int G, int QW, int QA, int &g, int &q) {
+    // Row group g and column quad q (q < QW: W products, else |W|) of product
+    // tile `item`.  The divisions by QW and QA are multiplications by their
+    // reciprocals rW = ceil(2^32 / QW), rA = ceil(2^32 / QA) keeping the high
+    // word: exact for item < 2^32 / QW, far beyond the tiles of one CTA.
+    static __device__ __forceinline__ uint32_t recip32(int q) { return 0xFFFFFFFFu / (uint32_t)q + 1u; }
+    static __device__ __forceinline__ void item_tile(int item, int G, int QW, int QA, uint32_t rW, uint32_t rA,
+                                                     int &g, int &q) {
         const int nW = G * QW;
         if (item < nW) {
-            g = item / QW;
+            g = (int)__umulhi((uint32_t)item, rW);
             q = item - g * QW;
         } else {
             const int k = item - nW;
-            g = k / QA;
+            g = (int)__umulhi((uint32_t)k, rA);
             q = QW + (k - g * QA);
         }
     }
@@ -734,7 +739,7 @@ struct EvalTile {
     template <class L>
     static __device__ void contract(const L &lay, Real *sConst, const Real *sRef, const NetParams<Real> &net,
                                     int layer, Real *S, const Real *sW, int n_in, int Mpad, int d, int NS,
-                                    bool delta) {
+                                    bool delta, uint32_t rW, uint32_t rA) {
         const int QW = (d + 1) * T / 4;       // quads of C coefficient columns and the constant column
         const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
         const int Q = QW + QA;
@@ -759,7 +764,7 @@ struct EvalTile {
                 for (int c = 0; c < 4; ++c) acc[0][r][c] = 0;
             if (item < total) {
                 int g, q;
-                item_tile(item, G, QW, QA, g, q);
+                item_tile(item, G, QW, QA, rW, rA, g, q);
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
                 const int i0 = part * n_in / parts, i1 = (part + 1) * n_in / parts;
@@ -778,7 +783,7 @@ struct EvalTile {
                 const int item = threadIdx.x + it * NT;
                 if (item < total) {
                     int g, q;
-                    item_tile(item, G, QW, QA, g, q);
+                    item_tile(item, G, QW, QA, rW, rA, g, q);
                     const bool is_abs = q >= QW;
                     const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
                     tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
@@ -799,7 +804,7 @@ struct EvalTile {
             const int item = (int)threadIdx.x / parts;
             if ((int)threadIdx.x % parts == 0 && item < total) {
                 int g, q;
-                item_tile(item, G, QW, QA, g, q);
+                item_tile(item, G, QW, QA, rW, rA, g, q);
                 const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) V4<Real>::st(S + (g * 8 + r) * NS + j0, acc[0][r]);
@@ -811,7 +816,7 @@ struct EvalTile {
             const int item = threadIdx.x + it * NT;
             if (item < total) {
                 int g, q;
-                item_tile(item, G, QW, QA, g, q);
+                item_tile(item, G, QW, QA, rW, rA, g, q);
                 const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) V4<Real>::st(S + (g * 8 + r) * NS + j0, acc[it][r]);
@@ -1006,6 +1011,8 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
 
     // float: hidden -> hidden constants as a reference box's plus offsets
     constexpr bool dconst = Tile::kCompensated;
+    // reciprocals of the product tiles' column-quad counts (see item_tile)
+    const uint32_t rW = Tile::recip32((d + 1) * T / 4), rA = Tile::recip32((d + 3) * T / 4);
     int alpha_off = 0;
     for (int k = 1; k < net.K; ++k) {
         Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
@@ -1021,7 +1028,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         }
         __syncthreads();
         // constants and products; barrier inside, then the in-place store
-        Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk);
+        Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA);
         __syncthreads();
     }
     Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
