@@ -71,6 +71,24 @@ __device__ AdjSmem carve_adj(float *sp, const AdjArgs &a) {
     return s;
 }
 
+// Quotient by a loop-invariant divisor n >= 1 without a division per use:
+// with m = floor((2^32 - 1) / n) + 1 (= ceil(2^32 / n) for n >= 2),
+// floor(x m / 2^32) = floor(x / n) whenever x n <= 2^32, because the excess
+// e = m n - 2^32 is below n and so x e / 2^32 < 1 cannot carry the fraction
+// x / n past the next integer.  Larger operands and n = 1 divide plainly.
+struct Div {
+    uint32_t m;
+    int n;
+    bool fast;
+    __device__ __forceinline__ Div(int n_, int x_end) : n(n_) {
+        fast = n_ > 1 && (uint64_t)(uint32_t)x_end * (uint32_t)n_ <= (1ull << 32);
+        m = fast ? 0xFFFFFFFFu / (uint32_t)n_ + 1u : 0u;
+    }
+    __device__ __forceinline__ int operator()(int x) const {
+        return fast ? (int)__umulhi((uint32_t)x, m) : x / n;
+    }
+};
+
 // The boxes a CTA works on together: box q (q < nb) at position pos0 + q,
 // its state at base + q * stride floats.
 struct Group {
@@ -106,11 +124,12 @@ __device__ void build_layer1(const AdjArgs &a, const Group &g) {
     const NetParams<float> &net = a.net;
     const int d = net.d, Q = d + 1, n1 = net.n[1];
     const int work = n1 * Q;
+    const Div by_work(work, g.nb * work), by_n(n1, work);
     for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
-        const int q = it / work;
+        const int q = by_work(it);
         const int li = it - q * work;
-        const int p = li % n1;
-        const int c = li / n1;
+        const int c = by_n(li);
+        const int p = li - c * n1;
         const AdjSmem s = g.box(a, q);
         float v;
         if (c < d) {
@@ -132,11 +151,12 @@ __device__ void relax_layer(const AdjArgs &a, const Group &g, int layer, bool fr
     const int Q = net.d + 1, n = net.n[layer], H = a.H;
     const int off = hidden_offset(net, layer);
     const int work = n * Q;
+    const Div by_work(work, g.nb * work), by_n(n, work);
     for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
-        const int q = it / work;
+        const int q = by_work(it);
         const int li = it - q * work;
-        const int j = li % n;
-        const int c = li / n;
+        const int c = by_n(li);
+        const int j = li - c * n;
         const AdjSmem s = g.box(a, q);
         const float *U = from_chk ? chk_u(a, s, layer) : s.U;
         const float *L = from_chk ? chk_l(a, s, layer) : s.L;
@@ -175,11 +195,13 @@ __device__ void contract(const AdjArgs &a, const Group &g, int k) {
     const int Q = net.d + 1, n_in = net.n[k], n_out = net.n[k + 1];
     const int nch = (Q + kAdjCols - 1) / kAdjCols;
     const int work = n_out * nch;
+    const Div by_work(work, g.nb * work), by_n(n_out, work);
     for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
-        const int q = it / work;
+        const int q = by_work(it);
         const int li = it - q * work;
-        const int p = li % n_out;
-        const int c0 = (li / n_out) * kAdjCols;
+        const int ch = by_n(li);
+        const int p = li - ch * n_out;
+        const int c0 = ch * kAdjCols;
         const int nc = Q - c0 < kAdjCols ? Q - c0 : kAdjCols;
         const AdjSmem s = g.box(a, q);
         float cc[kAdjCols], rr[kAdjCols];
@@ -218,8 +240,9 @@ __device__ void concretize_layer(const AdjArgs &a, const Group &g, int layer) {
     const NetParams<float> &net = a.net;
     const int d = net.d, Q = d + 1, n = net.n[layer], H = a.H;
     const int off = hidden_offset(net, layer);
+    const Div by_n(n, g.nb * n);
     for (int it = threadIdx.x; it < g.nb * n; it += blockDim.x) {
-        const int q = it / n;
+        const int q = by_n(it);
         const int j = it - q * n;
         const AdjSmem s = g.box(a, q);
         const int64_t pos = g.pos0 + q;
@@ -246,8 +269,9 @@ __device__ void concretize_layer(const AdjArgs &a, const Group &g, int layer) {
     }
     if (layer <= a.nck) {
         const int work = n * Q;
+        const Div by_work(work, g.nb * work);
         for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
-            const int q = it / work;
+            const int q = by_work(it);
             const int li = it - q * work;
             const AdjSmem s = g.box(a, q);
             chk_u(a, s, layer)[li] = s.U[li];
@@ -262,8 +286,9 @@ __device__ void recompute(const AdjArgs &a, const Group &g, int layer) {
     int j = layer < a.nck ? layer : a.nck;
     if (j >= 1) {
         const int work = a.net.n[j] * (a.net.d + 1);
+        const Div by_work(work, g.nb * work);
         for (int it = threadIdx.x; it < g.nb * work; it += blockDim.x) {
-            const int q = it / work;
+            const int q = by_work(it);
             const int li = it - q * work;
             const AdjSmem s = g.box(a, q);
             s.U[li] = chk_u(a, s, j)[li];
@@ -315,7 +340,7 @@ __device__ void unfold_add(const AdjArgs &a, const AdjSmem &s, int n_in, float *
 // memory; two instantiations so that the shared one keeps shared-memory
 // instructions.
 template <bool kGlobal>
-__global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(256, 2) slr_adjoint_kernel(const AdjArgs a) {
     extern __shared__ __align__(16) float smem_adj[];
     const NetParams<float> &net = a.net;
     const int K = net.K, d = net.d, Q = d + 1, R = net.R, H = a.H;
@@ -336,8 +361,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
         g.nb = (int)((n - pos0) < B ? (n - pos0) : B);
 
         // ---- the boxes: centre and radius (Sec. 2.2 bisection for path codes) ----
+        const Div by_d(d, B * d);
         for (int it = threadIdx.x; it < g.nb * d; it += blockDim.x) {
-            const int q = it / d;
+            const int q = by_d(it);
             const int i = it - q * d;
             const AdjSmem s = g.box(a, q);
             const BoxSource &src = a.src;
@@ -374,8 +400,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             __syncthreads();
         }
         // row bounds of the folded last layer and their upstream adjoints
+        const Div by_R(R, B * R);
         for (int it = threadIdx.x; it < g.nb * R; it += blockDim.x) {
-            const int q = it / R;
+            const int q = by_R(it);
             const int r = it - q * R;
             const AdjSmem s = g.box(a, q);
             const int64_t pos = pos0 + q;
@@ -401,10 +428,11 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             __syncthreads();
         }
         // d lo_r = d (L_r,d - sum |L_r,c|), d hi_r = d (U_r,d + sum |U_r,c|)
+        const Div by_RQ(R * Q, B * R * Q), by_Q(Q, R * Q);
         for (int it = threadIdx.x; it < g.nb * R * Q; it += blockDim.x) {
-            const int q = it / (R * Q);
+            const int q = by_RQ(it);
             const int li = it - q * R * Q;
-            const int r = li / Q;
+            const int r = by_Q(li);
             const int c = li - r * Q;
             const AdjSmem s = g.box(a, q);
             s.gA[li] = c == d ? s.ghi[r] : s.ghi[r] * sgnf(s.U[li]);
@@ -419,8 +447,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             if (!kept) recompute(a, g, k);
             relax_layer(a, g, k, kept);
             // (gU', gL') -> (gC', gR') = (gU' + gL', gU' - gL')
+            const Div by_oQ(n_out * Q, B * n_out * Q);
             for (int it = threadIdx.x; it < g.nb * n_out * Q; it += blockDim.x) {
-                const int q = it / (n_out * Q);
+                const int q = by_oQ(it);
                 const int li = it - q * n_out * Q;
                 const AdjSmem s = g.box(a, q);
                 const float u = s.gA[li], l = s.gB[li];
@@ -431,8 +460,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             // weight and bias gradients: dW[p][i] = sum_c gC'[p,c] C[i,c] + sgn(W) gR'[p,c] Rr[i,c]
             if (a.dW[k] != nullptr) {
                 const bool last = k == K - 1;
+                const Div by_in(n_in, n_out * n_in);
                 for (int it = threadIdx.x; it < n_out * n_in; it += blockDim.x) {
-                    const int p = it / n_in;
+                    const int p = by_in(it);
                     const int i = it - p * n_in;
                     const float sw = sgnf(weight(net, k, p, i));
                     float acc = 0.f;
@@ -460,11 +490,13 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             }
             // adjoints of the post-relaxation pair: gU^ = (W^T gC' + |W|^T gR') / 2, gL^ = (W^T gC' - |W|^T gR') / 2
             const int nch = (Q + kAdjCols - 1) / kAdjCols;
+            const Div by_ich(n_in * nch, B * n_in * nch), by_i(n_in, n_in * nch);
             for (int it = threadIdx.x; it < g.nb * n_in * nch; it += blockDim.x) {
-                const int q = it / (n_in * nch);
+                const int q = by_ich(it);
                 const int li = it - q * n_in * nch;
-                const int i = li % n_in;
-                const int c0 = (li / n_in) * kAdjCols;
+                const int ch = by_i(li);
+                const int i = li - ch * n_in;
+                const int c0 = ch * kAdjCols;
                 const int nc = Q - c0 < kAdjCols ? Q - c0 : kAdjCols;
                 const AdjSmem s = g.box(a, q);
                 float gc[kAdjCols], gr[kAdjCols];
@@ -496,8 +528,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
             __syncthreads();
             // through the relaxation (Eq. 1) of hidden layer k, one neuron per thread
             const int off = hidden_offset(net, k);
+            const Div by_j(n_in, B * n_in);
             for (int it = threadIdx.x; it < g.nb * n_in; it += blockDim.x) {
-                const int q = it / n_in;
+                const int q = by_j(it);
                 const int j = it - q * n_in;
                 const AdjSmem s = g.box(a, q);
                 const int64_t pos = pos0 + q;
@@ -559,8 +592,9 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
 
         // ---- layer 1: U = L = [W_1 diag(r) | W_1 m + b_1] ----
         const int n1 = net.n[1];
+        const Div by_1Q(n1 * Q, B * n1 * Q);
         for (int it = threadIdx.x; it < g.nb * n1 * Q; it += blockDim.x) {
-            const int q = it / (n1 * Q);
+            const int q = by_1Q(it);
             const int li = it - q * n1 * Q;
             const AdjSmem s = g.box(a, q);
             s.gA[li] += s.gB[li];
@@ -600,7 +634,7 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
         }
         if (a.d_lo != nullptr) {
             for (int it = threadIdx.x; it < g.nb * d; it += blockDim.x) {
-                const int q = it / d;
+                const int q = by_d(it);
                 const int i = it - q * d;
                 const AdjSmem s = g.box(a, q);
                 const int64_t pos = pos0 + q;
@@ -617,7 +651,7 @@ __global__ void __launch_bounds__(256) slr_adjoint_kernel(const AdjArgs a) {
         }
         if (a.d_r != nullptr) {
             for (int it = threadIdx.x; it < g.nb * d; it += blockDim.x) {
-                const int q = it / d;
+                const int q = by_d(it);
                 const int i = it - q * d;
                 const AdjSmem s = g.box(a, q);
                 float gr = 0.f;
