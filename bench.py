@@ -198,6 +198,8 @@ def main():
     ap.add_argument("--shard-level", type=int, default=-1,
                     help="strong scaling: the ranks share one count, rank r taking every N-th subtree below this "
                          "level (default: weak scaling, a problem per rank)")
+    ap.add_argument("--recheck-cluster", action="store_true",
+                    help="FP64 re-check with each tile on a cluster of 4 CTAs instead of one CTA")
     ap.add_argument("--split", default="widest", choices=["widest", "gradient"],
                     help="bisect the widest side, or per box the dimension of the 16-dimension split set "
                          "with the largest |dM/dr| r (adjoint gradient of the decision loss)")
@@ -267,6 +269,9 @@ def main():
         tile = {"tile_boxes": tb, "tile_threads": tt}
     if strong:
         tile.update(shard_count=world, shard_index=rank, shard_level=args.shard_level)
+    if args.recheck_cluster:
+        tile["recheck_cluster"] = 1
+        config["recheck"] = "each FP64 tile on a cluster of 4 CTAs"
     if args.precision == "tf32":
         tile["precision"] = pkg.PREC_TC_TF32
         config["precision"] = "split-TF32 tensor-core contraction (tcgen05), FP32 re-bound and FP64 re-check"

@@ -111,7 +111,11 @@ typedef struct {
                                share of level g (0 <= g <= D); the unsafe volume of levels
                                below g is added by shard 0 only, so the sums of unsafe_lo and
                                of unsafe_hi over the N shards are the whole count's */
-    int32_t reserved2;      /* must be 0 */
+    int32_t recheck_cluster; /* FP64 re-check: 0 (default) = each tile on one CTA; 1 = each tile
+                               on a cluster of 4 CTAs (4 SMs) where the GPU can run one, its
+                               products dealt over them and exchanged through distributed
+                               shared memory.  Both are sound; the products' inputs are summed
+                               in another order, so a bound may differ in its last float64 bits */
 } slr_options;
 
 #define SLR_MAX_LEVELS 63

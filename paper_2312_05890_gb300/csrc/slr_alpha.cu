@@ -11,7 +11,10 @@
 // slopes; every bound that decides a box comes from the sound evaluation
 // kernel at the chosen slopes.
 //
-// One box per CTA.  Per hidden neuron the forward pass keeps five scalars
+// A CTA works on a group of boxes together (as many as fit its shared-memory
+// share; one box with the state in global memory for networks whose state
+// does not fit), every phase a flat loop over the group's elements.  Per
+// hidden neuron the forward pass keeps five scalars
 // (the concrete bounds of both equations and the slope used); the symbolic
 // tensors of a hidden layer are kept in shared memory only for the first
 // `nck` layers and are recomputed from the nearest kept layer during the

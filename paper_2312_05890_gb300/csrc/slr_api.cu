@@ -78,6 +78,7 @@ struct slr_ctx {
     int T32 = 0, T64 = 0, NT32 = 0, NT64 = 0;
     size_t smem32 = 0, smem64 = 0;
     int grid32 = 0, grid64 = 0;
+    int grid64c = 0;   // > 0: the FP64 re-check on clusters (grid of that many CTAs)
     void *tc_buf = nullptr;               // tensor-core weight images
     slr::TcParams tcp{};
     int T_tc = 0, grid_tc = 0;
@@ -817,6 +818,13 @@ int run_adjoint(slr_ctx *ctx, const slr::AdjArgs &a, int grid, int64_t *launches
     return SLR_OK;
 }
 
+// FP64 re-check of a list of boxes (pass 1): on clusters where chosen.
+cudaError_t launch_recheck(slr_ctx *ctx, const slr::BoxSource &src, const slr::EvalOutputs &out) {
+    if (ctx->grid64c > 0)
+        return slr::launch_eval_f64_cluster(ctx->T64, ctx->grid64c, ctx->smem64, ctx->stream, ctx->nd, src, out, 1);
+    return slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, src, out, 1);
+}
+
 int prepare_device(slr_ctx *ctx) {
     if (!ctx->dev_dirty) return SLR_OK;
     if (ctx->widths.back() != (int)(ctx->C.size() / std::max<size_t>(1, ctx->e.size())))
@@ -916,6 +924,14 @@ int prepare_device(slr_ctx *ctx) {
             ctx->smem64 = c.smem;
             ctx->grid64 = c.blocks * ctx->sm_count;
         }
+    }
+    // on request, the same tile on a cluster of CTAs (products dealt over their
+    // SMs) where the GPU runs such clusters
+    ctx->grid64c = 0;
+    if (ctx->T64 > 0 && ctx->T64 <= 4 && ctx->NT64 == 256 && ctx->opt.recheck_cluster == 1 &&
+        slr::eval_gemm_items(ctx->T64, ctx->nd.d, ctx->nd.n_max_pad) <= slr::kRecheckCluster * 256) {
+        const int nc = slr::eval_f64_cluster_max(ctx->T64, ctx->smem64);
+        if (nc > 0) ctx->grid64c = nc * slr::kRecheckCluster;
     }
     // adjoint: keep as many hidden layers' equations in shared memory as fit in
     // 96 KB, recompute the others
@@ -1112,7 +1128,7 @@ void slr_default_options(slr_options *opt) {
     opt->shard_count = 1;
     opt->shard_index = 0;
     opt->shard_level = 0;
-    opt->reserved2 = 0;
+    opt->recheck_cluster = 0;
 }
 
 int slr_create(slr_ctx **out, int device, void *cuda_stream) {
@@ -1211,7 +1227,8 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
         if (opt->relax_mode != SLR_RELAX_NEURIFY)
             return fail(ctx, SLR_EUNSUPPORTED, "slope optimisation needs relax mode NEURIFY");
     }
-    if (opt->reserved2 != 0) return fail(ctx, SLR_EINVAL, "reserved option field must be 0");
+    if (opt->recheck_cluster != 0 && opt->recheck_cluster != 1)
+        return fail(ctx, SLR_EINVAL, "recheck_cluster must be 0 or 1");
     if (opt->shard_count < 1 || opt->shard_index < 0 || opt->shard_index >= opt->shard_count ||
         opt->shard_level < 0 || opt->shard_level > slr::kMaxDepth)
         return fail(ctx, SLR_EINVAL, "shard %d of %d at level %d is not valid", opt->shard_index, opt->shard_count,
@@ -1221,7 +1238,7 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
         return fail(ctx, SLR_EINVAL, "tile_boxes and tile_threads are set together");
     if (opt->relax_mode != ctx->opt.relax_mode || opt->precision != ctx->opt.precision ||
         opt->tile_boxes != ctx->opt.tile_boxes || opt->tile_threads != ctx->opt.tile_threads ||
-        opt->wide != ctx->opt.wide)
+        opt->wide != ctx->opt.wide || opt->recheck_cluster != ctx->opt.recheck_cluster)
         ctx->dev_dirty = true;
     ctx->opt = *opt;
     return SLR_OK;
@@ -1453,7 +1470,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
                 o2.cls = ctx->cls;
                 o2.tie_count = &ctx->ctr->ties;
                 o2.status = ctx->status;
-                CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
+                CK(ctx, launch_recheck(ctx, s2, o2));
                 ++launches;
             }
         } else {
@@ -1469,7 +1486,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
             o2.cls = ctx->cls;
             o2.tie_count = &ctx->ctr->ties;
             o2.status = ctx->status;
-            CK(ctx, slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, s2, o2, 1));
+            CK(ctx, launch_recheck(ctx, s2, o2));
             ++launches;
         }
         }

@@ -38,6 +38,9 @@ constexpr int kMaxDepth = 62;
 constexpr int kSplitPathBits = 16;
 constexpr int kSplitSetMax = 16;
 constexpr int kSplitMaxDepth = 12;
+// CTAs (on as many SMs) of the thread-block cluster that evaluates one tile of
+// the FP64 re-check together.
+constexpr int kRecheckCluster = 4;
 
 enum : uint8_t { kSafe = 0, kUnsafe = 1, kUndecided = 2 };
 enum : int { kRelaxNeurify = 0, kRelaxPaperLiteral = 1, kRelaxInterval = 2 };

@@ -28,6 +28,42 @@
 
 namespace slr {
 
+// ---- thread-block cluster (PTX): rank, barrier, stores to a peer's shared memory ----
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_index_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster arrives (its earlier shared-memory
+// writes released) and waits for all (acquiring theirs).
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(const void *p, uint32_t rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster4(uint32_t addr, const double (&v)[4]) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v[0]), "d"(v[1]) : "memory");
+    asm volatile("st.shared::cluster.v2.f64 [%0+16], {%1, %2};" ::"r"(addr), "d"(v[2]), "d"(v[3]) : "memory");
+}
+
 template <typename Real> struct V4;
 template <> struct V4<float> {
     static __device__ __forceinline__ void ld(const float *p, float (&v)[4]) {
@@ -824,6 +860,83 @@ struct EvalTile {
         }
     }
 
+    // ---- the same phase split over the CL CTAs of a thread-block cluster (float64) ----
+    // Every CTA of the cluster holds the tile's whole state and does the
+    // per-row work itself; the product tiles and the constant items are dealt
+    // round-robin (item i to rank i mod CL), and each CTA writes its results
+    // into the shared memory of every CTA of the cluster.  A product tile's
+    // inputs are split over up to 8 lanes (at least 4 inputs each), added in
+    // a fixed order.  Two cluster barriers: every CTA has read the state
+    // before any overwrites it, and every CTA sees all results before the
+    // next phase.
+    template <int CL, class L>
+    static __device__ void contract_cluster(const L &lay, Real *sConst, const NetParams<Real> &net, int layer,
+                                            Real *S, const Real *sW, int n_in, int Mpad, int d, int NS,
+                                            uint32_t rW, uint32_t rA) {
+        static_assert(sizeof(Real) == 8, "cluster contraction is the float64 re-check's");
+        const int QW = (d + 1) * T / 4;
+        const int QA = (d + 3) * T / 4;
+        const int G = Mpad / 8;
+        const int total = G * (QW + QA);
+        const int rank = (int)cluster_ctarank();
+        const int most = (total + CL - 1) / CL;   // product tiles of rank 0, the most of any rank
+        int parts = 1;
+        while (parts < 8 && 2 * parts * most <= NT && n_in >= 8 * parts) parts *= 2;
+        const int busy = parts * most;
+        const int n_out = net.n[layer + 1];
+        const int n_const = ((n_out + 1) / 2) * T;
+        const int my_const = (n_const - rank + CL - 1) / CL;
+        const int li = (int)threadIdx.x / parts, part = (int)threadIdx.x % parts;
+        const int item = rank + CL * li;
+        const bool has = (int)threadIdx.x < busy && item < total;
+        Real acc[8][4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+        int g = 0, q = 0;
+        if (has) {
+            item_tile(item, G, QW, QA, rW, rA, g, q);
+            const bool is_abs = q >= QW;
+            const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
+            const int i0 = part * n_in / parts, i1 = (part + 1) * n_in / parts;
+            tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, i1 - i0, Mpad, NS, is_abs, acc);
+        }
+        for (int m = 1; m < parts; m *= 2) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], m);
+        }
+        // this rank's constant items on the threads past the products
+        for (int t = (int)threadIdx.x - busy; t < my_const; t += NT)
+            if (t >= 0) const_item(lay, sConst, sW, Mpad, net, layer, rank + CL * t);
+        __syncthreads();
+        cluster_barrier();
+        if (has && part == 0) {
+            const int j0 = q >= QW ? (d + 1) * T + (q - QW) * 4 : q * 4;
+#pragma unroll 1
+            for (int c = 0; c < CL; ++c) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) st_cluster4(cluster_map(S + (g * 8 + r) * NS + j0, c), acc[r]);
+            }
+        }
+        const int nmp = net.n_max_pad;
+        for (int t = (int)threadIdx.x - busy; t < my_const; t += NT) {
+            if (t < 0) continue;
+            const int ci = rank + CL * t;
+            const int qq = ci / T, b = ci - qq * T;
+            for (int p = 2 * qq; p < 2 * qq + 2 && p < n_out; ++p) {
+                for (int k = 0; k < 3; ++k) {
+                    const Real *v = sConst + (k * nmp + p) * T + b;
+                    for (int c = 0; c < CL; ++c)
+                        if (c != rank) st_cluster(cluster_map(v, c), *v);
+                }
+            }
+        }
+        cluster_barrier();
+    }
+
     // Rows of the transposed weights, NT / Mpad rows per pass (one division
     // per thread, not one per element).
     static __device__ void stage_weights(Real *sW, const Real *Wt, int n_in, int n_out, int Mpad) {
@@ -956,7 +1069,7 @@ __device__ __forceinline__ int64_t source_count(const BoxSource &src) {
 // pass 1: re-check of such a list in the higher precision (writes the class,
 //         counts the boxes still depending on E as ties).
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int NT, int KI = 2>
+template <typename Real, int T, int NT, int KI = 2, int CL = 1>
 __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, const EvalOutputs &out, const int pass,
                           const TileSmem<Real> &sm, const int64_t base, const int64_t n) {
     using A = Arith<Real>;
@@ -1028,14 +1141,19 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         }
         __syncthreads();
         // constants and products; barrier inside, then the in-place store
-        Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA);
+        if constexpr (CL > 1) {
+            static_assert(!Tile::kCompensated, "the cluster tile is the float64 re-check's");
+            Tile::template contract_cluster<CL>(lay, sConst, net, k, sS, sW, net.n[k], Mpad, d, NS, rW, rA);
+        } else {
+            Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA);
+        }
         __syncthreads();
     }
     Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
     __syncthreads();
 
-    // ---- classify (Sec. 3) and write ------------------------------------
-    if (threadIdx.x < nb) {
+    // ---- classify (Sec. 3) and write (one CTA of a cluster) ----------------
+    if (threadIdx.x < nb && (CL == 1 || cluster_ctarank() == 0)) {
         const int b = threadIdx.x;
         const uint8_t cls = classify_rows<Real, T>(net, sLo, sHi, sErr, b, (Real)0);
         // optimistic bounds (raw +- E inward): the class the exact SLR could have
@@ -1088,6 +1206,23 @@ slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutput
     const int64_t n = source_count(src);
     for (int64_t base = (int64_t)blockIdx.x * T; base < n; base += (int64_t)gridDim.x * T)
         eval_tile<Real, T, NT, KI>(net, src, out, pass, sm, base, n);
+}
+
+// The float64 re-check with each tile on a cluster of kRecheckCluster CTAs (one
+// per SM): the few boxes of a level's re-check list then take several SMs'
+// float64 units each instead of one.  Every CTA of a cluster runs the same
+// tiles, so all reach the same cluster barriers; the last barrier keeps each
+// CTA resident until no peer can still write to its shared memory.
+template <typename Real, int T, int NT>
+__global__ void __cluster_dims__(kRecheckCluster, 1, 1) __launch_bounds__(NT, 1)
+slr_eval_cluster_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutputs out, const int pass) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileSmem<Real> sm = carve_smem<Real, T>(smem_raw, net.n_max_pad, net.d, net.n_in_max, net.R);
+    const int64_t n = source_count(src);
+    const int64_t c = cluster_index_x(), nc = cluster_count_x();
+    for (int64_t base = c * T; base < n; base += nc * T)
+        eval_tile<Real, T, NT, 2, kRecheckCluster>(net, src, out, pass, sm, base, n);
+    cluster_barrier();
 }
 
 // ---------------------------------------------------------------------------

@@ -68,6 +68,50 @@ int eval_blocks_per_sm_f64(int T, int NT, size_t smem) {
 
 int eval_f64_pair_tile_ok(int d) { return f64_pair_tile_ok(d) ? 1 : 0; }
 
+// The re-check with each tile on a cluster of kRecheckCluster CTAs of 256 threads.
+template <int T>
+static cudaError_t launch_cluster_t(int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
+                                    const BoxSource &src, const EvalOutputs &out, int pass) {
+    auto k = slr_eval_cluster_kernel<double, T, 256>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(net, src, out, pass);
+    return cudaGetLastError();
+}
+
+template <int T>
+static int cluster_max_t(size_t smem) {
+    auto k = slr_eval_cluster_kernel<double, T, 256>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kRecheckCluster * 256, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+cudaError_t launch_eval_f64_cluster(int T, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
+                                    const BoxSource &src, const EvalOutputs &out, int pass) {
+    if (grid <= 0 || grid % kRecheckCluster != 0) return cudaErrorInvalidValue;
+    if (T == 4) return launch_cluster_t<4>(grid, smem, s, net, src, out, pass);
+    if (T == 2 && f64_pair_tile_ok(net.d)) return launch_cluster_t<2>(grid, smem, s, net, src, out, pass);
+    return cudaErrorInvalidValue;
+}
+
+int eval_f64_cluster_max(int T, size_t smem) {
+    if (T == 4) return cluster_max_t<4>(smem);
+    if (T == 2) return cluster_max_t<2>(smem);
+    return 0;
+}
+
 
 template <int T>
 static cudaError_t launch_batch_t(int grid, size_t smem, cudaStream_t s, const NetParams<double> *nets,

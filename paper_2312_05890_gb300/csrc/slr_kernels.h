@@ -28,6 +28,12 @@ int eval_blocks_per_sm_f32(int T, int NT, size_t smem, int items);
 int eval_blocks_per_sm_f64(int T, int NT, size_t smem);
 // 1 when the FP64 kernel can take tiles of two boxes for d inputs.
 int eval_f64_pair_tile_ok(int d);
+// FP64 re-check with each tile on a cluster of kRecheckCluster CTAs (256
+// threads each, T = 2 for odd d or T = 4); grid a multiple of kRecheckCluster.
+cudaError_t launch_eval_f64_cluster(int T, int grid, size_t smem, cudaStream_t s, const NetParams<double> &net,
+                                    const BoxSource &src, const EvalOutputs &out, int pass);
+// Clusters of that kernel the GPU holds at once (0: cannot run it).
+int eval_f64_cluster_max(int T, size_t smem);
 
 // Tensor-core evaluation (FP32 state, split-TF32 contraction on tcgen05).
 size_t eval_tc_smem_bytes(int T, const NetParams<float> &net, const TcParams &tc);

@@ -188,6 +188,61 @@ def test_determinism(pkg):
     assert a == b and la == lb
 
 
+def _recheck_both_ways(pkg, p, D):
+    out = []
+    for cl in (1, 0):
+        with _counter(pkg, p, record_leaves=1, recheck_cluster=cl) as c:
+            r = c.count(D)
+            leaves = sorted(zip(*[x.tolist() for x in c.leaves()]))
+        for k in ("device_ms", "kernel_ms", "h2d_bytes", "d2h_bytes"):
+            r.pop(k)
+        out.append((r, leaves))
+    return out
+
+
+@pytest.mark.parametrize("name,D", [("acas", 17), ("nav", 12), ("tiny", 16)])
+def test_recheck_on_clusters_matches_single_cta(pkg, name, D):
+    """The FP64 re-check with each tile over a cluster of CTAs gives the
+    classes of the one-CTA tile (both sound; only the products' summation
+    order differs).  ACAS-shaped: two-box tiles (odd input count)."""
+    a, b = _recheck_both_ways(pkg, gen.make(name), D)
+    if name == "acas":
+        assert a[0]["rechecked"] > 0
+    assert a == b
+
+
+def _margin_at_a_corner(seed=0, width=32, D=12):
+    """2 -> width -> width -> 1 with dyadic weights, every neuron active on
+    the whole box [-1, 1]^2, so that y is linear there and y(0) = 0 exactly;
+    unsafe: y - 1e-12 >= 0.  The origin is a corner of boxes at every depth:
+    those on either side of the line y = 0 have a margin of -+1e-12, far
+    inside the float32 widening and far outside float64's, so every level
+    sends boxes to the FP64 re-check, which decides them as the oracle does."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.integers(1, 8, size=(width, 2)) / 64.0          # pre-activation >= 1 - 14/64
+    W2 = rng.integers(-8, 9, size=(width, width)) / 512.0    # |W2 h1| <= width * 8/512 * 1.22
+    W3 = rng.integers(-16, 17, size=(1, width)) / 64.0
+    b1 = np.ones(width)
+    b2 = np.ones(width)
+    h2 = W2 @ b1 + b2                                         # at x = 0, exact in float64
+    b3 = -(W3 @ h2)
+    net = gen.Network([w.astype(np.float32) for w in (W1, W2, W3)],
+                      [v.astype(np.float32) for v in (b1, b2, b3)])
+    assert float(b3[0]) == float(np.float32(b3[0]))
+    prop = gen._prop([[(np.ones(1, dtype=np.float32), -1e-12, False)]])
+    lo = np.full(2, -1.0, dtype=np.float32)
+    hi = np.full(2, 1.0, dtype=np.float32)
+    return gen.Problem("corner_margin_2-32-32-1", net, lo, hi, prop, D, seed)
+
+
+def test_recheck_on_clusters_even_inputs(pkg):
+    """Four-box tiles (even input count), both ways against the oracle."""
+    p = _margin_at_a_corner()
+    got = [_check_count(pkg, p, p.depth, recheck_cluster=cl) for cl in (1, 0)]
+    assert got[0]["rechecked"] > 0 and got[0]["tie_leaves"] == 0
+    assert got[0]["rechecked"] == got[1]["rechecked"]
+
+
 def test_without_recheck_is_still_sound(pkg):
     """With the FP64 re-check off, the GPU bracket contains the oracle's."""
     p = gen.acas_shaped(0)
