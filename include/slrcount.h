@@ -24,6 +24,7 @@
 #ifndef SLRCOUNT_H
 #define SLRCOUNT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -337,6 +338,33 @@ int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result
  * or streams at once on one device) race and give wrong counts; run them one
  * after another.  Each call clears the counters it needs before use. */
 int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out);
+
+/* Checkpoint and resume of a count at a level boundary.  Alg. 1 evaluates
+ * the tree level by level (Sec. 3), so between levels t and t + 1 the whole
+ * state of a count is the frontier F_{t+1} (the path codes of the boxes that
+ * level t left UNDECIDED) and the counters of levels 0..t.
+ *
+ * slr_count_checkpoint runs levels 0..t (0 <= t < D) of a count to depth D
+ * and writes that state into the caller's host buffer buf of cap bytes: a
+ * self-describing blob (format tag, D, t, a fingerprint of the network, box,
+ * property and the options that change results, the counters, then the
+ * frontier's 8-byte codes in frontier order).  *used receives its size in
+ * bytes.  If buf is NULL or cap < *used, nothing is written and SLR_EINVAL is
+ * returned with *used set: call again with a buffer that large (the levels
+ * are recomputed, with the same result).  The blob is plain host memory owned
+ * by the caller; it may be written to a file and resumed in another process
+ * on a GPU of the same kind.
+ *
+ * slr_count_resume continues such a count from level t + 1 to its depth D and
+ * fills out as slr_count would for the whole count (counts and per-level
+ * statistics of every level; device_ms, launches and kernel_ms cover the
+ * resumed levels only).  The context must hold the same network, box,
+ * property and result options (precision, relax_mode, fp64_recheck, wide),
+ * else SLR_EINVAL; a blob that is truncated or not a checkpoint gives
+ * SLR_EINVAL.  Neither call supports record_leaves, alpha_steps > 0, the
+ * gradient split rule or sharding (SLR_EUNSUPPORTED). */
+int slr_count_checkpoint(slr_ctx *ctx, int D, int t, void *buf, size_t cap, size_t *used);
+int slr_count_resume(slr_ctx *ctx, const void *buf, size_t bytes, slr_result *out);
 
 /* Message of the last failed call on this context ("" if none).  With a NULL
  * context, the message of the last failed slr_create on this thread. */

@@ -17,6 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libslrcount.so")
 
 SLR_OK = 0
+SLR_EINVAL = -1
 STATUS = {0: "SLR_OK", -1: "SLR_EINVAL", -2: "SLR_ENOMEM", -3: "SLR_ECUDA", -4: "SLR_ESTATE",
           -5: "SLR_EOVERFLOW", -6: "SLR_ETIMEOUT", -7: "SLR_EUNSUPPORTED"}
 SAFE, UNSAFE, UNDECIDED = 0, 1, 2
@@ -32,7 +33,7 @@ MAX_LEVELS = 63
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
            "slr_split_set", "slr_wait_selfcheck", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
-           "slr_optimize_alpha", "slr_last_error")
+           "slr_optimize_alpha", "slr_count_checkpoint", "slr_count_resume", "slr_last_error")
 
 
 class SlrError(RuntimeError):
@@ -123,6 +124,9 @@ def load_library(path: str = LIB_PATH):
         "slr_wait_selfcheck": (ctypes.c_int, [P, ctypes.c_int32]),
         "slr_count_noalloc": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
         "slr_count_batch": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_problem), ctypes.POINTER(slr_result)]),
+        "slr_count_checkpoint": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+        "slr_count_resume": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(slr_result)]),
         "slr_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -364,6 +368,28 @@ def slr_count_noalloc(ctx, D: int) -> dict:
     return res.to_dict()
 
 
+def slr_count_checkpoint(ctx, D: int, t: int, size_hint: int = 1 << 22) -> bytes:
+    """Levels 0..t of a count to depth D; returns the state to resume from (see the header)."""
+    lib = load_library()
+    used = ctypes.c_size_t(0)
+    buf = ctypes.create_string_buffer(size_hint)
+    rc = lib.slr_count_checkpoint(ctx, int(D), int(t), ctypes.cast(buf, ctypes.c_void_p), size_hint, ctypes.byref(used))
+    if rc == SLR_EINVAL and used.value > size_hint:
+        buf = ctypes.create_string_buffer(used.value)
+        rc = lib.slr_count_checkpoint(ctx, int(D), int(t), ctypes.cast(buf, ctypes.c_void_p), used.value,
+                                      ctypes.byref(used))
+    _check(lib, ctx, rc)
+    return buf.raw[:used.value]
+
+
+def slr_count_resume(ctx, state: bytes) -> dict:
+    """Finish a count from a checkpoint; the result covers the whole count."""
+    lib = load_library()
+    res = slr_result()
+    _check(lib, ctx, lib.slr_count_resume(ctx, bytes(state), len(state), ctypes.byref(res)))
+    return res.to_dict()
+
+
 def slr_count_batch(ctx, problems, depths=None):
     """Count many workloads.Problem-like objects together; returns one result dict per problem."""
     lib = load_library()
@@ -455,6 +481,12 @@ class Counter:
 
     def count_noalloc(self, D: int) -> dict:
         return slr_count_noalloc(self.ctx, D)
+
+    def checkpoint(self, D: int, t: int) -> bytes:
+        return slr_count_checkpoint(self.ctx, D, t)
+
+    def resume(self, state: bytes) -> dict:
+        return slr_count_resume(self.ctx, state)
 
     def bounds(self, lo, hi, want_rows=True, want_cls=True, want_err=False, alpha=None):
         return slr_bounds(self.ctx, lo, hi, self.R, want_rows, want_cls, want_err, alpha)

@@ -1309,7 +1309,19 @@ int slr_set_property(slr_ctx *ctx, int n_clauses, const int32_t *rows_per_clause
     return SLR_OK;
 }
 
-int slr_count(slr_ctx *ctx, int D, slr_result *out) {
+// A count's state at a level boundary (checkpoint): the counters of the
+// levels already counted and the frontier of the first level still to run.
+struct ResumeState {
+    int t_first;
+    const slr::LevelCounters *counters;   // host
+    const uint64_t *codes;                // host, frontier of level t_first
+    int64_t n;
+};
+
+// Levels t_first .. t_last of a count to depth D (t_first = 0 without a
+// resume state, t_last = D for a whole count); the result covers every level
+// counted so far.
+static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const ResumeState *rs) {
     int rc = check_ready(ctx);
     if (rc) return rc;
     if (!out) return fail(ctx, SLR_EINVAL, "out is NULL");
@@ -1358,9 +1370,24 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     CK(ctx, cudaMemcpyAsync(ctx->masks, ctx->h_stage + root_bytes, mask_bytes, cudaMemcpyHostToDevice, ctx->stream));
     const int64_t h2d = ctx->h2d_pending + (int64_t)(root_bytes + mask_bytes);
     ctx->h2d_pending = 0;
-    CK(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(slr::LevelCounters), ctx->stream));
+    const int t_first = rs ? rs->t_first : 0;
     CK(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
-    CK(ctx, slr::launch_init_count(ctx->codes[0], ctx->ctr, ctx->stream));
+    int64_t h2d_state = 0;
+    if (!rs) {
+        CK(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(slr::LevelCounters), ctx->stream));
+        CK(ctx, slr::launch_init_count(ctx->codes[0], ctx->ctr, ctx->stream));
+    } else {
+        if (rs->n > ctx->cap)
+            return fail(ctx, SLR_EINVAL, "the checkpoint's frontier of %lld boxes exceeds frontier_cap=%lld",
+                        (long long)rs->n, (long long)ctx->cap);
+        CK(ctx, cudaMemcpyAsync(ctx->ctr, rs->counters, sizeof(slr::LevelCounters), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        if (rs->n > 0)
+            CK(ctx, cudaMemcpyAsync(ctx->codes[t_first & 1], rs->codes, (size_t)rs->n * sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));   // the caller's host buffers are free after return
+        h2d_state = (int64_t)sizeof(slr::LevelCounters) + rs->n * (int64_t)sizeof(uint64_t);
+    }
 
     const bool leaves = ctx->opt.record_leaves != 0;
     const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0 && !ctx->wide;
@@ -1389,7 +1416,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         return capturing ? cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal)
                          : cudaEventRecord(e, ctx->stream);
     };
-    int64_t launches = 1;
+    int64_t launches = rs ? 0 : 1;
     ctx->gemm_ev_used = 0;
     ctx->gemm_launches = 0;
     ctx->gemm_flop = 0;
@@ -1414,7 +1441,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     }
     const uint64_t path_mask = grad_split ? (1ull << slr::kSplitPathBits) - 1ull : ~0ull;
     auto run_levels = [&]() -> int {
-    for (int t = 0; t <= D; ++t) {
+    for (int t = t_first; t <= t_last; ++t) {
         if (sharded && t == shard_g) {
             // this shard's subtrees: every shard_count-th box of level g
             CK(ctx, slr::launch_shard_level(ctx->codes[t & 1], ctx->codes[(t + 1) & 1], ctx->ctr, t,
@@ -1513,7 +1540,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     // The tile path reads no count on the host between levels: its level loop
     // is captured as a CUDA graph once per configuration and buffer set, and
     // replayed (fewer launch gaps between the small kernels of a level).
-    const bool graphable = !ctx->wide && !slopes && !grad_split;
+    const bool graphable = !ctx->wide && !slopes && !grad_split && !rs && t_last == D;
     if (graphable) {
         char key[512];
         std::snprintf(key, sizeof key,
@@ -1599,7 +1626,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     out->levels = levels;
     out->device_ms = ms;
     out->launches = launches;
-    out->h2d_bytes = h2d;
+    out->h2d_bytes = h2d + h2d_state;
     out->tile_boxes = ctx->wide ? ctx->wide_Bc : ctx->T32;
     out->tile_threads = ctx->wide ? 0 : ctx->NT32;
     out->d2h_bytes = (int64_t)(sizeof(slr::LevelCounters) + sizeof(unsigned int) + (slopes ? sizeof h_alpha : 0));
@@ -1611,7 +1638,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
         }
     }
     if (prof) {
-        for (int t = 0; t <= D; ++t) {
+        for (int t = t_first; t <= t_last; ++t) {
             float a = 0.f, b = 0.f, c2 = 0.f;
             cudaEventElapsedTime(&a, ctx->prof_ev[(size_t)t * 6 + 0], ctx->prof_ev[(size_t)t * 6 + 1]);
             cudaEventElapsedTime(&b, ctx->prof_ev[(size_t)t * 6 + 1], ctx->prof_ev[(size_t)t * 6 + 2]);
@@ -1644,6 +1671,119 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) {
     if (st & slr::kStatusTimeout)
         return fail(ctx, SLR_ETIMEOUT, "a bounded wait on the tensor core gave up; the result is incomplete");
     return SLR_OK;
+}
+
+int slr_count(slr_ctx *ctx, int D, slr_result *out) { return count_levels(ctx, D, out, D, nullptr); }
+
+// ---- checkpoint / resume ----------------------------------------------------
+namespace {
+constexpr uint32_t kCkptMagic = 0x43524c53u;   // "SLRC"
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    uint32_t magic, version;
+    int32_t D, t;
+    uint64_t fingerprint;
+    uint64_t n_codes;
+    uint64_t counters_bytes;
+};
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Network, box, property and the options that change a count's result.
+uint64_t problem_fingerprint(const slr_ctx *ctx) {
+    uint64_t h = 14695981039346656037ull;
+    h = fnv1a(h, &ctx->K, sizeof ctx->K);
+    h = fnv1a(h, ctx->widths.data(), ctx->widths.size() * sizeof(int));
+    for (const auto &w : ctx->W) h = fnv1a(h, w.data(), w.size() * sizeof(float));
+    for (const auto &v : ctx->b) h = fnv1a(h, v.data(), v.size() * sizeof(float));
+    h = fnv1a(h, ctx->lo.data(), ctx->lo.size() * sizeof(float));
+    h = fnv1a(h, ctx->hi.data(), ctx->hi.size() * sizeof(float));
+    h = fnv1a(h, &ctx->n_clauses, sizeof ctx->n_clauses);
+    h = fnv1a(h, ctx->rpc.data(), ctx->rpc.size() * sizeof(int));
+    h = fnv1a(h, ctx->C.data(), ctx->C.size() * sizeof(float));
+    h = fnv1a(h, ctx->e.data(), ctx->e.size() * sizeof(float));
+    h = fnv1a(h, ctx->strict.data(), ctx->strict.size());
+    const int32_t o[4] = {ctx->opt.precision, ctx->opt.relax_mode, ctx->opt.fp64_recheck, ctx->wide ? 1 : 0};
+    return fnv1a(h, o, sizeof o);
+}
+
+int check_resumable(slr_ctx *ctx, const char *what) {
+    if (ctx->opt.record_leaves) return fail(ctx, SLR_EUNSUPPORTED, "%s does not record leaves", what);
+    if (ctx->opt.alpha_steps > 0) return fail(ctx, SLR_EUNSUPPORTED, "%s runs fixed slopes only", what);
+    if (ctx->opt.split_rule != SLR_SPLIT_WIDEST)
+        return fail(ctx, SLR_EUNSUPPORTED, "%s splits the widest side only", what);
+    if (ctx->opt.shard_count > 1) return fail(ctx, SLR_EUNSUPPORTED, "%s does not shard", what);
+    return SLR_OK;
+}
+}  // namespace
+
+int slr_count_checkpoint(slr_ctx *ctx, int D, int t, void *buf, size_t cap, size_t *used) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!used) return fail(ctx, SLR_EINVAL, "used is NULL");
+    *used = 0;
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (D < 1 || D > slr::kMaxDepth) return fail(ctx, SLR_EINVAL, "D=%d out of range [1, %d]", D, slr::kMaxDepth);
+    if (t < 0 || t >= D) return fail(ctx, SLR_EINVAL, "checkpoint level t=%d out of range [0, %d)", t, D);
+    if ((rc = check_resumable(ctx, "slr_count_checkpoint"))) return rc;
+    slr_result part;
+    if ((rc = count_levels(ctx, D, &part, t, nullptr))) return rc;
+    // count_levels synchronised the stream and copied the counters to h_ctr
+    const uint64_t n = ctx->h_ctr->frontier_n[t + 1];
+    const size_t need = sizeof(CkptHeader) + sizeof(slr::LevelCounters) + (size_t)n * sizeof(uint64_t);
+    *used = need;
+    if (!buf || cap < need)
+        return fail(ctx, SLR_EINVAL, "the checkpoint needs %zu bytes (buffer of %zu)", need, buf ? cap : (size_t)0);
+    CkptHeader h{kCkptMagic, kCkptVersion, D, t, problem_fingerprint(ctx), n, sizeof(slr::LevelCounters)};
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    std::memcpy(p, &h, sizeof h);
+    std::memcpy(p + sizeof h, ctx->h_ctr, sizeof(slr::LevelCounters));
+    if (n > 0)
+        CK(ctx, cudaMemcpyAsync(p + sizeof h + sizeof(slr::LevelCounters), ctx->codes[(t + 1) & 1],
+                                (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SLR_OK;
+}
+
+int slr_count_resume(slr_ctx *ctx, const void *buf, size_t bytes, slr_result *out) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!out) return fail(ctx, SLR_EINVAL, "out is NULL");
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if ((rc = check_resumable(ctx, "slr_count_resume"))) return rc;
+    const size_t head = sizeof(CkptHeader) + sizeof(slr::LevelCounters);
+    if (!buf || bytes < head) return fail(ctx, SLR_EINVAL, "not a checkpoint (%zu bytes)", bytes);
+    const unsigned char *p = static_cast<const unsigned char *>(buf);
+    CkptHeader h;
+    std::memcpy(&h, p, sizeof h);
+    if (h.magic != kCkptMagic || h.version != kCkptVersion || h.counters_bytes != sizeof(slr::LevelCounters))
+        return fail(ctx, SLR_EINVAL, "not a checkpoint of this library version");
+    if (h.D < 1 || h.D > slr::kMaxDepth || h.t < 0 || h.t >= h.D)
+        return fail(ctx, SLR_EINVAL, "checkpoint with D=%d, t=%d is not valid", h.D, h.t);
+    if (h.n_codes > (bytes - head) / sizeof(uint64_t) || bytes != head + h.n_codes * sizeof(uint64_t))
+        return fail(ctx, SLR_EINVAL, "checkpoint of %zu bytes does not hold its %llu codes", bytes,
+                    (unsigned long long)h.n_codes);
+    CK(ctx, cudaSetDevice(ctx->device));
+    if ((rc = prepare_device(ctx))) return rc;   // decides the path (tile or wide) the fingerprint includes
+    if (h.fingerprint != problem_fingerprint(ctx))
+        return fail(ctx, SLR_EINVAL, "the checkpoint is of another network, box, property or result options");
+    std::vector<unsigned char> ctr(sizeof(slr::LevelCounters));
+    std::memcpy(ctr.data(), p + sizeof h, ctr.size());
+    const slr::LevelCounters *c = reinterpret_cast<const slr::LevelCounters *>(ctr.data());
+    if (c->frontier_n[h.t + 1] != h.n_codes)
+        return fail(ctx, SLR_EINVAL, "checkpoint counters and frontier disagree");
+    std::vector<uint64_t> codes((size_t)h.n_codes);
+    if (h.n_codes > 0) std::memcpy(codes.data(), p + head, (size_t)h.n_codes * sizeof(uint64_t));
+    ResumeState rs{h.t + 1, c, codes.data(), (int64_t)h.n_codes};
+    return count_levels(ctx, h.D, out, h.D, &rs);
 }
 
 int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, const float *alpha,

@@ -54,6 +54,9 @@ def test_null_context_is_rejected_without_a_gpu(lib):
     assert lib.slr_load_network(None, 1, None, None, None) == -1
     assert lib.slr_set_box(None, 1, None, None) == -1
     assert lib.slr_count(None, 3, None) == -1
+    used = ctypes.c_size_t(7)
+    assert lib.slr_count_checkpoint(None, 3, 1, None, 0, ctypes.byref(used)) == -1
+    assert lib.slr_count_resume(None, b"", 0, None) == -1
     assert lib.slr_destroy(None) == 0
     assert b"null context" in lib.slr_last_error(None)
     out = ctypes.c_void_p()
