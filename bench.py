@@ -118,55 +118,82 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# the oracle on the host cores (CPU baseline and reference arm)
+# the oracle on the host cores (CPU baseline, parity, stated error; reference arm)
 # ---------------------------------------------------------------------------
 
-def _worker_init(name, seed, D):
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"
-    global _W
+def oracle_count(p, D, budget_s, procs, leaves=False):
+    """The oracle's level-by-level count of p on `procs` host processes, stopped at
+    a level boundary after `budget_s` seconds (None: every level)."""
+    from oracle import pool
+    return pool.count_levels(p, D, procs=procs, budget_s=budget_s, leaves=leaves)
+
+
+def parity_of(gpu, ref, D):
+    """The GPU count against the oracle's, level by level over the levels the oracle finished
+    (boxes, safe, unsafe, undecided), and the bracket when it finished all of them."""
+    n = len(ref["levels"])
+    keys = ("boxes", "safe", "unsafe", "undecided")
+    first_bad = None
+    for t, lv in enumerate(ref["levels"]):
+        got = {k: gpu["level_" + k][t] for k in keys}
+        if got != {k: lv[k] for k in keys}:
+            first_bad = t
+            break
+    out = {"levels_compared": n, "oracle_complete": ref["complete"], "levels_equal": first_bad is None,
+           "gpu_lo": gpu["unsafe_lo"], "gpu_hi": gpu["unsafe_hi"]}
+    if first_bad is not None:
+        out["first_differing_level"] = first_bad
+    if ref["complete"]:
+        out["oracle_lo"], out["oracle_hi"] = ref["unsafe_lo"], ref["unsafe_hi"]
+        out["bracket_equal"] = (ref["unsafe_lo"], ref["unsafe_hi"]) == (gpu["unsafe_lo"], gpu["unsafe_hi"])
+    out["equal"] = out["levels_equal"] and out.get("bracket_equal", True)
+    return out
+
+
+STATED_ERROR_BOXES = {"tiny": 1024, "acas": 1024, "nav": 512, "mnist": 32}
+
+
+def stated_error(pkg, names=("tiny", "acas", "nav", "mnist"), seed=0):
+    """Per configuration and path: the largest deviation of the GPU row bounds from the
+    FP64 oracle's over random sub-boxes, relative to the row scale max(|lo|, |hi|) + (hi - lo).
+    'raw' is the FP32 SLR bound (sound bound with its widening removed), 'sound' the
+    widened bound the counter decides on, 'widening' the widening itself."""
+    import numpy as np
+
     import oracle
     from workloads import generators as gen
-    p = gen.make(name, seed)
-    _W = (oracle, p, oracle.split_schedule(p.lo, p.hi, D), D)
-
-
-def _worker_level(args):
-    codes, t = args
-    import numpy as np
-    oracle, p, sched, D = _W
-    codes = np.asarray(codes, dtype=np.int64)
-    lo, hi = oracle.decode(codes, t, sched, p.lo, p.hi)
-    rlo, rhi, _ = oracle.slr_forward(p.net, lo, hi, p.prop)
-    cls = oracle.classify(rlo, rhi, p.prop)
-    return codes[cls == oracle.UNDECIDED], int((cls == oracle.UNSAFE).sum())
-
-
-def oracle_sample(name, seed, D, budget_s, procs):
-    """The oracle's level-by-level count, its levels split over `procs` processes, stopped at a
-    level boundary after `budget_s` seconds.  Returns (boxes, seconds, levels)."""
-    import multiprocessing as mp
-
-    import numpy as np
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs, initializer=_worker_init, initargs=(name, seed, D)) as pool:
-        pool.map(_worker_level, [(np.zeros(1, np.int64), 0)] * procs)      # warm the workers
-        frontier = np.zeros(1, dtype=np.int64)
-        boxes, levels = 0, 0
-        t0 = time.perf_counter()
-        for t in range(D + 1):
-            if frontier.shape[0] == 0:
-                break
-            chunks = [c for c in np.array_split(frontier, max(1, min(procs * 4, frontier.shape[0]))) if c.size]
-            res = pool.map(_worker_level, [(c, t) for c in chunks])
-            boxes += int(frontier.shape[0])
-            levels = t + 1
-            und = np.concatenate([r[0] for r in res]) if res else np.zeros(0, np.int64)
-            frontier = np.concatenate([2 * und, 2 * und + 1]) if t < D else und
-            if time.perf_counter() - t0 > budget_s:
-                break
-        dt = time.perf_counter() - t0
-    return boxes, dt, levels
+    out = {}
+    for name in names:
+        p = gen.make(name)
+        n = STATED_ERROR_BOXES[name]
+        rng = np.random.default_rng(seed + 77)
+        u = np.sort(rng.random((2, n, p.d)), axis=0)
+        lo = (p.lo + (p.hi - p.lo) * u[0]).astype(np.float32)
+        hi = (p.lo + (p.hi - p.lo) * u[1]).astype(np.float32)
+        olo, ohi, _ = oracle.slr_forward(p.net, lo.astype(np.float64), hi.astype(np.float64), p.prop)
+        scale = np.maximum(np.abs(olo), np.abs(ohi)) + (ohi - olo) + 1e-30
+        paths = {"fp32_tile": {}, "tf32_tile": {"precision": pkg.PREC_TC_TF32}, "wide_tf32": {"wide": 1}}
+        if name == "mnist":
+            paths = {"wide_tf32": {}}
+        out[name] = {"boxes": n}
+        for path, opt in paths.items():
+            with pkg.Counter(0) as c:
+                c.set_problem(p)
+                if opt:
+                    c.set_options(**opt)
+                try:
+                    rl, rh, _, err = c.bounds(lo, hi, want_err=True)
+                except pkg.SlrError as e:      # e.g. a shape the tensor-core tile does not take
+                    out[name][path] = {"unavailable": str(e)}
+                    continue
+            rl = rl.astype(np.float64)
+            rh = rh.astype(np.float64)
+            raw = max(np.max(np.abs(rl + err - olo) / scale), np.max(np.abs(rh - err - ohi) / scale))
+            snd = max(np.max(np.abs(rl - olo) / scale), np.max(np.abs(rh - ohi) / scale))
+            sound = bool(np.all(rl <= olo + 1e-12 * scale) and np.all(rh >= ohi - 1e-12 * scale))
+            out[name][path] = {"raw": float(raw), "sound": float(snd), "widening": float(np.max(err / scale)),
+                               "contains_oracle": sound}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -182,7 +209,8 @@ def main():
     ap.add_argument("--workload", default="acas")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--depth", type=int, default=0, help="depth cap (default: the workload's)")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=40.0,
+                    help="the oracle leg stops at the first level boundary after this many seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (MB)")
@@ -200,6 +228,12 @@ def main():
                          "level (default: weak scaling, a problem per rank)")
     ap.add_argument("--recheck-cluster", action="store_true",
                     help="FP64 re-check with each tile on a cluster of 4 CTAs instead of one CTA")
+    ap.add_argument("--no-forms", action="store_true", help="skip the short legs of the chosen forms")
+    ap.add_argument("--no-batch-form", action="store_true", help="skip the batched leg among the forms")
+    ap.add_argument("--form-steps", type=int, default=3, help="timed counts per form leg")
+    ap.add_argument("--form-alpha-steps", type=int, default=20, help="Adam steps of the slope-optimised form")
+    ap.add_argument("--no-stated-error", action="store_true",
+                    help="skip the per-configuration bound error against the oracle")
     ap.add_argument("--split", default="widest", choices=["widest", "gradient"],
                     help="bisect the widest side, or per box the dimension of the 16-dimension split set "
                          "with the largest |dM/dr| r (adjoint gradient of the decision loss)")
@@ -233,14 +267,18 @@ def main():
             return
         budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
         for _ in range(args.warmup):
-            oracle_sample(args.workload, args.seed, D, budget, procs)
-        tot_boxes, tot_s, lv = 0, 0.0, 0
+            oracle_count(p, D, budget, procs)
+        tot_boxes, tot_s, reached = 0, 0.0, []
         for _ in range(args.steps):
-            b, s, lv = oracle_sample(args.workload, args.seed, D, budget, procs)
-            tot_boxes += b
-            tot_s += s
+            r = oracle_count(p, D, budget, procs)
+            tot_boxes += r["boxes"]
+            tot_s += r["seconds"]
+            reached.append(len(r["levels"]))
         v = tot_boxes / tot_s
-        sample = f"levels 0..{lv - 1} of the count ({tot_boxes // max(1, args.steps)} boxes per step)"
+        depths = f"{min(reached) - 1}" if min(reached) == max(reached) else f"{min(reached) - 1}-{max(reached) - 1}"
+        sample = (f"levels 0..{depths} of the count: each step stops at the first level boundary after "
+                  f"{budget:.1f} s (steps reached mixed depths when a range is given), "
+                  f"{tot_boxes // max(1, args.steps)} boxes per step on average")
         print(json.dumps({
             "impl": "reference", "metric": "slr_subdomain_bounds_per_sec", "value": v, "unit": "boxes/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -318,6 +356,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t_wall
+    # the FP32 FMA rate under the same clocks: the roofline denominator of the tile kernel
+    fp32_peak = pkg.slr_measure_fp32_peak(local_rank)
     clocks = sampler.stop()
     last = r
 
@@ -343,14 +383,18 @@ def main():
     eval_s = kern[0] / 1e3
     achieved = fpb * boxes / eval_s / 1e12
     clk = clocks.get("sm_mhz") or 2070.0
-    peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    nominal = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    peak = fp32_peak["tflops"]
     eval_launches = args.steps * (D + 1)
     traffic = None
     if TRAFFIC["source_sha"] == kernel_sha() and TRAFFIC["bytes_per_box"]:
         traffic = TRAFFIC["bytes_per_box"] * boxes / eval_launches
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "slr_eval_kernel<float>",
-                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk:.0f} MHz (sampled median)",
+                "peak_basis": (f"measured: FFMA-throughput kernel in this process ({fp32_peak['ms']:.1f} ms, 16 "
+                               f"independent chains per thread, 2048 threads per SM); nominal at the sampled "
+                               f"{clk:.0f} MHz: {SMS} x {FP32_LANES_PER_SM} lanes x 2 = {nominal:.1f} TFLOP/s"),
+                "frac_of_nominal": achieved / nominal,
                 "flop_per_box": fpb, "kernel_share": kern[0] / max(1e-9, sum(dev_ms)),
                 "avg_launch_ms": kern[0] / eval_launches}
     if gemm_launches:
@@ -367,11 +411,24 @@ def main():
                     "executed_tflops": 3 * ach, "kernel_share": gemm_ms / max(1e-9, sum(dev_ms)),
                     "avg_launch_ms": gemm_ms / gemm_launches, "launches": gemm_launches}
 
-    cpu = None
+    # ---- chosen forms against the plain FP32 path (short legs, same problem) ----
+    forms = None
+    if not args.no_forms and not strong and args.alpha_steps == 0 and args.precision == "fp32" \
+            and args.split == "widest":
+        forms = run_forms(pkg, p, D, args, last, flush)
+
+    # ---- the oracle on the host cores: CPU baseline, parity of the count, stated error ----
+    cpu = parity = serr = None
     if rank == 0 and not args.no_cpu_baseline:
-        cb, cs, lv = oracle_sample(args.workload, args.seed, D, args.cpu_budget, procs)
-        cpu = {"value": cb / cs, "unit": "boxes/s", "cores": procs, "kind": "oracle",
-               "sample": f"levels 0..{lv - 1} of the same count, {cb} boxes, {cs:.1f} s, one process per core"}
+        ref = oracle_count(p, D, args.cpu_budget, procs)
+        lv = len(ref["levels"])
+        cpu = {"value": ref["boxes"] / ref["seconds"], "unit": "boxes/s", "cores": ref["procs"], "kind": "oracle",
+               "sample": (f"levels 0..{lv - 1} of the same count" + (" (the whole count)" if ref["complete"] else "")
+                          + f", {ref['boxes']} boxes, {ref['seconds']:.1f} s, one process per core")}
+        if not strong and args.alpha_steps == 0 and args.split == "widest":
+            parity = parity_of(last, ref, D)
+        if not args.no_stated_error and args.workload in STATED_ERROR_BOXES:
+            serr = stated_error(pkg)
 
     if rank == 0:
         line = {
@@ -390,6 +447,12 @@ def main():
             "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks,
         }
+        if parity is not None:
+            line["parity"] = parity
+        if forms is not None:
+            line["forms"] = forms
+        if serr is not None:
+            line["stated_error"] = serr
         def summary(x):
             return {"unsafe_lo": x["unsafe_lo"], "unsafe_hi": x["unsafe_hi"], "boxes": x["boxes"],
                     "device_ms": x["device_ms"], "boxes_per_s": x["boxes"] / (x["device_ms"] / 1e3)}
@@ -401,8 +464,78 @@ def main():
             if fixed_split is not None:
                 line["slope_opt"]["fixed_slopes_gradient_split"] = summary(fixed_split)
         print(json.dumps(line))
+        if parity is not None and not parity["equal"]:
+            sys.stderr.write("bench: the GPU count differs from the oracle's: %s\n" % json.dumps(parity))
+            c.close()
+            multirank.finish(dist)
+            sys.exit(3)
     c.close()
     multirank.finish(dist)
+
+
+def run_forms(pkg, p, D, args, fp32, flush):
+    """Short legs of the chosen forms on the same problem: the split-TF32 tensor-core
+    contraction, slope-optimised counting (projected Adam on the lower slopes) and,
+    as its own workload, the batched persistent count; each against the plain FP32
+    path (the timed leg) at equal counts."""
+    import torch
+
+    def leg(opts, steps, warm):
+        with pkg.Counter(torch.cuda.current_device()) as c:
+            c.set_problem(p)
+            c.set_options(**opts)
+            for _ in range(warm):
+                c.count(D)
+            ms, boxes = [], 0
+            for _ in range(steps):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                r = c.count(D)
+                ms.append(r["device_ms"])
+                boxes += r["boxes"]
+        out = {"boxes_per_s": boxes / (sum(ms) / 1e3), "ms_per_count": sum(ms) / len(ms),
+               "unsafe_lo": r["unsafe_lo"], "unsafe_hi": r["unsafe_hi"], "boxes": r["boxes"], "steps": steps}
+        return out, r
+
+    forms = {"fp32": {"boxes_per_s": fp32["boxes"] / (fp32["device_ms"] / 1e3), "ms_per_count": fp32["device_ms"],
+                      "unsafe_lo": fp32["unsafe_lo"], "unsafe_hi": fp32["unsafe_hi"], "boxes": fp32["boxes"],
+                      "note": "the timed leg above"}}
+    try:
+        f, r = leg({"precision": pkg.PREC_TC_TF32}, args.form_steps, 1)
+        f["same_count_as_fp32"] = (r["unsafe_lo"], r["unsafe_hi"]) == (fp32["unsafe_lo"], fp32["unsafe_hi"])
+        f["rechecked_fp32"] = r["rechecked_fp32"]
+        forms["split_tf32"] = f
+    except pkg.SlrError as e:
+        forms["split_tf32"] = {"unavailable": str(e)}
+    steps = args.form_alpha_steps
+    f, r = leg({"alpha_steps": steps, "alpha_lr": 0.1}, max(1, args.form_steps - 1), 1)
+    f["alpha_steps"] = steps
+    f["alpha_boxes"] = r["alpha_boxes"]
+    f["alpha_decided"] = r["alpha_decided"]
+    f["nested_in_fp32"] = fp32["unsafe_lo"] <= r["unsafe_lo"] <= r["unsafe_hi"] <= fp32["unsafe_hi"]
+    f["boxes_saved_vs_fp32"] = fp32["boxes"] - r["boxes"]
+    forms["slope_optimised"] = f
+    if not args.no_batch_form:
+        forms["batched"] = batch_form(pkg, args, flush)
+    return forms
+
+
+def batch_form(pkg, args, flush):
+    """One short leg of the batched workload (256 problems of uneven size per step)."""
+    import torch
+
+    from workloads import generators as gen
+    probs = gen.batched_uneven(args.seed)
+    with pkg.Counter(torch.cuda.current_device()) as c:
+        c.count_batch(probs)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        res = c.count_batch(probs)
+    boxes = sum(r["boxes"] for r in res)
+    ms = res[0]["device_ms"]
+    return {"boxes_per_s": boxes / (ms / 1e3), "ms_per_step": ms, "problems": len(probs), "boxes": boxes,
+            "workload": "batched: 256 problems over 16 networks, depth caps 12-22 (its own workload; "
+                        "--workload batch times it in full)"}
 
 
 def bench_batch(args, world, rank, local_rank):
@@ -457,7 +590,7 @@ def bench_batch(args, world, rank, local_rank):
         cb = 0
         for p in probs:
             cb += oracle.count(p.net, p.lo, p.hi, p.prop, p.depth, max_boxes=4096).boxes
-            if time.perf_counter() - t0 > args.cpu_budget:
+            if time.perf_counter() - t0 > min(args.cpu_budget, 20.0):
                 break
         cs = time.perf_counter() - t0
         cpu = {"value": cb / cs, "unit": "boxes/s", "cores": 1, "kind": "oracle",

@@ -318,10 +318,15 @@ int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems, slr_result
 /* slr_count for callers that cannot allocate GPU memory.  The paper has no
  * counterpart: this entry exists for programs that set the library up once
  * and then count from code where cudaMalloc/cudaFree are not allowed (while a
- * framework's caching allocator holds the device memory, inside a real-time
- * loop that must not stall on allocation, or while capturing a CUDA graph).
+ * framework's caching allocator holds the device memory, or inside a
+ * real-time loop that must not stall on allocation, which can synchronise the
+ * whole device).
  *
- * Same arguments, result and classification as slr_count, but every scratch
+ * It runs the FP32 tile path with fixed slopes and the one-CTA FP64 re-check:
+ * a context set to the wide path, alpha_steps > 0, precision TC_TF32,
+ * recheck_cluster, the gradient split rule or sharding gets SLR_EUNSUPPORTED.
+ * Otherwise it takes the same arguments and gives the same result and
+ * classification as slr_count, but every scratch
  * buffer (two frontiers of path codes, class bytes, the FP64 re-check list,
  * level counters, root box and split masks) lives in one fixed device array
  * of about 4.8 MB that the library defines at file scope: each GPU that loads
@@ -359,12 +364,25 @@ int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out);
  * fills out as slr_count would for the whole count (counts and per-level
  * statistics of every level; device_ms, launches and kernel_ms cover the
  * resumed levels only).  The context must hold the same network, box,
- * property and result options (precision, relax_mode, fp64_recheck, wide),
- * else SLR_EINVAL; a blob that is truncated or not a checkpoint gives
- * SLR_EINVAL.  Neither call supports record_leaves, alpha_steps > 0, the
+ * property and result options (precision, relax_mode, fp64_recheck,
+ * recheck_cluster, wide), else SLR_EINVAL; a blob that is truncated or not a
+ * checkpoint gives SLR_EINVAL.  The blob also records the FP32 tile (boxes
+ * and threads per CTA) of the checkpointed levels: the resumed levels run
+ * that tile, whatever the context's own choice, because the tile fixes the
+ * order of the FP32 sums and so which boxes take the FP64 re-check.  Neither call supports record_leaves, alpha_steps > 0, the
  * gradient split rule or sharding (SLR_EUNSUPPORTED). */
 int slr_count_checkpoint(slr_ctx *ctx, int D, int t, void *buf, size_t cap, size_t *used);
 int slr_count_resume(slr_ctx *ctx, const void *buf, size_t bytes, slr_result *out);
+
+/* Measurement aid (no paper counterpart): the FP32 fused multiply-add rate of
+ * CUDA device `device` in TFLOP/s (2 FLOP per FMA), the roofline denominator
+ * of the CUDA-core kernels.  Runs, on a stream of its own, a kernel in which
+ * every thread of 8 CTAs of 256 threads per SM issues 16 independent FMA
+ * chains of `iters` steps (>= 1; 1 << 19 takes about 70 ms on a GB300), four
+ * times, and reports the fastest of the last three: *tflops (required) and
+ * its duration in ms (*ms, nullable).  SLR_EINVAL for a NULL tflops or
+ * iters < 1, SLR_ECUDA if a CUDA call fails. */
+int slr_measure_fp32_peak(int device, int iters, double *tflops, double *ms);
 
 /* Message of the last failed call on this context ("" if none).  With a NULL
  * context, the message of the last failed slr_create on this thread. */

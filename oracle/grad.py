@@ -31,13 +31,17 @@ def _central(f, x0, h):
     return g
 
 
-def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6, w_idx=None):
+def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6, w_idx=None, alpha_idx=None,
+                 box_idx=None):
     """Central-difference gradients of J; entries at kinks are NaN.
 
     alpha: list of per-layer slope arrays, or None for the slopes u/(u-l)
     (then J is differentiated through that formula and 'alpha' is empty).
     w_idx: optional dict layer -> flat indices of the weights to difference
     (the others are NaN); all weights when None.
+    alpha_idx, box_idx: optional indices (into the concatenated slopes, and
+    into the input dimensions for both box endpoints) to difference; the
+    others are NaN; all when None.
     Returns dict with 'alpha' (list per hidden layer), 'lo', 'hi', 'W', 'b'.
     """
     lo = np.asarray(lo, np.float64)
@@ -71,11 +75,11 @@ def fd_gradients(net, lo, hi, prop, alpha, w_hi, w_lo, h=1e-3, tol=1e-6, w_idx=N
     out = {}
     if free:
         a0 = np.concatenate(alpha) if alpha else np.zeros(0)
-        out["alpha"] = split(both(lambda v: objective(net, lo, hi, prop, split(v), w_hi, w_lo), a0))
+        out["alpha"] = split(both(lambda v: objective(net, lo, hi, prop, split(v), w_hi, w_lo), a0, alpha_idx))
     else:
         out["alpha"] = []
-    out["lo"] = both(lambda v: objective(net, v, hi, prop, alpha, w_hi, w_lo), lo)
-    out["hi"] = both(lambda v: objective(net, lo, v, prop, alpha, w_hi, w_lo), hi)
+    out["lo"] = both(lambda v: objective(net, v, hi, prop, alpha, w_hi, w_lo), lo, box_idx)
+    out["hi"] = both(lambda v: objective(net, lo, v, prop, alpha, w_hi, w_lo), hi, box_idx)
 
     class _N:
         pass

@@ -33,7 +33,8 @@ MAX_LEVELS = 63
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
            "slr_split_set", "slr_wait_selfcheck", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
-           "slr_optimize_alpha", "slr_count_checkpoint", "slr_count_resume", "slr_last_error")
+           "slr_optimize_alpha", "slr_count_checkpoint", "slr_count_resume", "slr_measure_fp32_peak",
+           "slr_last_error")
 
 
 class SlrError(RuntimeError):
@@ -127,6 +128,8 @@ def load_library(path: str = LIB_PATH):
         "slr_count_checkpoint": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t,
                                                 ctypes.POINTER(ctypes.c_size_t)]),
         "slr_count_resume": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(slr_result)]),
+        "slr_measure_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double)]),
         "slr_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -366,6 +369,17 @@ def slr_count_noalloc(ctx, D: int) -> dict:
     res = slr_result()
     _check(lib, ctx, lib.slr_count_noalloc(ctx, int(D), ctypes.byref(res)))
     return res.to_dict()
+
+
+def slr_measure_fp32_peak(device: int = 0, iters: int = 1 << 19) -> dict:
+    """FP32 FMA rate of the device in TFLOP/s, measured by the library's FFMA kernel."""
+    lib = load_library()
+    tf = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    rc = lib.slr_measure_fp32_peak(int(device), int(iters), ctypes.byref(tf), ctypes.byref(ms))
+    if rc != SLR_OK:
+        raise SlrError(rc, "slr_measure_fp32_peak failed")
+    return {"tflops": tf.value, "ms": ms.value, "iters": int(iters)}
 
 
 def slr_count_checkpoint(ctx, D: int, t: int, size_hint: int = 1 << 22) -> bytes:

@@ -1076,6 +1076,13 @@ int slr_internal_noalloc_view(slr_ctx *ctx, slr_noalloc_view *v) {
     if (ctx->opt.split_rule != SLR_SPLIT_WIDEST)
         return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc splits the widest side only");
     if (ctx->opt.shard_count > 1) return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc does not shard");
+    // options whose count differs from the fixed-slope FP32 tile path it runs
+    if (ctx->opt.alpha_steps > 0)
+        return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc counts with fixed slopes only (alpha_steps > 0)");
+    if (ctx->opt.precision != SLR_PREC_FP32)
+        return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc runs the FP32 contraction only (precision != FP32)");
+    if (ctx->opt.recheck_cluster != 0)
+        return fail(ctx, SLR_EUNSUPPORTED, "slr_count_noalloc re-checks each tile on one CTA (recheck_cluster)");
     v->device = ctx->device;
     v->stream = ctx->stream;
     v->d = ctx->widths[0];
@@ -1678,14 +1685,19 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) { return count_levels(ctx, D
 // ---- checkpoint / resume ----------------------------------------------------
 namespace {
 constexpr uint32_t kCkptMagic = 0x43524c53u;   // "SLRC"
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
+// The FP32 tile (boxes and threads per CTA) is part of the state: small tiles
+// split a product's inputs over lanes, so the summation order, and with it
+// which boxes land on the FP64 re-check list, depends on the tile.  A resume
+// runs the checkpoint's tile whatever the autotuner of its context chose.
 struct CkptHeader {
     uint32_t magic, version;
     int32_t D, t;
     uint64_t fingerprint;
     uint64_t n_codes;
     uint64_t counters_bytes;
+    int32_t tile_boxes, tile_threads;
 };
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
@@ -1711,7 +1723,8 @@ uint64_t problem_fingerprint(const slr_ctx *ctx) {
     h = fnv1a(h, ctx->C.data(), ctx->C.size() * sizeof(float));
     h = fnv1a(h, ctx->e.data(), ctx->e.size() * sizeof(float));
     h = fnv1a(h, ctx->strict.data(), ctx->strict.size());
-    const int32_t o[4] = {ctx->opt.precision, ctx->opt.relax_mode, ctx->opt.fp64_recheck, ctx->wide ? 1 : 0};
+    const int32_t o[5] = {ctx->opt.precision, ctx->opt.relax_mode, ctx->opt.fp64_recheck, ctx->wide ? 1 : 0,
+                          ctx->opt.recheck_cluster};
     return fnv1a(h, o, sizeof o);
 }
 
@@ -1742,7 +1755,8 @@ int slr_count_checkpoint(slr_ctx *ctx, int D, int t, void *buf, size_t cap, size
     *used = need;
     if (!buf || cap < need)
         return fail(ctx, SLR_EINVAL, "the checkpoint needs %zu bytes (buffer of %zu)", need, buf ? cap : (size_t)0);
-    CkptHeader h{kCkptMagic, kCkptVersion, D, t, problem_fingerprint(ctx), n, sizeof(slr::LevelCounters)};
+    CkptHeader h{kCkptMagic, kCkptVersion, D, t, problem_fingerprint(ctx), n, sizeof(slr::LevelCounters),
+                 ctx->T32, ctx->NT32};
     unsigned char *p = static_cast<unsigned char *>(buf);
     std::memcpy(p, &h, sizeof h);
     std::memcpy(p + sizeof h, ctx->h_ctr, sizeof(slr::LevelCounters));
@@ -1783,7 +1797,27 @@ int slr_count_resume(slr_ctx *ctx, const void *buf, size_t bytes, slr_result *ou
     std::vector<uint64_t> codes((size_t)h.n_codes);
     if (h.n_codes > 0) std::memcpy(codes.data(), p + head, (size_t)h.n_codes * sizeof(uint64_t));
     ResumeState rs{h.t + 1, c, codes.data(), (int64_t)h.n_codes};
-    return count_levels(ctx, h.D, out, h.D, &rs);
+    if (ctx->wide || (h.tile_boxes == ctx->T32 && h.tile_threads == ctx->NT32))
+        return count_levels(ctx, h.D, out, h.D, &rs);
+    // the checkpoint's FP32 tile for the resumed levels, the context's own afterwards
+    TileChoice tile{};
+    for (const TileChoice &cand : tile_candidates(ctx->nf))
+        if (cand.T == h.tile_boxes && cand.NT == h.tile_threads) tile = cand;
+    if (tile.T == 0)
+        return fail(ctx, SLR_EINVAL, "the checkpoint's tile %d x %d is not available for this network", h.tile_boxes,
+                    h.tile_threads);
+    const int T0 = ctx->T32, NT0 = ctx->NT32, g0 = ctx->grid32;
+    const size_t s0 = ctx->smem32;
+    ctx->T32 = tile.T;
+    ctx->NT32 = tile.NT;
+    ctx->smem32 = tile.smem;
+    ctx->grid32 = tile.blocks * ctx->sm_count;
+    rc = count_levels(ctx, h.D, out, h.D, &rs);
+    ctx->T32 = T0;
+    ctx->NT32 = NT0;
+    ctx->grid32 = g0;
+    ctx->smem32 = s0;
+    return rc;
 }
 
 int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, const float *alpha,

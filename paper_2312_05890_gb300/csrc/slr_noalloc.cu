@@ -3,10 +3,9 @@
 //
 // Who needs it: a caller that sets the library up once and then counts from a
 // loop in which allocation is not allowed or not possible, for example while
-// a framework's caching allocator already holds the device memory, inside a
-// real-time control loop that must not stall on cudaMalloc/cudaFree (they can
-// synchronise the device), or while building a CUDA graph by stream capture,
-// where allocation calls are not permitted.
+// a framework's caching allocator already holds the device memory, or inside
+// a real-time control loop that must not stall on cudaMalloc/cudaFree (they
+// can synchronise the device).
 //
 // How: every buffer the count needs besides the network (two frontiers of
 // path codes, the class bytes, the re-check list, the level counters and the

@@ -38,3 +38,29 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_parity_field_compares_levels_and_bracket():
+    """bench.parity_of: equal when every level the oracle finished and the
+    bracket agree; a differing level or bracket is reported (CPU)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from workloads import generators as gen
+    p = gen.tiny(0)
+    D = 10
+    want = oracle.count(p.net, p.lo, p.hi, p.prop, D)
+    ref = {"levels": want.levels, "complete": True, "unsafe_lo": want.unsafe_lo, "unsafe_hi": want.unsafe_hi}
+    gpu = {"unsafe_lo": want.unsafe_lo, "unsafe_hi": want.unsafe_hi}
+    for k in ("boxes", "safe", "unsafe", "undecided"):
+        gpu["level_" + k] = [lv[k] for lv in want.levels]
+    assert bench.parity_of(gpu, ref, D)["equal"]
+    bad = dict(gpu, level_safe=list(gpu["level_safe"]))
+    bad["level_safe"][5] += 1
+    r = bench.parity_of(bad, ref, D)
+    assert not r["equal"] and r["first_differing_level"] == 5
+    r = bench.parity_of(dict(gpu, unsafe_hi=gpu["unsafe_hi"] + 1), ref, D)
+    assert not r["equal"] and r["levels_equal"] and not r["bracket_equal"]
+    part = dict(ref, levels=want.levels[:4], complete=False)
+    r = bench.parity_of(gpu, part, D)
+    assert r["equal"] and r["levels_compared"] == 4 and "oracle_lo" not in r

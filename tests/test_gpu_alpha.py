@@ -401,3 +401,39 @@ def test_wide_count_with_slopes_nests(pkg):
         opt = c.count(D)
     assert fixed["unsafe_lo"] <= opt["unsafe_lo"] <= opt["unsafe_hi"] <= fixed["unsafe_hi"]
     assert opt["alpha_boxes"] > 0
+
+
+@pytest.mark.parametrize("free", [True, False])
+def test_wide_product_adjoint_mnist_against_oracle(pkg, free):
+    """784 -> 3x256 -> 10: the per-layer tensor-core product adjoint that the
+    slope-optimised MNIST-shaped count runs, against the FP64 oracle's central
+    differences (h = 1e-3) at 200 sampled slope coordinates and 100 sampled
+    input dimensions (both endpoints) of each of two boxes, within 2e-3 of each
+    array's scale; free slopes and the default slopes u/(u-l)."""
+    from oracle import pool
+    p = gen.make("mnist")
+    n = 2
+    lo, hi = random_sub_boxes(p, n, seed=16, min_frac=0.5)
+    R = p.prop.C.shape[0]
+    rng = np.random.default_rng(21 + int(free))
+    g_lo = rng.normal(size=(n, R)).astype(np.float32)
+    g_hi = rng.normal(size=(n, R)).astype(np.float32)
+    with _counter(pkg, p) as c:
+        H = c.alpha_width()
+        A = rng.uniform(0.05, 0.95, size=(n, H)).astype(np.float32) if free else None
+        out = c.margin_backward(lo, hi, g_lo, g_hi, alpha=A)
+    checked = 0
+    for b in range(n):
+        a_idx = sorted(rng.choice(H, size=200, replace=False).tolist())
+        b_idx = sorted(rng.choice(p.d, size=100, replace=False).tolist())
+        fd = pool.fd_gradients_sampled(p.net, lo[b].astype(np.float64), hi[b].astype(np.float64), p.prop,
+                                       _split_alpha(p.net, A[b].astype(np.float64)) if free else None,
+                                       g_hi[b].astype(np.float64), g_lo[b].astype(np.float64), a_idx, b_idx)
+        pairs = [("d_lo", "lo"), ("d_hi", "hi")] + ([("d_alpha", "alpha")] if free else [])
+        for gkey, fkey in pairs:
+            ok, e = _close(out[gkey][b], fd[fkey], 2e-3)
+            assert ok, (gkey, b, e)
+            checked += int(np.count_nonzero(~np.isnan(fd[fkey])))
+    # a quarter of the coordinates at least is kink-free (a box side is 0.02-0.04
+    # wide, so h = 1e-3 flips some neuron's case for about half the box coordinates)
+    assert checked >= (n * (200 + 2 * 100) if free else n * 2 * 100) // 4

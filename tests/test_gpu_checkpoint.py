@@ -79,3 +79,26 @@ def test_checkpoint_errors(pkg):
         with pytest.raises(pkg.SlrError) as ei:
             other.resume(state)
         assert ei.value.code == -1
+
+
+def test_resume_runs_the_checkpoints_tile(pkg):
+    """The FP32 tile decides the products' summation order (small tiles split
+    their inputs over lanes), so a fresh context left to its own autotuner
+    resumes with the checkpoint's tile and reproduces the count exactly."""
+    p = gen.make("acas")
+    D, t = 14, 8
+    with pkg.Counter(0) as probe:
+        probe.set_problem(p)
+        tuned = tuple(probe.count(4)["tile"])
+    forced = (8, 256) if tuned != (8, 256) else (16, 256)
+    with pkg.Counter(0) as c:
+        c.set_problem(p)
+        c.set_options(tile_boxes=forced[0], tile_threads=forced[1])
+        whole = _strip(c.count(D))
+        state = c.checkpoint(D, t)
+    with pkg.Counter(0) as fresh:
+        fresh.set_problem(p)
+        got = fresh.resume(state)
+        assert tuple(got["tile"]) == forced
+        assert _strip(got) == whole
+        assert tuple(fresh.count(4)["tile"]) == tuned      # the context keeps its own tile afterwards

@@ -326,3 +326,33 @@ def test_replayed_level_loop_follows_changes(pkg):
     for got, ref in want:
         for k in keys:
             assert got[k] == ref[k], k
+
+
+def test_full_depth_acas_whole_leaf_set(pkg):
+    """Depth 20 on the ACAS-shaped net, the benchmark's count: every level's
+    statistics, the bracket and the whole sorted leaf set (about a million
+    leaves) equal the oracle's, run level by level on a pool of host processes."""
+    from oracle import pool
+    p = gen.acas_shaped(0)
+    D = p.depth
+    with _counter(pkg, p, record_leaves=1) as c:
+        got = c.count(D)
+        codes, depth, cls = c.leaves()
+    want = pool.count_levels(p, D, leaves=True)
+    assert want["complete"]
+    assert (got["unsafe_lo"], got["unsafe_hi"]) == (want["unsafe_lo"], want["unsafe_hi"])
+    for t, lv in enumerate(want["levels"]):
+        assert (got["level_boxes"][t], got["level_safe"][t], got["level_unsafe"][t], got["level_undecided"][t]) == \
+            (lv["boxes"], lv["safe"], lv["unsafe"], lv["undecided"]), t
+    assert got["tie_leaves"] == 0
+
+    def keyed(c_, t_, k_):
+        c_ = np.asarray(c_, np.int64)
+        t_ = np.asarray(t_, np.int64)
+        order = np.lexsort((c_, t_))
+        return t_[order], c_[order], np.asarray(k_, np.int64)[order]
+
+    gt, gc, gk = keyed(codes, depth, cls)
+    wt, wc, wk = keyed(want["leaf_codes"], want["leaf_depth"], want["leaf_cls"])
+    assert gt.shape == wt.shape
+    assert np.array_equal(gt, wt) and np.array_equal(gc, wc) and np.array_equal(gk, wk)

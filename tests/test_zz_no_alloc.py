@@ -1,8 +1,9 @@
 """slr_count_noalloc against slr_count (needs a GB300).
 
 slr_count_noalloc serves callers that cannot allocate GPU memory once set up
-(a framework's caching allocator holding the device memory, a real-time loop,
-stream capture): its scratch lives in a fixed array inside the library.  Its
+(a framework's caching allocator holding the device memory, or a real-time
+loop that must not stall on cudaMalloc/cudaFree): its scratch lives in a fixed
+array inside the library.  Its
 counts must equal those of the allocating entry point, on two calls in a row
 (the array keeps the previous call's contents, so each call must clear it).
 This file is collected last so that a failure here stops a -x run only after
@@ -58,3 +59,37 @@ def test_noalloc_rejects_a_frontier_beyond_its_scratch(pkg):
         assert ei.value.code == -5 and "262144" in str(ei.value)
         # the array is usable again right after the failed call
         assert c.count_noalloc(12)["unsafe_hi"] == c.count(12)["unsafe_hi"]
+
+
+@pytest.mark.parametrize("opt", [dict(alpha_steps=5), dict(precision=1), dict(recheck_cluster=1), dict(wide=1)])
+def test_noalloc_refuses_options_it_does_not_run(pkg, opt):
+    """Slope steps, the tensor-core contraction, the cluster re-check and the
+    wide path would make slr_count count differently: the entry refuses them
+    (SLR_EUNSUPPORTED) instead of returning the fixed-slope FP32 count."""
+    p = gen.make("acas")
+    with pkg.Counter(0) as c:
+        c.set_problem(p)
+        c.set_options(**opt)
+        c.count(6)
+        with pytest.raises(pkg.SlrError) as ei:
+            c.count_noalloc(6)
+        assert ei.value.code == -7
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(pkg):
+    """After the first call, repeated calls leave the device's free memory as
+    it was: the entry point allocates nothing."""
+    torch = pytest.importorskip("torch")
+    p = gen.make("acas")
+    with pkg.Counter(0) as c:
+        c.set_problem(p)
+        want = c.count(16)
+        c.count_noalloc(16)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info(0)
+        for _ in range(3):
+            got = c.count_noalloc(16)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(0)
+    assert free1 == free0, (free0, free1)
+    assert {k: got[k] for k in KEYS} == {k: want[k] for k in KEYS}
