@@ -374,6 +374,60 @@ int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out);
 int slr_count_checkpoint(slr_ctx *ctx, int D, int t, void *buf, size_t cap, size_t *used);
 int slr_count_resume(slr_ctx *ctx, const void *buf, size_t bytes, slr_result *out);
 
+/* Approximate counter CountingProVe_SLR (Sec. 2.3; Sec. 4, Table 1's
+ * "Approximations" block).  Each of `trials` independent trials starts from
+ * the context's box and makes up to `splits` balanced splits: it samples
+ * `samples` points uniformly in the current box (SplitMix64, Steele, Lea and
+ * Flood 2014, as a counter-based generator keyed by seed, trial, split, point
+ * and coordinate), evaluates the network in float64 at each one, and splits
+ * the widest side (ties to the lowest index) at the lower median of the
+ * sampled unsafe points' coordinates on that side (rounded to the nearest
+ * float32; the midpoint when no sample is unsafe), so that the sampled
+ * violations are shared evenly by the halves; a fair coin (one more draw)
+ * keeps one half.  A side too narrow to split ends the trial's splitting.
+ * The final leaf is counted exactly, as slr_count does with the context's
+ * options, to depth leaf_depth: [lo_l, hi_l] in units of 2^-leaf_depth of the
+ * leaf.  The trial's estimate of the violation rate is
+ *     X = 2^s lo_l 2^-leaf_depth vol(leaf) / vol(root)   (s: splits made).
+ * Since the coin picks each half with probability 1/2, E[X] is at most the
+ * violation rate VR; by Markov's inequality P(X >= 2^beta VR) <= 2^-beta, so
+ *     vr_lower = 2^-beta min_i X_i <= VR   with probability >= 1 - 2^(-beta trials)
+ * (the confidence reported).  The library computes this guarantee; the
+ * paper states it for CountingProVe without the derivation.  Volumes of
+ * zero-width root sides are left out of vol(.).  Needs network, box and
+ * property (SLR_ESTATE); SLR_EINVAL for options out of range; sharded
+ * contexts get SLR_EUNSUPPORTED.  leaf_lo, leaf_hi (nullable, trials x d
+ * float32) receive each trial's leaf box. */
+#define SLR_APPROX_MAX_TRIALS 64
+typedef struct {
+    int32_t trials;      /* 1..64; default 8 */
+    int32_t splits;      /* balanced splits per trial before the exact count, 0..62; default 10 */
+    int32_t samples;     /* points sampled per split, 1 .. 2^24 - 2; default 4096 */
+    int32_t leaf_depth;  /* depth of the exact count of the final leaf, 0..62; default 12 */
+    double beta;         /* tolerance > 0 of the lower bound; default 1 */
+    uint64_t seed;       /* generator seed; default 0 */
+} slr_approx_options;
+
+typedef struct {
+    double vr_lower;                                   /* 2^-beta min over trials of X_i */
+    double confidence;                                 /* 1 - 2^(-beta trials) */
+    double vr_mean;                                    /* mean of the X_i */
+    int32_t trials;
+    int32_t splits_done[SLR_APPROX_MAX_TRIALS];        /* s of each trial */
+    uint64_t leaf_unsafe_lo[SLR_APPROX_MAX_TRIALS];    /* exact count of the leaf, units 2^-leaf_depth */
+    uint64_t leaf_unsafe_hi[SLR_APPROX_MAX_TRIALS];
+    double leaf_volume[SLR_APPROX_MAX_TRIALS];         /* vol(leaf) / vol(root) */
+    double estimate[SLR_APPROX_MAX_TRIALS];            /* X_i */
+    double estimate_hi[SLR_APPROX_MAX_TRIALS];         /* X_i with hi_l in place of lo_l */
+    uint64_t boxes;                                    /* boxes bounded by the leaves' exact counts */
+    uint64_t samples_unsafe;                           /* sampled points found unsafe */
+    double device_ms;                                  /* device time of sampling and leaf counts */
+} slr_approx_result;
+
+void slr_default_approx_options(slr_approx_options *opt);
+int slr_count_approx(slr_ctx *ctx, const slr_approx_options *opt, slr_approx_result *out, float *leaf_lo,
+                     float *leaf_hi);
+
 /* Measurement aid (no paper counterpart): the FP32 fused multiply-add rate of
  * CUDA device `device` in TFLOP/s (2 FLOP per FMA), the roofline denominator
  * of the CUDA-core kernels.  Runs, on a stream of its own, a kernel in which

@@ -34,6 +34,7 @@ EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options"
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
            "slr_split_set", "slr_wait_selfcheck", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
            "slr_optimize_alpha", "slr_count_checkpoint", "slr_count_resume", "slr_measure_fp32_peak",
+           "slr_default_approx_options", "slr_count_approx",
            "slr_last_error")
 
 
@@ -85,6 +86,33 @@ class slr_result(ctypes.Structure):
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 
 
+APPROX_MAX_TRIALS = 64
+_AT = APPROX_MAX_TRIALS
+
+
+class slr_approx_options(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("splits", ctypes.c_int32), ("samples", ctypes.c_int32),
+                ("leaf_depth", ctypes.c_int32), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class slr_approx_result(ctypes.Structure):
+    _fields_ = [("vr_lower", ctypes.c_double), ("confidence", ctypes.c_double), ("vr_mean", ctypes.c_double),
+                ("trials", ctypes.c_int32), ("splits_done", ctypes.c_int32 * _AT),
+                ("leaf_unsafe_lo", ctypes.c_uint64 * _AT), ("leaf_unsafe_hi", ctypes.c_uint64 * _AT),
+                ("leaf_volume", ctypes.c_double * _AT), ("estimate", ctypes.c_double * _AT),
+                ("estimate_hi", ctypes.c_double * _AT), ("boxes", ctypes.c_uint64),
+                ("samples_unsafe", ctypes.c_uint64), ("device_ms", ctypes.c_double)]
+
+    def to_dict(self):
+        n = int(self.trials)
+        return dict(vr_lower=float(self.vr_lower), confidence=float(self.confidence), vr_mean=float(self.vr_mean),
+                    trials=n, splits_done=list(self.splits_done[:n]), leaf_unsafe_lo=list(self.leaf_unsafe_lo[:n]),
+                    leaf_unsafe_hi=list(self.leaf_unsafe_hi[:n]), leaf_volume=list(self.leaf_volume[:n]),
+                    estimate=list(self.estimate[:n]), estimate_hi=list(self.estimate_hi[:n]),
+                    boxes=int(self.boxes), samples_unsafe=int(self.samples_unsafe),
+                    device_ms=float(self.device_ms))
+
+
 class slr_problem(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("widths", ctypes.c_void_p), ("W", ctypes.c_void_p), ("b", ctypes.c_void_p),
                 ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("n_clauses", ctypes.c_int32),
@@ -130,6 +158,9 @@ def load_library(path: str = LIB_PATH):
         "slr_count_resume": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(slr_result)]),
         "slr_measure_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_double)]),
+        "slr_default_approx_options": (None, [ctypes.POINTER(slr_approx_options)]),
+        "slr_count_approx": (ctypes.c_int, [P, ctypes.POINTER(slr_approx_options), ctypes.POINTER(slr_approx_result),
+                                            P, P]),
         "slr_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -371,6 +402,24 @@ def slr_count_noalloc(ctx, D: int) -> dict:
     return res.to_dict()
 
 
+def slr_count_approx(ctx, d: int, **kw) -> dict:
+    """CountingProVe_SLR (see the header): the lower bound of the violation rate with its
+    confidence, per-trial splits, leaf counts, volumes and estimates, and each trial's leaf box."""
+    lib = load_library()
+    o = slr_approx_options()
+    lib.slr_default_approx_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    res = slr_approx_result()
+    n = max(1, int(o.trials))
+    llo = np.zeros((n, d), dtype=np.float32)
+    lhi = np.zeros((n, d), dtype=np.float32)
+    _check(lib, ctx, lib.slr_count_approx(ctx, ctypes.byref(o), ctypes.byref(res), _ptr(llo), _ptr(lhi)))
+    out = res.to_dict()
+    out["leaf_lo"], out["leaf_hi"] = llo, lhi
+    return out
+
+
 def slr_measure_fp32_peak(device: int = 0, iters: int = 1 << 19) -> dict:
     """FP32 FMA rate of the device in TFLOP/s, measured by the library's FFMA kernel."""
     lib = load_library()
@@ -492,6 +541,9 @@ class Counter:
 
     def count_batch(self, problems, depths=None):
         return slr_count_batch(self.ctx, problems, depths)
+
+    def count_approx(self, **kw) -> dict:
+        return slr_count_approx(self.ctx, self.widths[0], **kw)
 
     def count_noalloc(self, D: int) -> dict:
         return slr_count_noalloc(self.ctx, D)

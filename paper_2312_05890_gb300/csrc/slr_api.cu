@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "slrcount.h"
+#include "slr_approx.h"
 #include "slr_kernels.h"
 #include "slr_noalloc.h"
 
@@ -119,6 +120,8 @@ struct slr_ctx {
     void *wadj_buf = nullptr;             // the wide adjoint's chunk state
     size_t wadj_bytes = 0;
     int wadj_Bc = 0;
+    void *approx_buf = nullptr;           // approximate counter: box, sampled coordinates, count
+    size_t approx_bytes = 0;
     void *wide_buf = nullptr;             // chunk state
     size_t wide_buf_bytes = 0;
     std::vector<cudaEvent_t> gemm_ev;     // profile: a pair around each product launch
@@ -1191,6 +1194,7 @@ int slr_destroy(slr_ctx *ctx) {
     if (ctx->wide_helper) slr_destroy(ctx->wide_helper);
     cudaFree(ctx->split_buf);
     cudaFree(ctx->wadj_buf);
+    cudaFree(ctx->approx_buf);
     if (ctx->count_graph) cudaGraphExecDestroy(ctx->count_graph);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
@@ -1818,6 +1822,172 @@ int slr_count_resume(slr_ctx *ctx, const void *buf, size_t bytes, slr_result *ou
     ctx->grid32 = g0;
     ctx->smem32 = s0;
     return rc;
+}
+
+// ---- approximate counter (CountingProVe_SLR, Sec. 2.3; Table 1) ------------
+namespace {
+
+// The exact count of the box [lo, hi] with the context's network, property and
+// options; the context's own box is put back afterwards.
+int count_sub_box(slr_ctx *ctx, const std::vector<float> &lo, const std::vector<float> &hi, int D, slr_result *out) {
+    std::vector<float> lo0 = ctx->lo, hi0 = ctx->hi;
+    ctx->lo = lo;
+    ctx->hi = hi;
+    const int rc = count_levels(ctx, D, out, D, nullptr);
+    ctx->lo.swap(lo0);
+    ctx->hi.swap(hi0);
+    return rc;
+}
+
+}  // namespace
+
+void slr_default_approx_options(slr_approx_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->trials = 8;
+    o->splits = 10;
+    o->samples = 4096;
+    o->leaf_depth = 12;
+    o->beta = 1.0;
+    o->seed = 0;
+}
+
+int slr_count_approx(slr_ctx *ctx, const slr_approx_options *o, slr_approx_result *out, float *leaf_lo,
+                     float *leaf_hi) {
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (!o || !out) return fail(ctx, SLR_EINVAL, "null options or result");
+    if (o->trials < 1 || o->trials > SLR_APPROX_MAX_TRIALS)
+        return fail(ctx, SLR_EINVAL, "trials=%d out of range [1, %d]", o->trials, SLR_APPROX_MAX_TRIALS);
+    if (o->splits < 0 || o->splits > slr::kMaxDepth)
+        return fail(ctx, SLR_EINVAL, "splits=%d out of range [0, %d]", o->splits, slr::kMaxDepth);
+    if (o->samples < 1 || o->samples >= slr::kApproxCoinPoint)
+        return fail(ctx, SLR_EINVAL, "samples=%d out of range [1, %d)", o->samples, slr::kApproxCoinPoint);
+    if (o->leaf_depth < 0 || o->leaf_depth > slr::kMaxDepth)
+        return fail(ctx, SLR_EINVAL, "leaf_depth=%d out of range [0, %d]", o->leaf_depth, slr::kMaxDepth);
+    if (!(o->beta > 0.0) || !std::isfinite(o->beta)) return fail(ctx, SLR_EINVAL, "beta must be finite and > 0");
+    if (ctx->opt.shard_count > 1) return fail(ctx, SLR_EUNSUPPORTED, "the approximate counter does not shard");
+    CK(ctx, cudaSetDevice(ctx->device));
+    if ((rc = prepare_device(ctx))) return rc;
+    const int d = ctx->widths[0];
+    const size_t need = align_up(2 * (size_t)d * sizeof(double)) + align_up((size_t)o->samples * sizeof(double)) +
+                        align_up(sizeof(unsigned long long));
+    if (ctx->approx_bytes < need) {
+        cudaFree(ctx->approx_buf);
+        ctx->approx_buf = nullptr;
+        ctx->approx_bytes = 0;
+        CK(ctx, cudaMalloc(&ctx->approx_buf, need));
+        ctx->approx_bytes = need;
+    }
+    unsigned char *base = static_cast<unsigned char *>(ctx->approx_buf);
+    double *d_box = reinterpret_cast<double *>(base);
+    double *d_coord = reinterpret_cast<double *>(base + align_up(2 * (size_t)d * sizeof(double)));
+    unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(
+        base + align_up(2 * (size_t)d * sizeof(double)) + align_up((size_t)o->samples * sizeof(double)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, SLR_ECUDA, "cudaEventCreate");
+    }
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } guard{e0, e1};
+
+    std::memset(out, 0, sizeof *out);
+    out->trials = o->trials;
+    std::vector<double> box(2 * (size_t)d), coord;
+    double est_min = 0.0, est_sum = 0.0;
+    for (int t = 0; t < o->trials; ++t) {
+        std::vector<float> lo = ctx->lo, hi = ctx->hi;
+        int s = 0;
+        for (int j = 0; j < o->splits; ++j) {
+            // the widest side, ties to the lowest index
+            int dim = 0;
+            double wmax = -1.0;
+            for (int i = 0; i < d; ++i) {
+                const double w = (double)hi[i] - (double)lo[i];
+                if (w > wmax) {
+                    wmax = w;
+                    dim = i;
+                }
+            }
+            if (!(wmax > 0.0)) break;
+            for (int i = 0; i < d; ++i) {
+                box[i] = lo[i];
+                box[d + i] = hi[i];
+            }
+            CK(ctx, cudaMemcpyAsync(d_box, box.data(), box.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                    ctx->stream));
+            CK(ctx, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), ctx->stream));
+            CK(ctx, cudaEventRecord(e0, ctx->stream));
+            CK(ctx, slr::launch_approx_sample(ctx->nd, d_box, d_box + d, dim, o->seed, t, j, o->samples, d_coord,
+                                              d_cnt, ctx->sm_count, ctx->stream));
+            CK(ctx, cudaEventRecord(e1, ctx->stream));
+            unsigned long long n_uns = 0;
+            CK(ctx, cudaMemcpyAsync(&n_uns, d_cnt, sizeof n_uns, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            n_uns = std::min<unsigned long long>(n_uns, (unsigned long long)o->samples);
+            coord.resize((size_t)n_uns);
+            if (n_uns > 0) {
+                CK(ctx, cudaMemcpyAsync(coord.data(), d_coord, (size_t)n_uns * sizeof(double),
+                                        cudaMemcpyDeviceToHost, ctx->stream));
+                CK(ctx, cudaStreamSynchronize(ctx->stream));
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            out->device_ms += ms;
+            out->samples_unsafe += n_uns;
+            // split point: the lower median of the sampled violations on this
+            // side (the midpoint without any), to the nearest float32, strictly inside
+            double m64;
+            if (n_uns > 0) {
+                const size_t k = (size_t)(n_uns - 1) / 2;
+                std::nth_element(coord.begin(), coord.begin() + k, coord.end());
+                m64 = coord[k];
+            } else {
+                m64 = 0.5 * ((double)lo[dim] + (double)hi[dim]);
+            }
+            float m = (float)m64;
+            if (!(lo[dim] < m && m < hi[dim])) {
+                m = (float)(0.5 * ((double)lo[dim] + (double)hi[dim]));
+                if (!(lo[dim] < m && m < hi[dim])) break;
+            }
+            // a fair coin keeps one half
+            const unsigned long long c = slr::splitmix64(o->seed, slr::approx_draw_index(t, j, slr::kApproxCoinPoint, 0));
+            if ((c >> 63) == 0ull) hi[dim] = m;
+            else lo[dim] = m;
+            ++s;
+        }
+        slr_result r;
+        if ((rc = count_sub_box(ctx, lo, hi, o->leaf_depth, &r))) return rc;
+        double vol = 1.0;
+        for (int i = 0; i < d; ++i) {
+            const double wr = (double)ctx->hi[i] - (double)ctx->lo[i];
+            if (wr > 0.0) vol = vol * (((double)hi[i] - (double)lo[i]) / wr);
+        }
+        const double est = std::ldexp((double)r.unsafe_lo * vol, s - o->leaf_depth);
+        out->splits_done[t] = s;
+        out->leaf_unsafe_lo[t] = r.unsafe_lo;
+        out->leaf_unsafe_hi[t] = r.unsafe_hi;
+        out->leaf_volume[t] = vol;
+        out->estimate[t] = est;
+        out->estimate_hi[t] = std::ldexp((double)r.unsafe_hi * vol, s - o->leaf_depth);
+        out->boxes += r.boxes;
+        out->device_ms += r.device_ms;
+        est_min = t == 0 ? est : std::min(est_min, est);
+        est_sum += est;
+        if (leaf_lo) std::memcpy(leaf_lo + (size_t)t * d, lo.data(), (size_t)d * sizeof(float));
+        if (leaf_hi) std::memcpy(leaf_hi + (size_t)t * d, hi.data(), (size_t)d * sizeof(float));
+    }
+    out->vr_lower = est_min * std::pow(2.0, -o->beta);
+    out->confidence = 1.0 - std::pow(2.0, -o->beta * o->trials);
+    out->vr_mean = est_sum / o->trials;
+    return SLR_OK;
 }
 
 int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi, const float *alpha,
