@@ -169,10 +169,30 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt);
 /* The network N (Sec. 2.1): K affine layers (1 <= K <= 16), widths[0..K] with
  * widths[0] = d inputs and widths[K] outputs (each 1..1024).  W[k] points to a
  * row-major widths[k+1] x widths[k] float32 matrix and b[k] to widths[k+1]
- * float32 biases; ReLU follows every layer except the last.  All values must be
- * finite.  Copied to the device. */
+ * float32 biases; ReLU follows every layer except the last (slr_set_activations
+ * changes that).  All values must be finite.  Copied to the device. */
 int slr_load_network(slr_ctx *ctx, int K, const int32_t *widths,
                      const float *const *W, const float *const *b);
+
+/* Activation after each hidden layer.  Sec. 3 relaxes ReLU (Eq. 1) and names
+ * other activations only as an extension; the S-shaped ones here are relaxed
+ * by lines over the pre-activation's concrete interval [l, u]:
+ *   l >= 0 (concave side): upper = tangent at (l + u) / 2, lower = chord;
+ *   u <= 0 (convex side):  upper = chord, lower = tangent at (l + u) / 2;
+ *   l < 0 < u:             slope min(s'(l), s'(u)) through (u, s(u)) above
+ *                          and through (l, s(l)) below;
+ * with every intercept rounded outward by a bound of the error of CUDA's
+ * tanh/exp (their documented ulp accuracy), so the bounds stay sound.
+ * RELAX_INTERVAL keeps [s(l), s(u)].  Networks with S-shaped activations
+ * take no slopes (alpha_steps, slr_margin_backward, slr_optimize_alpha,
+ * supplied slopes) and no gradient split rule: SLR_EUNSUPPORTED. */
+enum { SLR_ACT_RELU = 0, SLR_ACT_TANH = 1, SLR_ACT_SIGMOID = 2 };
+
+/* Activations of the loaded network's K - 1 hidden layers: act[k] follows
+ * layer k (SLR_ACT_*); n must be K - 1.  slr_load_network resets every
+ * hidden layer to ReLU.  SLR_ESTATE before a network is loaded, SLR_EINVAL
+ * for a wrong n or an unknown value. */
+int slr_set_activations(slr_ctx *ctx, int n, const int32_t *act);
 
 /* The input box P (Sec. 2.1): d float32 endpoints with lo[i] <= hi[i], finite. */
 int slr_set_box(slr_ctx *ctx, int d, const float *lo, const float *hi);

@@ -70,12 +70,19 @@ def fold_property(net, prop):
     return Ws, bs
 
 
+def _acts(net):
+    """Activation of each hidden layer ('relu' unless the network says otherwise)."""
+    act = list(getattr(net, "act", None) or [])
+    return act if act else ["relu"] * (len(net.W) - 1)
+
+
 def _as64(net, prop):
     class _N:
         pass
     n = _N()
     n.W = [np.asarray(w, dtype=np.float64) for w in net.W]
     n.b = [np.asarray(x, dtype=np.float64) for x in net.b]
+    n.act = _acts(net)
     p = None
     if prop is not None:
         p = _N()
@@ -117,6 +124,7 @@ def interval_forward(net, a, b, prop=None, exact=False):
     without a property) and pre[k] = (l, u) are the pre-activation bounds of
     hidden layer k+1.
     """
+    acts = _acts(net)
     if not exact:
         net, prop = _as64(net, prop)
         a = np.asarray(a, dtype=np.float64)
@@ -130,7 +138,10 @@ def interval_forward(net, a, b, prop=None, exact=False):
         u2 = (Wp @ u[..., :, None])[..., 0] + (Wn @ l[..., :, None])[..., 0] + bb
         if k < len(Ws) - 1:
             pre.append((l2, u2))
-            l, u = np.where(l2 > 0, l2, l2 * 0), np.where(u2 > 0, u2, u2 * 0)
+            if acts[k] == "relu":
+                l, u = np.where(l2 > 0, l2, l2 * 0), np.where(u2 > 0, u2, u2 * 0)
+            else:                                  # monotone: the image of [l2, u2]
+                l, u = act_value(acts[k], l2), act_value(acts[k], u2)
         else:
             l, u = l2, u2
     return l, u, pre
@@ -196,6 +207,71 @@ def _relax(U, L, ll, ul, lu, uu, alpha, mode):
     return U2, L2
 
 
+# ---------------------------------------------------------------------------
+# S-shaped activations (tanh, logistic sigmoid): Sec. 3 names activations
+# other than ReLU only as an extension; the relaxation below is this build's
+# restatement for monotone functions that are convex below 0 and concave
+# above it, with a derivative largest at 0 and falling off on both sides.
+# ---------------------------------------------------------------------------
+
+def act_value(name, z):
+    if name == "tanh":
+        return np.tanh(z)
+    if name == "sigmoid":
+        return 1.0 / (1.0 + np.exp(-z))
+    return np.maximum(z, 0.0)
+
+
+def act_slope(name, z):
+    if name == "tanh":
+        t = np.tanh(z)
+        return 1.0 - t * t
+    s = 1.0 / (1.0 + np.exp(-z))
+    return s * (1.0 - s)
+
+
+def _relax_s(U, L, ll, uu, name):
+    """Relax one hidden layer of an S-shaped activation s over z in [l, u] = [ll, uu].
+
+      l >= 0 (s concave): upper = tangent at m = (l + u) / 2, lower = chord;
+      u <= 0 (s convex):  upper = chord, lower = tangent at m;
+      l < 0 < u:          both with slope lam = min(s'(l), s'(u)), the upper
+                          through (u, s(u)), the lower through (l, s(l));
+      l == u:             both the constant s(l).
+    A tangent lies below a convex function and above a concave one, a chord
+    the other way round; in the straddling case s' >= lam on [l, u] (s' is
+    largest at 0 and falls off on both sides), so the upper line minus s
+    decreases to 0 at u and the lower line minus s increases from 0 at l.
+    The new equations are U' = a_u U + b_u and L' = a_l L + b_l (a >= 0, and
+    l <= L, U <= u on the box).
+    """
+    l, u = ll, uu
+    sl, su = act_value(name, l), act_value(name, u)
+    width = u - l
+    pos = width > 0
+    chord = np.where(pos, (su - sl) / np.where(pos, width, 1.0), 0.0)
+    m = 0.5 * (l + u)
+    tm = act_slope(name, m)
+    lam = np.minimum(act_slope(name, l), act_slope(name, u))
+    concave = l >= 0
+    convex = (~concave) & (u <= 0)
+    # upper line a_u z + b_u
+    a_u = np.where(concave, tm, np.where(convex, chord, lam))
+    b_u = np.where(concave, act_value(name, m) - tm * m, np.where(convex, sl - chord * l, su - lam * u))
+    # lower line a_l z + b_l
+    a_l = np.where(concave, chord, np.where(convex, tm, lam))
+    b_l = np.where(concave, sl - chord * l, np.where(convex, act_value(name, m) - tm * m, sl - lam * l))
+    a_u = np.where(pos, a_u, 0.0)
+    a_l = np.where(pos, a_l, 0.0)
+    b_u = np.where(pos, b_u, sl)
+    b_l = np.where(pos, b_l, sl)
+    U2 = U * a_u[..., None]
+    U2[..., -1] = U2[..., -1] + b_u
+    L2 = L * a_l[..., None]
+    L2[..., -1] = L2[..., -1] + b_l
+    return U2, L2
+
+
 def slr_forward(net, a, b, prop=None, alpha=None, mode="neurify", exact=False):
     """SLR bounds of the property rows (or outputs) over each box.
 
@@ -210,6 +286,9 @@ def slr_forward(net, a, b, prop=None, alpha=None, mode="neurify", exact=False):
     U' = W+ U + W- L + b, L' = W+ L + W- U + b (W+ = max(W,0), W- = min(W,0)).
     The row bounds are lo = min L', hi = max U' over the box.
     """
+    acts = _acts(net)
+    if any(x != "relu" for x in acts) and (exact or alpha is not None):
+        raise ValueError("S-shaped activations: no exact rationals and no supplied slopes")
     if not exact:
         net, prop = _as64(net, prop)
         a = np.asarray(a, dtype=np.float64)
@@ -227,7 +306,11 @@ def slr_forward(net, a, b, prop=None, alpha=None, mode="neurify", exact=False):
         ll, ul = concretize(L, a, b)
         lu, uu = concretize(U, a, b)
         pre.append((ll, ul, lu, uu))
-        U, L = _relax(U, L, ll, ul, lu, uu, None if alpha is None else alpha[k - 1], mode)
+        name = acts[k - 1]
+        if name == "relu":
+            U, L = _relax(U, L, ll, ul, lu, uu, None if alpha is None else alpha[k - 1], mode)
+        else:
+            U, L = _relax_s(U, L, ll, uu, name)
         W, bb = Ws[k], bs[k]
         Wp, Wn = _pos(W), _neg(W)
         U2 = Wp @ U + Wn @ L
@@ -283,11 +366,12 @@ def forward_points(net, x, prop=None):
     h = np.asarray(x, dtype=np.float64)
     pre = []
     K = len(net.W)
+    acts = _acts(net)
     for k in range(K):
         z = h @ np.asarray(net.W[k], dtype=np.float64).T + np.asarray(net.b[k], dtype=np.float64)
         if k < K - 1:
             pre.append(z)
-            h = np.maximum(z, 0.0)
+            h = act_value(acts[k], z)
         else:
             h = z
     if prop is not None:

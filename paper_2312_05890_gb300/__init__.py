@@ -31,6 +31,7 @@ MAX_LEVELS = 63
 
 # Names the header declares (checked by the CPU test that loads the library).
 EXPORTS = ("slr_create", "slr_destroy", "slr_default_options", "slr_set_options", "slr_load_network",
+           "slr_set_activations",
            "slr_set_box", "slr_set_property", "slr_count", "slr_bounds", "slr_leaves", "slr_schedule",
            "slr_split_set", "slr_wait_selfcheck", "slr_count_noalloc", "slr_count_batch", "slr_alpha_width", "slr_margin_backward",
            "slr_optimize_alpha", "slr_count_checkpoint", "slr_count_resume", "slr_measure_fp32_peak",
@@ -140,6 +141,7 @@ def load_library(path: str = LIB_PATH):
         "slr_set_options": (ctypes.c_int, [P, ctypes.POINTER(slr_options)]),
         "slr_load_network": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
         "slr_set_box": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+        "slr_set_activations": (ctypes.c_int, [P, ctypes.c_int, P]),
         "slr_set_property": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, P, P, P]),
         "slr_count": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(slr_result)]),
         "slr_bounds": (ctypes.c_int, [P, i64, P, P, P, P, P, P, P, ctypes.c_int]),
@@ -217,6 +219,16 @@ def slr_load_network(ctx, W, b):
     wp = (ctypes.c_void_p * K)(*[w.ctypes.data for w in Ws])
     bp = (ctypes.c_void_p * K)(*[x.ctypes.data for x in bs])
     _check(lib, ctx, lib.slr_load_network(ctx, K, _ptr(widths), wp, bp))
+
+
+ACTIVATIONS = {"relu": 0, "tanh": 1, "sigmoid": 2}
+
+
+def slr_set_activations(ctx, act):
+    """Activation of each hidden layer ('relu', 'tanh', 'sigmoid' or the SLR_ACT_* numbers)."""
+    lib = load_library()
+    a = np.ascontiguousarray([ACTIVATIONS.get(x, x) for x in act], dtype=np.int32)
+    _check(lib, ctx, lib.slr_set_activations(ctx, int(a.shape[0]), _ptr(a) if a.size else None))
 
 
 def slr_set_box(ctx, lo, hi):
@@ -526,6 +538,9 @@ class Counter:
     def set_problem(self, problem):
         """Load a workloads.Problem (network, box and property)."""
         self.load_network(problem.net.W, problem.net.b)
+        act = list(getattr(problem.net, "act", None) or [])
+        if act:
+            slr_set_activations(self.ctx, act)
         self.set_box(problem.lo, problem.hi)
         p = problem.prop
         self.set_property(p.rows_per_clause, p.C, p.e, p.strict)

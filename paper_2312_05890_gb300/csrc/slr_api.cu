@@ -70,6 +70,7 @@ struct slr_ctx {
     std::vector<int> rpc;
     std::vector<float> C, e;
     std::vector<uint8_t> strict;
+    std::vector<int> act;                 // activation after each hidden layer (empty: ReLU)
     bool has_net = false, has_box = false, has_prop = false;
 
     bool dev_dirty = true;
@@ -297,6 +298,7 @@ void layout_params(const Src *ctx, const HostLayers<Real> &L, unsigned char *dev
     }
     for (int r = 0; r < p.R; ++r) p.strict[r] = ctx->strict[r];
     p.relax_mode = ctx->opt.relax_mode;
+    for (int k = 0; k + 1 < K; ++k) p.act[k] = (uint8_t)(k < (int)ctx->act.size() ? ctx->act[k] : slr::kActRelu);
 }
 
 struct TileChoice {
@@ -1275,6 +1277,7 @@ int slr_load_network(slr_ctx *ctx, int K, const int32_t *widths, const float *co
     ctx->widths.assign(widths, widths + K + 1);
     ctx->W.swap(Wv);
     ctx->b.swap(bv);
+    ctx->act.clear();
     ctx->has_net = true;
     ctx->dev_dirty = true;
     ctx->leaves_valid = false;
@@ -1292,6 +1295,20 @@ int slr_set_box(slr_ctx *ctx, int d, const float *lo, const float *hi) {
     ctx->lo.assign(lo, lo + d);
     ctx->hi.assign(hi, hi + d);
     ctx->has_box = true;
+    ctx->leaves_valid = false;
+    return SLR_OK;
+}
+
+int slr_set_activations(slr_ctx *ctx, int n, const int32_t *act) {
+    if (!ctx) return fail(nullptr, SLR_EINVAL, "null context");
+    if (!ctx->has_net) return fail(ctx, SLR_ESTATE, "load the network before its activations");
+    if (n != ctx->K - 1 || (n > 0 && !act))
+        return fail(ctx, SLR_EINVAL, "%d activations given for %d hidden layers", n, ctx->K - 1);
+    for (int k = 0; k < n; ++k)
+        if (act[k] != SLR_ACT_RELU && act[k] != SLR_ACT_TANH && act[k] != SLR_ACT_SIGMOID)
+            return fail(ctx, SLR_EINVAL, "activation %d of hidden layer %d unknown", act[k], k);
+    ctx->act.assign(act, act + n);
+    ctx->dev_dirty = true;
     ctx->leaves_valid = false;
     return SLR_OK;
 }
@@ -1727,6 +1744,7 @@ uint64_t problem_fingerprint(const slr_ctx *ctx) {
     h = fnv1a(h, ctx->C.data(), ctx->C.size() * sizeof(float));
     h = fnv1a(h, ctx->e.data(), ctx->e.size() * sizeof(float));
     h = fnv1a(h, ctx->strict.data(), ctx->strict.size());
+    h = fnv1a(h, ctx->act.data(), ctx->act.size() * sizeof(int));
     const int32_t o[5] = {ctx->opt.precision, ctx->opt.relax_mode, ctx->opt.fp64_recheck, ctx->wide ? 1 : 0,
                           ctx->opt.recheck_cluster};
     return fnv1a(h, o, sizeof o);
@@ -1998,6 +2016,9 @@ int slr_bounds(slr_ctx *ctx, int64_t n, const float *box_lo, const float *box_hi
     if ((row_lo == nullptr) != (row_hi == nullptr)) return fail(ctx, SLR_EINVAL, "row_lo and row_hi go together");
     if (alpha && ctx->opt.relax_mode != SLR_RELAX_NEURIFY)
         return fail(ctx, SLR_EUNSUPPORTED, "supplied slopes need relax mode NEURIFY");
+    if (alpha)
+        for (int a : ctx->act)
+            if (a != SLR_ACT_RELU) return fail(ctx, SLR_EUNSUPPORTED, "supplied slopes need a ReLU network");
     if (n == 0) return SLR_OK;
     CK(ctx, cudaSetDevice(ctx->device));
     int rc = prepare_device(ctx);
@@ -2159,6 +2180,7 @@ struct ProblemHost {
     std::vector<int> rpc;
     std::vector<float> C, e;
     std::vector<uint8_t> strict;
+    std::vector<int> act;                 // empty: ReLU after every hidden layer
     int depth = 0;
 };
 
@@ -2738,6 +2760,9 @@ void adam_step(slr::AdjArgs &a, int t, float lr) {
 int check_adjoint(slr_ctx *ctx) {
     if (ctx->opt.relax_mode != SLR_RELAX_NEURIFY)
         return fail(ctx, SLR_EUNSUPPORTED, "the adjoint needs relax mode NEURIFY");
+    for (int a : ctx->act)
+        if (a != SLR_ACT_RELU)
+            return fail(ctx, SLR_EUNSUPPORTED, "slopes, the adjoint and the gradient split rule need ReLU networks");
     if (ctx->adj_grid <= 0)
         return fail(ctx, SLR_EUNSUPPORTED, "network too large for the adjoint kernel (%zu bytes of shared memory)",
                     ctx->adj_smem);

@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(kSampleThreads) approx_sample_kernel(const Net
         __syncwarp();
         const double xd = h0[dim];
         // layers: 0 row-major (n[1] x d), k >= 1 transposed (n[k] x n[k+1]); the
-        // last one carries the property rows folded in; ReLU after the others
+        // last one carries the property rows folded in; the network's
+        // activation after the others
         double *src = h0, *dst = h1;
         for (int layer = 0; layer < K; ++layer) {
             const int n_in = net.n[layer], n_out = net.n[layer + 1];
@@ -52,7 +53,11 @@ __global__ void __launch_bounds__(kSampleThreads) approx_sample_kernel(const Net
                     const double *w = net.Wt[layer] + j;
                     for (int i = 0; i < n_in; ++i) acc = __fma_rn(w[(size_t)i * n_out], src[i], acc);
                 }
-                dst[j] = (layer + 1 < K && acc < 0.0) ? 0.0 : acc;
+                if (layer + 1 < K) {
+                    const int a = net.act[layer];
+                    acc = a == kActTanh ? tanh(acc) : (a == kActSigmoid ? 1.0 / (1.0 + exp(-acc)) : (acc < 0.0 ? 0.0 : acc));
+                }
+                dst[j] = acc;
             }
             __syncwarp();
             double *t = src;

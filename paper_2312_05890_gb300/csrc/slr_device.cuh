@@ -44,6 +44,8 @@ constexpr int kRecheckCluster = 4;
 
 enum : uint8_t { kSafe = 0, kUnsafe = 1, kUndecided = 2 };
 enum : int { kRelaxNeurify = 0, kRelaxPaperLiteral = 1, kRelaxInterval = 2 };
+// Activation after a hidden layer.
+enum : int { kActRelu = 0, kActTanh = 1, kActSigmoid = 2 };
 
 enum : uint32_t {
     kStatusOverflow = 1u,      // a level exceeded the frontier capacity
@@ -84,6 +86,7 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float add_up(float a, float b) { return __fadd_ru(a, b); }
     static __device__ __forceinline__ float add_dn(float a, float b) { return __fadd_rd(a, b); }
     static __device__ __forceinline__ float mul_up(float a, float b) { return __fmul_ru(a, b); }
+    static __device__ __forceinline__ float mul_dn(float a, float b) { return __fmul_rd(a, b); }
     static __device__ __forceinline__ float div_up(float a, float b) { return __fdiv_ru(a, b); }
     static __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
     static __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -99,6 +102,7 @@ template <> struct Arith<double> {
     static __device__ __forceinline__ double add_up(double a, double b) { return __dadd_ru(a, b); }
     static __device__ __forceinline__ double add_dn(double a, double b) { return __dadd_rd(a, b); }
     static __device__ __forceinline__ double mul_up(double a, double b) { return __dmul_ru(a, b); }
+    static __device__ __forceinline__ double mul_dn(double a, double b) { return __dmul_rd(a, b); }
     static __device__ __forceinline__ double div_up(double a, double b) { return __ddiv_ru(a, b); }
     static __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -128,6 +132,7 @@ struct NetParams {
     int clause_end[kMaxRows];    // exclusive end row of each clause
     uint8_t strict[kMaxRows];
     int relax_mode;
+    uint8_t act[kMaxLayers];     // activation after layer k (k < K - 1): kAct*
 };
 
 // Where the boxes of one evaluation come from.

@@ -272,6 +272,35 @@ struct RelaxPlan {
     Real nh, nl, rd, E, N;
 };
 
+// S-shaped activations (tanh, logistic sigmoid): the value and derivative at
+// z with bounds of their errors.  CUDA documents tanhf and expf as accurate
+// to 2 ulp and tanh and exp to 1 ulp; with the roundings added here the
+// value's error stays below 16 units of 2^-24 (float) or 2^-53 (double)
+// relative, and the derivative's (1 - t^2, s (1 - s), both in [0, 1]) below
+// 16 such units absolutely: those are the margins returned.
+template <typename Real> __device__ __forceinline__ Real act_tanh(Real z);
+template <> __device__ __forceinline__ float act_tanh<float>(float z) { return tanhf(z); }
+template <> __device__ __forceinline__ double act_tanh<double>(double z) { return tanh(z); }
+template <typename Real> __device__ __forceinline__ Real act_exp(Real z);
+template <> __device__ __forceinline__ float act_exp<float>(float z) { return expf(z); }
+template <> __device__ __forceinline__ double act_exp<double>(double z) { return exp(z); }
+
+template <typename Real>
+__device__ __forceinline__ void act_eval(int act, Real z, Real &v, Real &ev, Real &dv, Real &ed) {
+    using A = Arith<Real>;
+    if (act == kActTanh) {
+        v = act_tanh<Real>(z);
+        dv = A::fma_rn(-v, v, (Real)1);
+    } else {
+        const Real e = act_exp<Real>(-z);
+        v = A::div_rn((Real)1, (Real)1 + e);
+        dv = A::mul_rn(v, (Real)1 - v);
+    }
+    dv = dv > (Real)0 ? dv : (Real)0;
+    ev = A::add_up(A::mul_up(A::abs(v), (Real)8 * A::ulp2), A::tiny);
+    ed = (Real)8 * A::ulp2;
+}
+
 template <typename Real, int T, int NT, int KI = 2>
 struct EvalTile {
     using A = Arith<Real>;
@@ -481,10 +510,100 @@ struct EvalTile {
     // chi, clo: the row's constant (float-float); rd: its radius constant; E: its
     // error bound.  a_ptr: the supplied lower slope of the
     // row, or null for u_l / (u_l - l_l).
+    // ---- relaxation of an S-shaped activation (tanh, sigmoid) of one hidden row ----
+    // The true pre-activation z lies in [L - E, U + E] within [zl, zu] = [ll - E,
+    // uu + E].  Lines a z + b bounding s on [zl, zu] (a >= 0): on the concave
+    // side (zl >= 0) the tangent at the midpoint above and the chord below, on
+    // the convex side (zu <= 0) the other way round, and across 0 the slope
+    // lam = min(s'(zl), s'(zu)) through (zu, s(zu)) above and (zl, s(zl)) below
+    // (s' is largest at 0, so s' >= lam on [zl, zu]).  Every intercept is
+    // rounded outward with the margins of act_eval: a chord keeps the line
+    // on the right side of both end values (enough for a convex or concave
+    // s), a tangent loses at most ed |z - m| to its inexact slope.  Then
+    // U' = a_u U + b_u and L' = a_l L + b_l bound s(z) up to a E <= E.
+    static __device__ __forceinline__ RelaxPlan<Real> plan_sshape(const RowBounds<Real> &bd, int d, int act,
+                                                                  int relax_mode, Real chi, Real clo, Real rd,
+                                                                  Real E) {
+        RelaxPlan<Real> pl;
+        const Real zl = A::add_dn(bd.ll, -E), zu = A::add_up(bd.uu, E);
+        Real vl, evl, dl, edl, vu, evu, du, edu;
+        act_eval<Real>(act, zl, vl, evl, dl, edl);
+        act_eval<Real>(act, zu, vu, evu, du, edu);
+        const Real width = A::add_up(zu, -zl);
+        const Real tiny_w = A::mul_up(A::abs(zl) + A::abs(zu), (Real)64 * A::ulp2) + A::tiny;
+        if (relax_mode == kRelaxInterval || !(width > tiny_w)) {
+            // the constant interval [s(zl), s(zu)] (s is increasing)
+            const Real a = A::add_dn(vl, -evl), b = A::add_up(vu, evu);
+            pl.kind = 1;
+            pl.pp = 0;
+            pl.qq = 0;
+            two_sum<Real>(a, b, pl.nh, pl.nl);
+            pl.nh *= (Real)0.5;
+            pl.nl *= (Real)0.5;
+            pl.rd = A::mul_up(A::add_up(b, -a), (Real)0.5);
+            pl.N = pl.rd;
+            pl.E = (Real)4 * A::tiny;
+            return pl;
+        }
+        const Real lip = act == kActTanh ? (Real)1 : (Real)0.25;
+        Real a_u, b_u, a_l, b_l;
+        if (zl >= (Real)0 || zu <= (Real)0) {
+            Real sc = A::div_rn(vu - vl, zu - zl);
+            sc = sc < (Real)0 ? (Real)0 : (sc > lip ? lip : sc);
+            const Real m = (zl + zu) * (Real)0.5;
+            Real vm, evm, dm, edm;
+            act_eval<Real>(act, m, vm, evm, dm, edm);
+            const Real slack = A::mul_up(edm, width);   // |z - m| <= width
+            if (zl >= (Real)0) {
+                // concave: tangent above, chord below
+                a_u = dm;
+                b_u = A::add_up(A::add_up(A::add_up(vm, evm), -A::mul_dn(dm, m)), slack);
+                a_l = sc;
+                const Real b1 = A::add_dn(A::add_dn(vl, -evl), -A::mul_up(sc, zl));
+                const Real b2 = A::add_dn(A::add_dn(vu, -evu), -A::mul_up(sc, zu));
+                b_l = b1 < b2 ? b1 : b2;
+            } else {
+                // convex: chord above, tangent below
+                a_u = sc;
+                const Real b1 = A::add_up(A::add_up(vl, evl), -A::mul_dn(sc, zl));
+                const Real b2 = A::add_up(A::add_up(vu, evu), -A::mul_dn(sc, zu));
+                b_u = b1 > b2 ? b1 : b2;
+                a_l = dm;
+                b_l = A::add_dn(A::add_dn(A::add_dn(vm, -evm), -A::mul_up(dm, m)), -slack);
+            }
+        } else {
+            const Real m1 = A::add_dn(dl, -edl), m2 = A::add_dn(du, -edu);
+            Real lam = m1 < m2 ? m1 : m2;
+            lam = lam > (Real)0 ? lam : (Real)0;
+            a_u = lam;
+            a_l = lam;
+            b_u = A::add_up(A::add_up(vu, evu), -A::mul_dn(lam, zu));
+            b_l = A::add_dn(A::add_dn(vl, -evl), -A::mul_up(lam, zl));
+        }
+        // (C, R) <- ((U' + L') / 2, (U' - L') / 2)
+        pl.kind = 2;
+        pl.pp = (a_u + a_l) * (Real)0.5;
+        pl.qq = (a_u - a_l) * (Real)0.5;
+        const Real hc = (b_u + b_l) * (Real)0.5, hr = (b_u - b_l) * (Real)0.5;
+        Real ph, pe;
+        two_prod<Real>(pl.pp, chi, ph, pe);
+        const Real rest = pe + A::fma_rn(pl.pp, clo, A::fma_rn(pl.qq, rd, hc));
+        two_sum<Real>(ph, rest, pl.nh, pl.nl);
+        pl.rd = A::fma_rn(pl.qq, chi, A::fma_rn(pl.qq, clo, A::fma_rn(pl.pp, rd, hr)));
+        const Real a_max = a_u > a_l ? a_u : a_l;
+        const Real tot = A::add_up(A::add_up(bd.NC, bd.NR), A::add_up(A::abs(chi), A::abs(clo)));
+        const Real mag = A::add_up(A::mul_up(a_max, tot), A::add_up(A::abs(b_u), A::abs(b_l)));
+        const Real err = A::add_up(A::mul_up((Real)8 * A::ulp2, mag), (Real)(2 * d + 8) * A::tiny);
+        pl.E = A::add_up(A::mul_up(a_max, E), err);
+        pl.N = A::mul_up(A::add_up(mag, A::add_up(err, err)), (Real)1 + (Real)4 * A::ulp2);
+        return pl;
+    }
+
     static __device__ __forceinline__ RelaxPlan<Real> plan_row(const RowBounds<Real> &bd, int d, int relax_mode,
                                                                Real chi, Real clo, Real rd, Real E,
-                                                               const float *a_ptr) {
+                                                               const float *a_ptr, int act = kActRelu) {
         RelaxPlan<Real> pl;
+        if (act != kActRelu) return plan_sshape(bd, d, act, relax_mode, chi, clo, rd, E);
         if (relax_mode == kRelaxInterval) {
             // Moore intervals: relu is monotone and 1-Lipschitz, so the row becomes
             // the constant interval [relu(ll), relu(uu)] (centre exact as a
@@ -590,11 +709,11 @@ struct EvalTile {
     // ---- bounds and ReLU relaxation of one hidden row, in place ----------------------
     template <class Row>
     static __device__ __forceinline__ void relax_row(const Row &R, int d, int relax_mode, Real chi, Real clo, Real E,
-                                                     const float *a_ptr) {
+                                                     const float *a_ptr, int act = kActRelu) {
         const int cr = cR(d);
         RowBounds<Real> bd;
         bd.compute(R, d, chi, clo);
-        const RelaxPlan<Real> pl = plan_row(bd, d, relax_mode, chi, clo, R(cr + d), E, a_ptr);
+        const RelaxPlan<Real> pl = plan_row(bd, d, relax_mode, chi, clo, R(cr + d), E, a_ptr, act);
         if (pl.kind != 0) {
             for (int j = 0; j < d; ++j) {
                 Real c = R(j), r = R(cr + j);
@@ -636,7 +755,7 @@ struct EvalTile {
                 const int64_t pos = base + b < n ? base + b : base;
                 a_ptr = alpha + pos * alpha_ld + alpha_off + p;
             }
-            relax_row(R, d, net.relax_mode, chi, clo, E, a_ptr);
+            relax_row(R, d, net.relax_mode, chi, clo, E, a_ptr, net.act[layer - 1]);
             lay.finish_row(p, b);
         }
     }

@@ -178,7 +178,7 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
         if (net.K > 1) {
             t.finish(chi, clo, 0.f);
             const float *a_ptr = alpha != nullptr ? alpha + (base + b) * alpha_ld + p : nullptr;
-            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, E, a_ptr);
+            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, 0.f, E, a_ptr, net.act[0]);
         }
         plan[lane] = pl;
     }
@@ -304,7 +304,7 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
             for (int j = 1; j < layer; ++j) off += net.n[j];
             a_ptr = alpha + (base + b) * alpha_ld + off + p;
         }
-        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, a_ptr);
+        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, a_ptr, net.act[layer - 1]);
     }
     __syncthreads();
     if (live) {

@@ -24,12 +24,18 @@ import numpy as np
 
 @dataclass
 class Network:
-    """K affine layers; ReLU after every layer but the last.
+    """K affine layers; an activation after every layer but the last.
 
     ``W[k]`` has shape (widths[k+1], widths[k]); ``b[k]`` has widths[k+1].
+    ``act[k]`` names the activation after layer k ('relu', 'tanh' or
+    'sigmoid'); an empty list means ReLU everywhere.
     """
     W: list
     b: list
+    act: list = field(default_factory=list)
+
+    def activation(self, k):
+        return self.act[k] if self.act else "relu"
 
     @property
     def widths(self):
@@ -99,12 +105,20 @@ def _unit(n, i, scale=1.0):
 # Seed selection (plain forward pass; not the method)
 # ---------------------------------------------------------------------------
 
+def _activate(name, h):
+    if name == "tanh":
+        return np.tanh(h)
+    if name == "sigmoid":
+        return 1.0 / (1.0 + np.exp(-h))
+    return np.maximum(h, 0.0)
+
+
 def _forward(net, x):
     h = x.astype(np.float32)
     for k in range(net.K):
         h = h @ net.W[k].T + net.b[k]
         if k < net.K - 1:
-            h = np.maximum(h, 0.0)
+            h = _activate(net.activation(k), h)
     return h
 
 
@@ -218,6 +232,54 @@ def mnist_shaped(seed: int = 0) -> Problem:
     raise RuntimeError("no seed puts class 0 on top")
 
 
+def _acas_tanh_raw(seed):
+    p = _acas_raw(seed)
+    p.net.act = ["tanh"] * (p.net.K - 1)
+    p.name = "acas_tanh_5-50x6-5"
+    return p
+
+
+def _nav_sigmoid_raw(seed):
+    p = _nav_raw(seed)
+    p.net.act = ["sigmoid"] * (p.net.K - 1)
+    p.name = "nav_sigmoid_22-64-64-3"
+    return p
+
+
+def _tiny_act_raw(act):
+    def raw(seed):
+        p = _tiny_raw(seed)
+        p.net.act = [act] * (p.net.K - 1)
+        p.name = f"tiny_{act}_2-8-8-1"
+        return p
+    return raw
+
+
+@functools.lru_cache(maxsize=16)
+def tiny_tanh(seed: int = 0) -> Problem:
+    """The tiny workload with tanh after both hidden layers; VR in [5%, 95%]."""
+    return _first_in_window(_tiny_act_raw("tanh"), seed, (0.05, 0.95))
+
+
+@functools.lru_cache(maxsize=16)
+def tiny_sigmoid(seed: int = 0) -> Problem:
+    """The tiny workload with the logistic sigmoid after both hidden layers; VR in [5%, 95%]."""
+    return _first_in_window(_tiny_act_raw("sigmoid"), seed, (0.05, 0.95))
+
+
+@functools.lru_cache(maxsize=16)
+def acas_tanh(seed: int = 0) -> Problem:
+    """The ACAS-shaped workload with tanh after every hidden layer (Sec. 3 names other
+    activations as an extension of the ReLU relaxation); VR in [0.5%, 50%]."""
+    return _first_in_window(_acas_tanh_raw, seed, (0.005, 0.5))
+
+
+@functools.lru_cache(maxsize=16)
+def nav_sigmoid(seed: int = 0) -> Problem:
+    """The nav-shaped workload with the logistic sigmoid after every hidden layer; VR in [5%, 50%]."""
+    return _first_in_window(_nav_sigmoid_raw, seed, (0.05, 0.5))
+
+
 def linear_2d(seed: int = 0, depth: int = 12) -> Problem:
     """A single affine layer y = w.x + c on [-1,1]^2, unsafe y < 0 (closed-form test case)."""
     rng = np.random.default_rng(seed)
@@ -316,6 +378,10 @@ CONFIGS = {
     "nav": nav_shaped,
     "mnist": mnist_shaped,
     "rare": rare_violation,
+    "acas_tanh": acas_tanh,
+    "tiny_tanh": tiny_tanh,
+    "tiny_sigmoid": tiny_sigmoid,
+    "nav_sigmoid": nav_sigmoid,
 }
 
 
