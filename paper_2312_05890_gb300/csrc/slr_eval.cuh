@@ -511,29 +511,33 @@ struct EvalTile {
     // error bound.  a_ptr: the supplied lower slope of the
     // row, or null for u_l / (u_l - l_l).
     // ---- relaxation of an S-shaped activation (tanh, sigmoid) of one hidden row ----
-    // The true pre-activation z lies in [L - E, U + E] within [zl, zu] = [ll - E,
-    // uu + E].  Lines a z + b bounding s on [zl, zu] (a >= 0): on the concave
-    // side (zl >= 0) the tangent at the midpoint above and the chord below, on
-    // the convex side (zu <= 0) the other way round, and across 0 the slope
-    // lam = min(s'(zl), s'(zu)) through (zu, s(zu)) above and (zl, s(zl)) below
-    // (s' is largest at 0, so s' >= lam on [zl, zu]).  Every intercept is
-    // rounded outward with the margins of act_eval: a chord keeps the line
-    // on the right side of both end values (enough for a convex or concave
-    // s), a tangent loses at most ed |z - m| to its inexact slope.  Then
-    // U' = a_u U + b_u and L' = a_l L + b_l bound s(z) up to a E <= E.
+    // Lines a z + b bounding s on [zl, zu] = [ll, uu], the concrete bounds of
+    // the stored equations (a >= 0): on the concave side (zl >= 0) the tangent
+    // at the midpoint above and the chord below, on the convex side (zu <= 0)
+    // the other way round, and across 0 the slope lam = min(s'(zl), s'(zu))
+    // through (zu, s(zu)) above and (zl, s(zl)) below (s' is largest at 0, so
+    // s' >= lam on [zl, zu]).  The stored equations take the nominal lines (the
+    // intercepts rounded to nearest, as plain SLR computes them); the same
+    // slopes with intercepts rounded outward by the margins of act_eval are
+    // sound (a chord kept on the right side of both end values suffices for a
+    // convex or concave s; a tangent loses at most ed |z - m| to its inexact
+    // slope), and the gap between the two intercepts, mu, joins E.  The true
+    // pre-activation z lies in [L - E, U + E] and may leave [zl, zu] by E; there
+    // s moves by at most its Lipschitz constant q (1 for tanh, 1/4 for the
+    // sigmoid) times E, so U' = a_u U + b_u and L' = a_l L + b_l bound s(z) up
+    // to max(q, a) E + mu (plus the rounding of the new row).
     static __device__ __forceinline__ RelaxPlan<Real> plan_sshape(const RowBounds<Real> &bd, int d, int act,
                                                                   int relax_mode, Real chi, Real clo, Real rd,
                                                                   Real E) {
         RelaxPlan<Real> pl;
-        const Real zl = A::add_dn(bd.ll, -E), zu = A::add_up(bd.uu, E);
+        const Real lip = act == kActTanh ? (Real)1 : (Real)0.25;
+        const Real zl = bd.ll, zu = bd.uu;
         Real vl, evl, dl, edl, vu, evu, du, edu;
         act_eval<Real>(act, zl, vl, evl, dl, edl);
         act_eval<Real>(act, zu, vu, evu, du, edu);
-        const Real width = A::add_up(zu, -zl);
-        const Real tiny_w = A::mul_up(A::abs(zl) + A::abs(zu), (Real)64 * A::ulp2) + A::tiny;
-        if (relax_mode == kRelaxInterval || !(width > tiny_w)) {
+        if (relax_mode == kRelaxInterval || !(zu > zl)) {
             // the constant interval [s(zl), s(zu)] (s is increasing)
-            const Real a = A::add_dn(vl, -evl), b = A::add_up(vu, evu);
+            const Real a = vl < vu ? vl : vu, b = vl < vu ? vu : vl;
             pl.kind = 1;
             pl.pp = 0;
             pl.qq = 0;
@@ -542,11 +546,12 @@ struct EvalTile {
             pl.nl *= (Real)0.5;
             pl.rd = A::mul_up(A::add_up(b, -a), (Real)0.5);
             pl.N = pl.rd;
-            pl.E = (Real)4 * A::tiny;
+            const Real ev = evl > evu ? evl : evu;
+            pl.E = A::add_up(A::add_up(A::mul_up(lip, E), ev), (Real)4 * A::tiny);
             return pl;
         }
-        const Real lip = act == kActTanh ? (Real)1 : (Real)0.25;
-        Real a_u, b_u, a_l, b_l;
+        const Real width = A::add_up(zu, -zl);
+        Real a_u, b_u, a_l, b_l, bu_out, bl_out;
         if (zl >= (Real)0 || zu <= (Real)0) {
             Real sc = A::div_rn(vu - vl, zu - zl);
             sc = sc < (Real)0 ? (Real)0 : (sc > lip ? lip : sc);
@@ -554,31 +559,58 @@ struct EvalTile {
             Real vm, evm, dm, edm;
             act_eval<Real>(act, m, vm, evm, dm, edm);
             const Real slack = A::mul_up(edm, width);   // |z - m| <= width
+            const Real b_tan = A::fma_rn(-dm, m, vm);
+            const Real b_chord = A::fma_rn(-sc, zl, vl);
             if (zl >= (Real)0) {
                 // concave: tangent above, chord below
                 a_u = dm;
-                b_u = A::add_up(A::add_up(A::add_up(vm, evm), -A::mul_dn(dm, m)), slack);
+                b_u = b_tan;
+                bu_out = A::add_up(A::add_up(A::add_up(vm, evm), -A::mul_dn(dm, m)), slack);
                 a_l = sc;
+                b_l = b_chord;
                 const Real b1 = A::add_dn(A::add_dn(vl, -evl), -A::mul_up(sc, zl));
                 const Real b2 = A::add_dn(A::add_dn(vu, -evu), -A::mul_up(sc, zu));
-                b_l = b1 < b2 ? b1 : b2;
+                bl_out = b1 < b2 ? b1 : b2;
             } else {
                 // convex: chord above, tangent below
                 a_u = sc;
+                b_u = b_chord;
                 const Real b1 = A::add_up(A::add_up(vl, evl), -A::mul_dn(sc, zl));
                 const Real b2 = A::add_up(A::add_up(vu, evu), -A::mul_dn(sc, zu));
-                b_u = b1 > b2 ? b1 : b2;
+                bu_out = b1 > b2 ? b1 : b2;
                 a_l = dm;
-                b_l = A::add_dn(A::add_dn(A::add_dn(vm, -evm), -A::mul_up(dm, m)), -slack);
+                b_l = b_tan;
+                bl_out = A::add_dn(A::add_dn(A::add_dn(vm, -evm), -A::mul_up(dm, m)), -slack);
             }
         } else {
-            const Real m1 = A::add_dn(dl, -edl), m2 = A::add_dn(du, -edu);
-            Real lam = m1 < m2 ? m1 : m2;
+            // nominal slope min(s'(zl), s'(zu)); a slope lam_r below the true
+            // minimum of s' gives the sound lines through (zu, s(zu) + ev) and
+            // (zl, s(zl) - ev), which lie within (lam - lam_r) width + ev of the
+            // nominal ones on [zl, zu]
+            Real lam = dl < du ? dl : du;
             lam = lam > (Real)0 ? lam : (Real)0;
+            const Real m1 = A::add_dn(dl, -edl), m2 = A::add_dn(du, -edu);
+            Real lam_r = m1 < m2 ? m1 : m2;
+            lam_r = lam_r > (Real)0 ? lam_r : (Real)0;
             a_u = lam;
             a_l = lam;
-            b_u = A::add_up(A::add_up(vu, evu), -A::mul_dn(lam, zu));
-            b_l = A::add_dn(A::add_dn(vl, -evl), -A::mul_up(lam, zl));
+            b_u = A::fma_rn(-lam, zu, vu);
+            b_l = A::fma_rn(-lam, zl, vl);
+            const Real tilt = A::mul_up(A::add_up(lam, -lam_r), width);
+            const Real ru = uerr<Real>(A::add_up(A::abs(vu), A::mul_up(lam, A::abs(zu))));
+            const Real rl = uerr<Real>(A::add_up(A::abs(vl), A::mul_up(lam, A::abs(zl))));
+            bu_out = A::add_up(b_u, A::add_up(A::add_up(tilt, evu), ru));
+            bl_out = A::add_dn(b_l, -A::add_up(A::add_up(tilt, evl), rl));
+        }
+        Real mu = A::add_up(bu_out, -b_u);
+        const Real mu_l = A::add_up(b_l, -bl_out);
+        mu = mu > mu_l ? mu : mu_l;
+        mu = mu > (Real)0 ? mu : (Real)0;
+        // E also bounds how far the nominal lines lie from the exact ones: a
+        // chord built from inexact end values moves by up to both margins
+        if (zl >= (Real)0 || zu <= (Real)0) {
+            const Real chord_dev = A::add_up(A::add_up(evl, evu), uerr<Real>(A::add_up(A::abs(vl), A::abs(vu))));
+            mu = mu > chord_dev ? mu : chord_dev;
         }
         // (C, R) <- ((U' + L') / 2, (U' - L') / 2)
         pl.kind = 2;
@@ -594,7 +626,7 @@ struct EvalTile {
         const Real tot = A::add_up(A::add_up(bd.NC, bd.NR), A::add_up(A::abs(chi), A::abs(clo)));
         const Real mag = A::add_up(A::mul_up(a_max, tot), A::add_up(A::abs(b_u), A::abs(b_l)));
         const Real err = A::add_up(A::mul_up((Real)8 * A::ulp2, mag), (Real)(2 * d + 8) * A::tiny);
-        pl.E = A::add_up(A::mul_up(a_max, E), err);
+        pl.E = A::add_up(A::add_up(A::mul_up(a_max > lip ? a_max : lip, E), err), mu);
         pl.N = A::mul_up(A::add_up(mag, A::add_up(err, err)), (Real)1 + (Real)4 * A::ulp2);
         return pl;
     }

@@ -10,12 +10,20 @@ import oracle
 from oracle import approx
 from workloads import generators as gen
 
-from .gpu_common import BOUND_RTOL, bound_errors, random_sub_boxes
+from .gpu_common import bound_errors, random_sub_boxes
 from .test_gpu_parity import _check_count
 
 pytestmark = pytest.mark.gpu
 
 CONFIGS = ["acas_tanh", "nav_sigmoid", "tiny_tanh", "tiny_sigmoid"]
+
+# The FP32 path evaluates tanh and exp in float (2 ulp): the lines' slopes and
+# values carry about 2^-21 absolutely, which a tangent's intercept multiplies
+# by the pre-activation midpoint |m| (up to about 10 here) and each row sums
+# over 50-64 neurons; against row scales of 1-10 that is a few 1e-5, so the
+# raw bounds of these networks are held to 4e-5 of the row scale (ReLU
+# networks: 1e-5).  The widened bounds contain the oracle's exactly.
+SSHAPE_RTOL = 4e-5
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +54,7 @@ def test_bounds_match_oracle(pkg, name, n, path):
     scale = np.maximum(np.abs(olo), np.abs(ohi)) + (ohi - olo)
     assert np.all(rl <= olo + 1e-12 * scale) and np.all(rh >= ohi - 1e-12 * scale)
     elo, ehi, _ = bound_errors(rl.astype(np.float64) + err, rh.astype(np.float64) - err, olo, ohi)
-    assert elo.max() <= BOUND_RTOL and ehi.max() <= BOUND_RTOL, (elo.max(), ehi.max())
+    assert elo.max() <= SSHAPE_RTOL and ehi.max() <= SSHAPE_RTOL, (elo.max(), ehi.max())
     ocls = oracle.classify(olo, ohi, p.prop)
     dec = cls != oracle.UNDECIDED
     assert np.array_equal(cls[dec], ocls[dec])
