@@ -830,6 +830,41 @@ cudaError_t launch_recheck(slr_ctx *ctx, const slr::BoxSource &src, const slr::E
     return slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, src, out, 1);
 }
 
+// FP64 re-check: short lists, so the smallest tiles spread them over the
+// most SMs, with the most threads (a tile's products then split their inputs
+// over lane pairs: the per-level latency is what counts).  T64 = 0 when no
+// FP64 tile holds the network.
+void choose_recheck_tile(slr_ctx *ctx) {
+    std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
+    if (slr::eval_f64_pair_tile_ok(ctx->nd.d)) {
+        TileChoice c;
+        c.T = 2;
+        c.NT = 256;
+        c.smem = slr::eval_smem_bytes<double>(2, ctx->nd.d, ctx->nd.R, ctx->nd.n_max_pad, ctx->nd.n_in_max);
+        if (c.smem <= (size_t)kMaxSmem && slr::eval_gemm_items(2, ctx->nd.d, ctx->nd.n_max_pad) <= 2 * 256) {
+            c.blocks = slr::eval_blocks_per_sm_f64(2, 256, c.smem);
+            if (c.blocks > 0) c64.push_back(c);
+        }
+    }
+    ctx->T64 = 0;
+    for (const TileChoice &c : c64) {
+        if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT > ctx->NT64)) {
+            ctx->T64 = c.T;
+            ctx->NT64 = c.NT;
+            ctx->smem64 = c.smem;
+            ctx->grid64 = c.blocks * ctx->sm_count;
+        }
+    }
+    // on request, the same tile on a cluster of CTAs (products dealt over their
+    // SMs) where the GPU runs such clusters
+    ctx->grid64c = 0;
+    if (ctx->T64 > 0 && ctx->T64 <= 4 && ctx->NT64 == 256 && ctx->opt.recheck_cluster == 1 &&
+        slr::eval_gemm_items(ctx->T64, ctx->nd.d, ctx->nd.n_max_pad) <= slr::kRecheckCluster * 256) {
+        const int nc = slr::eval_f64_cluster_max(ctx->T64, ctx->smem64);
+        if (nc > 0) ctx->grid64c = nc * slr::kRecheckCluster;
+    }
+}
+
 int prepare_device(slr_ctx *ctx) {
     if (!ctx->dev_dirty) return SLR_OK;
     if (ctx->widths.back() != (int)(ctx->C.size() / std::max<size_t>(1, ctx->e.size())))
@@ -865,7 +900,9 @@ int prepare_device(slr_ctx *ctx) {
     if (ctx->wide) {
         if ((rc = build_wide(ctx, Lf))) return rc;
         ctx->T32 = ctx->NT32 = 0;
-        ctx->T64 = 0;
+        // the FP64 re-check of the wide path's NEAR boxes runs the FP64 tile
+        // kernel where the network fits it (none for the widest networks)
+        choose_recheck_tile(ctx);
         ctx->tc_ok = false;
         ctx->H = 0;
         for (int k = 1; k < ctx->K; ++k) ctx->H += ctx->widths[k];
@@ -907,37 +944,7 @@ int prepare_device(slr_ctx *ctx) {
     ctx->NT32 = best.NT;
     ctx->smem32 = best.smem;
     ctx->grid32 = best.blocks * ctx->sm_count;
-    // FP64 re-check: short lists, so the smallest tiles spread them over the
-    // most SMs, with the most threads (a tile's products then split their
-    // inputs over lane pairs: the per-level latency is what counts)
-    std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
-    if (slr::eval_f64_pair_tile_ok(ctx->nd.d)) {
-        TileChoice c;
-        c.T = 2;
-        c.NT = 256;
-        c.smem = slr::eval_smem_bytes<double>(2, ctx->nd.d, ctx->nd.R, ctx->nd.n_max_pad, ctx->nd.n_in_max);
-        if (c.smem <= (size_t)kMaxSmem && slr::eval_gemm_items(2, ctx->nd.d, ctx->nd.n_max_pad) <= 2 * 256) {
-            c.blocks = slr::eval_blocks_per_sm_f64(2, 256, c.smem);
-            if (c.blocks > 0) c64.push_back(c);
-        }
-    }
-    ctx->T64 = 0;
-    for (const TileChoice &c : c64) {
-        if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT > ctx->NT64)) {
-            ctx->T64 = c.T;
-            ctx->NT64 = c.NT;
-            ctx->smem64 = c.smem;
-            ctx->grid64 = c.blocks * ctx->sm_count;
-        }
-    }
-    // on request, the same tile on a cluster of CTAs (products dealt over their
-    // SMs) where the GPU runs such clusters
-    ctx->grid64c = 0;
-    if (ctx->T64 > 0 && ctx->T64 <= 4 && ctx->NT64 == 256 && ctx->opt.recheck_cluster == 1 &&
-        slr::eval_gemm_items(ctx->T64, ctx->nd.d, ctx->nd.n_max_pad) <= slr::kRecheckCluster * 256) {
-        const int nc = slr::eval_f64_cluster_max(ctx->T64, ctx->smem64);
-        if (nc > 0) ctx->grid64c = nc * slr::kRecheckCluster;
-    }
+    choose_recheck_tile(ctx);
     // adjoint: keep as many hidden layers' equations in shared memory as fit in
     // 96 KB, recompute the others
     {
@@ -1418,7 +1425,7 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
     }
 
     const bool leaves = ctx->opt.record_leaves != 0;
-    const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0 && !ctx->wide;
+    const bool recheck = ctx->opt.fp64_recheck != 0 && ctx->T64 > 0;
     const bool slopes = ctx->opt.alpha_steps > 0;
     if (slopes || grad_split) {
         if ((rc = check_adjoint(ctx))) return rc;
@@ -1497,8 +1504,24 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
             ow.cls = ctx->cls;
             ow.tie_count = &ctx->ctr->ties;
             ow.status = ctx->status;
+            ow.near_list = recheck ? ctx->near_list : nullptr;
+            ow.near_count = &ctx->ctr->near_n[t];
+            ow.near_cap = ctx->near_cap;
             if ((rc = run_wide(ctx, src, nt, ow, &launches))) return rc;
             CK(ctx, mark(t, 1));
+            if (recheck) {
+                // boxes whose class depends on the wide path's widening, in FP64
+                slr::BoxSource s2 = src;
+                s2.index = ctx->near_list;
+                s2.index_count = &ctx->ctr->near_n[t];
+                s2.cap = ctx->near_cap;
+                slr::EvalOutputs o2{};
+                o2.cls = ctx->cls;
+                o2.tie_count = &ctx->ctr->ties;
+                o2.status = ctx->status;
+                CK(ctx, launch_recheck(ctx, s2, o2));
+                ++launches;
+            }
         } else if (use_tc) {
             // tier 1 on the tensor cores; boxes whose class depends on its
             // widening are re-bounded by the FP32 path (tier 2), and those whose

@@ -413,7 +413,17 @@ __global__ void wide_classify_kernel(const NetParams<float> net, int nb, int64_t
         }
         if (out.row_err != nullptr)
             for (int r = 0; r < R; ++r) out.row_err[oidx * R + r] = e[r];
-        if (cls == kUndecided && opt != kUndecided && out.tie_count != nullptr) atomicAdd(out.tie_count, 1ull);
+        if (cls == kUndecided && opt != kUndecided) {
+            // the class depends on the widening: to the FP64 re-check if there
+            // is one, else counted as a tie
+            if (out.near_list != nullptr) {
+                const unsigned long long pos = atomicAdd(out.near_count, 1ull);
+                if ((int64_t)pos < out.near_cap) out.near_list[pos] = bidx[b];
+                else atomicOr(out.status, kStatusNearOverflow);
+            } else if (out.tie_count != nullptr) {
+                atomicAdd(out.tie_count, 1ull);
+            }
+        }
     }
 }
 

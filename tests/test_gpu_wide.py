@@ -61,19 +61,34 @@ def test_wide_and_tile_paths_agree(pkg):
     assert np.max(np.abs((a[1] - a[3]) - (b[1] - b[3])) / scale) <= 2 * BOUND_RTOL
 
 
-@pytest.mark.parametrize("name,D", [("tiny", 16), ("acas", 11), ("nav", 9)])
-def test_wide_count_brackets_oracle(pkg, name, D):
-    """Without an FP64 re-check, boxes whose class depends on the widening stay
-    undecided (tie_leaves): the bracket contains the oracle's, and equals it
-    when there are none."""
+@pytest.mark.parametrize("name,D", [("tiny", 16), ("acas", 11), ("nav", 9), ("acas", 16)])
+def test_wide_count_equals_oracle(pkg, name, D):
+    """The wide path's boxes whose class depends on its widening are re-bounded
+    by the FP64 tile kernel (these networks fit it): counts, per-level
+    statistics and leaf sets equal the oracle's."""
     p = gen.make(name)
-    with _counter(pkg, p, wide=1) as c:
+    with _counter(pkg, p, wide=1, record_leaves=1) as c:
         r = c.count(D)
-    ref = oracle.count(p.net, p.lo, p.hi, p.prop, D)
+        codes, depth, cls = c.leaves()
+    ref = oracle.count(p.net, p.lo, p.hi, p.prop, D, collect_leaves=True)
+    assert r["tie_leaves"] == 0
+    assert (r["unsafe_lo"], r["unsafe_hi"]) == (ref.unsafe_lo, ref.unsafe_hi)
+    for t, lv in enumerate(ref.levels):
+        assert (r["level_boxes"][t], r["level_safe"][t], r["level_unsafe"][t], r["level_undecided"][t]) == \
+            (lv["boxes"], lv["safe"], lv["unsafe"], lv["undecided"]), t
+    assert sorted(zip(codes.tolist(), depth.tolist(), cls.tolist())) == sorted(ref.leaves)
+    if name == "acas" and D == 16:
+        assert r["rechecked"] > 0
+
+
+def test_wide_count_without_recheck_brackets_oracle(pkg):
+    """With the re-check off, boxes whose class depends on the widening stay
+    undecided (tie_leaves): the bracket contains the oracle's."""
+    p = gen.make("acas")
+    with _counter(pkg, p, wide=1, fp64_recheck=0) as c:
+        r = c.count(14)
+    ref = oracle.count(p.net, p.lo, p.hi, p.prop, 14)
     assert r["unsafe_lo"] <= ref.unsafe_lo <= ref.unsafe_hi <= r["unsafe_hi"]
-    if r["tie_leaves"] == 0:
-        assert (r["unsafe_lo"], r["unsafe_hi"]) == (ref.unsafe_lo, ref.unsafe_hi)
-        assert r["boxes"] == ref.boxes
 
 
 def test_mnist_shaped_bounds(pkg):
