@@ -223,6 +223,9 @@ def main():
                     help="boxes x threads per CTA of the FP32 evaluation kernel, e.g. 16x256 (default: timed choice)")
     ap.add_argument("--alpha-cap", type=int, default=1 << 20,
                     help="most undecided boxes per level whose slopes are optimised")
+    ap.add_argument("--alpha-margin", type=float, default=0.2,
+                    help="optimise only boxes whose decision gap is within this fraction of their bound width "
+                         "(0: every undecided box)")
     ap.add_argument("--shard-level", type=int, default=-1,
                     help="strong scaling: the ranks share one count, rank r taking every N-th subtree below this "
                          "level (default: weak scaling, a problem per rank)")
@@ -325,7 +328,7 @@ def main():
             fixed_split = c.count(D)     # fixed slopes, gradient split
     if args.alpha_steps:
         c.set_options(profile=1, alpha_steps=args.alpha_steps, alpha_lr=args.alpha_lr, alpha_cap=args.alpha_cap,
-                      **tile)
+                      alpha_margin=args.alpha_margin, **tile)
     else:
         c.set_options(profile=1, alpha_cap=args.alpha_cap, **tile)
     for _ in range(args.warmup):
@@ -508,8 +511,9 @@ def run_forms(pkg, p, D, args, fp32, flush):
     except pkg.SlrError as e:
         forms["split_tf32"] = {"unavailable": str(e)}
     steps = args.form_alpha_steps
-    f, r = leg({"alpha_steps": steps, "alpha_lr": 0.1}, max(1, args.form_steps - 1), 1)
+    f, r = leg({"alpha_steps": steps, "alpha_lr": 0.1, "alpha_margin": args.alpha_margin}, args.form_steps, 1)
     f["alpha_steps"] = steps
+    f["alpha_margin"] = args.alpha_margin
     f["alpha_boxes"] = r["alpha_boxes"]
     f["alpha_decided"] = r["alpha_decided"]
     f["nested_in_fp32"] = fp32["unsafe_lo"] <= r["unsafe_lo"] <= r["unsafe_hi"] <= fp32["unsafe_hi"]

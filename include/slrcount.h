@@ -117,6 +117,14 @@ typedef struct {
                                products dealt over them and exchanged through distributed
                                shared memory.  Both are sound; the products' inputs are summed
                                in another order, so a bound may differ in its last float64 bits */
+    float alpha_margin;     /* alpha_steps > 0: optimise only the UNDECIDED boxes whose decision gap
+                               at the fixed slopes (the smaller of the SAFE gap sum_c max(0, min_r hi_r)
+                               and the UNSAFE gap min_c max(0, -min_r lo_r)) is at most alpha_margin
+                               times the box's widest row bound hi_r - lo_r; the others keep fixed
+                               slopes (most boxes far from a decision stay undecided whatever the
+                               slopes).  0: every UNDECIDED box up to alpha_cap.  Default 0.2.
+                               Not applied under SLR_SPLIT_GRADIENT, whose split choices need the
+                               optimised slopes of every UNDECIDED box */
 } slr_options;
 
 #define SLR_MAX_LEVELS 63

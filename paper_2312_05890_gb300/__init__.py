@@ -53,7 +53,8 @@ class slr_options(ctypes.Structure):
                 ("alpha_steps", ctypes.c_int32), ("alpha_lr", ctypes.c_float), ("alpha_cap", ctypes.c_int64),
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
                 ("wide", ctypes.c_int32), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
-                ("shard_level", ctypes.c_int32), ("recheck_cluster", ctypes.c_int32)]
+                ("shard_level", ctypes.c_int32), ("recheck_cluster", ctypes.c_int32),
+                ("alpha_margin", ctypes.c_float)]
 
 
 _U64A = ctypes.c_uint64 * (MAX_LEVELS + 1)

@@ -751,6 +751,49 @@ __global__ void slr_gather_undecided_kernel(const uint8_t *cls, const unsigned l
     }
 }
 
+// Keeps the listed boxes (positions p < *n_in of lo, hi) whose decision gap
+// (the smaller of the SAFE gap sum_c max(0, min_{r in c} hi_r) and the UNSAFE
+// gap min_c max(0, -min_{r in c} lo_r)) is at most tau times the widest
+// hi_r - lo_r of the box; appends their frontier indices list_in[p] to
+// list_out (order across warps unspecified).
+__global__ void slr_margin_filter_kernel(const NetParams<float> net, const float *lo, const float *hi,
+                                         const unsigned long long *n_in, int64_t cap, const int64_t *list_in,
+                                         int64_t *list_out, unsigned long long *n_out, float tau) {
+    int64_t n = (int64_t)*n_in;
+    n = n < cap ? n : cap;
+    const int R = net.R;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        bool keep = false;
+        if (p < n) {
+            const float *l = lo + p * R, *h = hi + p * R;
+            float safe_gap = 0.f, unsafe_gap = INFINITY, width = 0.f;
+            int r0 = 0;
+            for (int c = 0; c < net.n_clauses; ++c) {
+                const int r1 = net.clause_end[c];
+                float mh = INFINITY, ml = INFINITY;
+                for (int r = r0; r < r1; ++r) {
+                    mh = fminf(mh, h[r]);
+                    ml = fminf(ml, l[r]);
+                    width = fmaxf(width, h[r] - l[r]);
+                }
+                safe_gap += fmaxf(mh, 0.f);
+                unsafe_gap = fminf(unsafe_gap, fmaxf(-ml, 0.f));
+                r0 = r1;
+            }
+            keep = fminf(safe_gap, unsafe_gap) <= tau * width;
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+        if (ballot == 0u) continue;
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(n_out, (unsigned long long)__popc(ballot));
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (keep) list_out[start + __popc(ballot & ((1u << lane) - 1u))] = list_in[p];
+    }
+}
+
 size_t adjoint_box_bytes(const AdjArgs &a) { return sizeof(float) * adj_box_floats(a); }
 
 size_t adjoint_smem_bytes(const AdjArgs &a) {
@@ -793,6 +836,13 @@ cudaError_t launch_merge_bounds(const NetParams<float> &net, int64_t n, const un
 cudaError_t launch_gather_undecided(const uint8_t *cls, const unsigned long long *n, int64_t cap, int64_t *list,
                                     unsigned long long *list_n, int64_t list_cap, int grid, cudaStream_t s) {
     slr_gather_undecided_kernel<<<grid, 256, 0, s>>>(cls, n, cap, list, list_n, list_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_margin_filter(const NetParams<float> &net, const float *lo, const float *hi,
+                                 const unsigned long long *n_in, int64_t cap, const int64_t *list_in,
+                                 int64_t *list_out, unsigned long long *n_out, float tau, int grid, cudaStream_t s) {
+    slr_margin_filter_kernel<<<grid, 256, 0, s>>>(net, lo, hi, n_in, cap, list_in, list_out, n_out, tau);
     return cudaGetLastError();
 }
 

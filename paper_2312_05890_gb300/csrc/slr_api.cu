@@ -1141,6 +1141,7 @@ void slr_default_options(slr_options *opt) {
     opt->alpha_steps = 0;
     opt->alpha_lr = 0.1f;
     opt->alpha_cap = (int64_t)1 << 16;
+    opt->alpha_margin = 0.2f;
     opt->tile_boxes = 0;
     opt->tile_threads = 0;
     opt->wide = 0;
@@ -1244,6 +1245,8 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
             return fail(ctx, SLR_EINVAL, "alpha_lr must be finite and positive");
         if (opt->alpha_cap < 1 || opt->alpha_cap > ((int64_t)1 << 24))
             return fail(ctx, SLR_EINVAL, "alpha_cap %lld out of range", (long long)opt->alpha_cap);
+        if (!(opt->alpha_margin >= 0.f) || !std::isfinite(opt->alpha_margin))
+            return fail(ctx, SLR_EINVAL, "alpha_margin must be finite and >= 0");
         if (opt->relax_mode != SLR_RELAX_NEURIFY)
             return fail(ctx, SLR_EUNSUPPORTED, "slope optimisation needs relax mode NEURIFY");
     }
@@ -2807,12 +2810,13 @@ int check_adjoint(slr_ctx *ctx) {
 struct AlphaBuffers {
     float *alpha, *m, *v, *lo_new, *hi_new, *lo_best, *hi_best;
     int8_t *dir;
-    int64_t *list;
+    int64_t *list, *list2;
+    unsigned long long *n_all;    // boxes gathered before the margin filter
 };
 
 size_t alpha_bytes(int64_t cap, int64_t H, int R) {
     return align_up((size_t)cap * H * sizeof(float)) * 3 + align_up((size_t)cap * R * sizeof(float)) * 4 +
-           align_up((size_t)cap) + align_up((size_t)cap * sizeof(int64_t));
+           align_up((size_t)cap) + 2 * align_up((size_t)cap * sizeof(int64_t)) + align_up(sizeof(unsigned long long));
 }
 
 AlphaBuffers carve_alpha(void *base, int64_t cap, int64_t H, int R) {
@@ -2832,6 +2836,8 @@ AlphaBuffers carve_alpha(void *base, int64_t cap, int64_t H, int R) {
     b.hi_best = (float *)take((size_t)cap * R * sizeof(float));
     b.dir = (int8_t *)take((size_t)cap);
     b.list = (int64_t *)take((size_t)cap * sizeof(int64_t));
+    b.list2 = (int64_t *)take((size_t)cap * sizeof(int64_t));
+    b.n_all = (unsigned long long *)take(sizeof(unsigned long long));
     return b;
 }
 
@@ -2928,13 +2934,30 @@ int slr_internal_alpha_level(slr_ctx *ctx, const slr::BoxSource &frontier, int t
     if (!ctx->alpha_ctr) CK(ctx, cudaMalloc(&ctx->alpha_ctr, 2 * (slr::kMaxDepth + 2) * sizeof(unsigned long long)));
     const AlphaBuffers b = carve_alpha(ctx->alpha_buf, cap, ctx->H, R);
     unsigned long long *list_n = ctx->alpha_ctr + 2 * t;
-    CK(ctx, slr::launch_gather_undecided(ctx->cls, frontier.count, ctx->cap, b.list, list_n, cap,
-                                         std::max(1, ctx->sm_count * 4), ctx->stream));
-    *launches += 1;
     slr::BoxSource src = frontier;
+    src.cap = cap;
+    // (the gradient split rule takes every UNDECIDED box's split from its
+    // optimised slopes, so there every box is optimised)
+    if (ctx->opt.alpha_margin > 0.f && ctx->opt.split_rule != SLR_SPLIT_GRADIENT) {
+        // only boxes whose decision gap at the fixed slopes is within
+        // alpha_margin of their widest row bound: the rest are far from any
+        // decision that tighter slopes could reach
+        CK(ctx, cudaMemsetAsync(b.n_all, 0, sizeof(unsigned long long), ctx->stream));
+        CK(ctx, slr::launch_gather_undecided(ctx->cls, frontier.count, ctx->cap, b.list2, b.n_all, cap,
+                                             std::max(1, ctx->sm_count * 4), ctx->stream));
+        src.index = b.list2;
+        src.index_count = b.n_all;
+        if ((rc = eval_by_position(ctx, src, nullptr, b.lo_new, b.hi_new, cap))) return rc;
+        CK(ctx, slr::launch_margin_filter(ctx->nf, b.lo_new, b.hi_new, b.n_all, cap, b.list2, b.list, list_n,
+                                          ctx->opt.alpha_margin, std::max(1, ctx->sm_count * 4), ctx->stream));
+        *launches += 3;
+    } else {
+        CK(ctx, slr::launch_gather_undecided(ctx->cls, frontier.count, ctx->cap, b.list, list_n, cap,
+                                             std::max(1, ctx->sm_count * 4), ctx->stream));
+        *launches += 1;
+    }
     src.index = b.list;
     src.index_count = list_n;
-    src.cap = cap;
     return optimise_slopes(ctx, src, cap, list_n, b, ctx->opt.alpha_steps, ctx->opt.alpha_lr, nullptr, ctx->cls,
                            list_n + 1, false, launches);
 }

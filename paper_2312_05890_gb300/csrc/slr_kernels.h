@@ -126,6 +126,9 @@ cudaError_t launch_merge_bounds(const NetParams<float> &net, int64_t n, const un
                                 const float *lo_new, const float *hi_new, float *lo_best, float *hi_best,
                                 uint8_t *cls_pos, uint8_t *cls_idx, const int64_t *index, int first,
                                 unsigned long long *decided, cudaStream_t s);
+cudaError_t launch_margin_filter(const NetParams<float> &net, const float *lo, const float *hi,
+                                 const unsigned long long *n_in, int64_t cap, const int64_t *list_in,
+                                 int64_t *list_out, unsigned long long *n_out, float tau, int grid, cudaStream_t s);
 cudaError_t launch_gather_undecided(const uint8_t *cls, const unsigned long long *n, int64_t cap, int64_t *list,
                                     unsigned long long *list_n, int64_t list_cap, int grid, cudaStream_t s);
 

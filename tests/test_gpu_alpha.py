@@ -227,18 +227,26 @@ def test_optimised_slopes_tighten_acas(pkg):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name,D", [("tiny", 14), ("acas", 12), ("nav", 10)])
-def test_count_with_slopes_nests_in_fixed_count(pkg, name, D):
+@pytest.mark.parametrize("margin", [0.0, 0.2])
+def test_count_with_slopes_nests_in_fixed_count(pkg, name, D, margin):
+    """Every undecided box optimised (margin 0) or only those near a decision
+    (margin 0.2, the default): the count nests inside the fixed-slope one,
+    which equals the oracle's, and repeats exactly."""
     p = gen.make(name)
     with _counter(pkg, p) as c:
         fixed = c.count(D)
-        c.set_options(alpha_steps=20, alpha_lr=0.1)
+        c.set_options(alpha_steps=20, alpha_lr=0.1, alpha_margin=margin)
         opt = c.count(D)
         again = c.count(D)
+        c.set_options(alpha_steps=20, alpha_lr=0.1, alpha_margin=0.0)
+        full = c.count(D)
     ref = oracle.count(p.net, p.lo, p.hi, p.prop, D)
     assert (fixed["unsafe_lo"], fixed["unsafe_hi"]) == (ref.unsafe_lo, ref.unsafe_hi)
     assert fixed["unsafe_lo"] <= opt["unsafe_lo"] <= opt["unsafe_hi"] <= fixed["unsafe_hi"]
     assert opt["boxes"] <= fixed["boxes"]
-    assert opt["alpha_boxes"] > 0
+    assert opt["alpha_boxes"] <= full["alpha_boxes"]
+    if margin == 0.0:
+        assert opt["alpha_boxes"] > 0
     # the optimisation is deterministic: no atomics feed the slopes
     assert (again["unsafe_lo"], again["unsafe_hi"], again["boxes"]) == (opt["unsafe_lo"], opt["unsafe_hi"], opt["boxes"])
 
@@ -397,7 +405,7 @@ def test_wide_count_with_slopes_nests(pkg):
     D = 11
     with _counter(pkg, p, wide=1) as c:
         fixed = c.count(D)
-        c.set_options(wide=1, alpha_steps=10, alpha_lr=0.1)
+        c.set_options(wide=1, alpha_steps=10, alpha_lr=0.1, alpha_margin=0.0)
         opt = c.count(D)
     assert fixed["unsafe_lo"] <= opt["unsafe_lo"] <= opt["unsafe_hi"] <= fixed["unsafe_hi"]
     assert opt["alpha_boxes"] > 0

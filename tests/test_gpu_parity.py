@@ -189,11 +189,15 @@ def test_determinism(pkg):
 
 
 def _recheck_both_ways(pkg, p, D):
+    """Both re-check forms on the same FP32 tile (the autotuner of two contexts
+    may time two tiles differently, and the tile fixes which boxes are NEAR)."""
     out = []
+    tile = {}
     for cl in (1, 0):
-        with _counter(pkg, p, record_leaves=1, recheck_cluster=cl) as c:
+        with _counter(pkg, p, record_leaves=1, recheck_cluster=cl, **tile) as c:
             r = c.count(D)
             leaves = sorted(zip(*[x.tolist() for x in c.leaves()]))
+        tile = dict(tile_boxes=r["tile"][0], tile_threads=r["tile"][1])
         for k in ("device_ms", "kernel_ms", "h2d_bytes", "d2h_bytes"):
             r.pop(k)
         out.append((r, leaves))

@@ -153,8 +153,8 @@ def test_gradient_rule_with_optimised_slopes(pkg):
     count repeats exactly."""
     p = _shrunk("acas", 0.1)
     D = 12
-    r, codes, depth, cls, S = _gpu_count(pkg, p, D, alpha_steps=10, alpha_lr=0.1)
-    r2, *_ = _gpu_count(pkg, p, D, alpha_steps=10, alpha_lr=0.1)
+    r, codes, depth, cls, S = _gpu_count(pkg, p, D, alpha_steps=10, alpha_lr=0.1, alpha_margin=0.0)
+    r2, *_ = _gpu_count(pkg, p, D, alpha_steps=10, alpha_lr=0.1, alpha_margin=0.0)
     assert (r2["unsafe_lo"], r2["unsafe_hi"], r2["boxes"]) == (r["unsafe_lo"], r["unsafe_hi"], r["boxes"])
     assert r["alpha_boxes"] > 0
     assert sum(1 << (D - int(t)) for t in depth) == 1 << D
