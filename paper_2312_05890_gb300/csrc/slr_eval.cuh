@@ -64,6 +64,16 @@ __device__ __forceinline__ void st_cluster4(uint32_t addr, const double (&v)[4])
     asm volatile("st.shared::cluster.v2.f64 [%0+16], {%1, %2};" ::"r"(addr), "d"(v[2]), "d"(v[3]) : "memory");
 }
 
+// Four consecutive values from shared memory at a 32-bit shared address.
+template <typename Real> __device__ __forceinline__ void lds4(uint32_t addr, Real (&v)[4]);
+template <> __device__ __forceinline__ void lds4<float>(uint32_t addr, float (&v)[4]) {
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(addr));
+}
+template <> __device__ __forceinline__ void lds4<double>(uint32_t addr, double (&v)[4]) {
+    asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(addr));
+    asm("ld.shared.v2.f64 {%0, %1}, [%2+16];" : "=d"(v[2]), "=d"(v[3]) : "r"(addr));
+}
+
 template <typename Real> struct V4;
 template <> struct V4<float> {
     static __device__ __forceinline__ void ld(const float *p, float (&v)[4]) {
@@ -739,8 +749,10 @@ struct EvalTile {
     }
 
     // ---- bounds and ReLU relaxation of one hidden row, in place ----------------------
+    // Returns true when the relaxed row is identically zero (a stable inactive
+    // neuron whose error bound is 0): its columns add nothing to the next product.
     template <class Row>
-    static __device__ __forceinline__ void relax_row(const Row &R, int d, int relax_mode, Real chi, Real clo, Real E,
+    static __device__ __forceinline__ bool relax_row(const Row &R, int d, int relax_mode, Real chi, Real clo, Real E,
                                                      const float *a_ptr, int act = kActRelu) {
         const int cr = cR(d);
         RowBounds<Real> bd;
@@ -759,13 +771,18 @@ struct EvalTile {
         R(cr + d) = pl.rd;
         R(cN(d)) = pl.N;
         R(cE(d)) = pl.E;
+        return pl.kind == 1 && pl.nh == (Real)0 && pl.nl == (Real)0 && pl.rd == (Real)0 && pl.N == (Real)0 &&
+               pl.E == (Real)0;
     }
 
     // ---- one hidden layer: constant, error, concrete bounds, ReLU relaxation ----
+    // `live` (nullable): live[p] is set to 1 for every row p that is not
+    // identically zero in some box of the tile (the flags start at 0).
     template <class L>
     static __device__ void hidden_epilogue(const L &lay, const Real *sConst, const NetParams<Real> &net, int layer,
                                            Real gcoef, const float *alpha = nullptr, int64_t alpha_ld = 0,
-                                           int64_t base = 0, int64_t n = 0, int alpha_off = 0, bool delta = false) {
+                                           int64_t base = 0, int64_t n = 0, int alpha_off = 0, bool delta = false,
+                                           int *live = nullptr) {
         const int d = net.d;
         const int nrows = net.n[layer];
         const int n_in = net.n[layer - 1];
@@ -787,7 +804,8 @@ struct EvalTile {
                 const int64_t pos = base + b < n ? base + b : base;
                 a_ptr = alpha + pos * alpha_ld + alpha_off + p;
             }
-            relax_row(R, d, net.relax_mode, chi, clo, E, a_ptr, net.act[layer - 1]);
+            const bool zero = relax_row(R, d, net.relax_mode, chi, clo, E, a_ptr, net.act[layer - 1]);
+            if (live != nullptr && !zero) live[p] = 1;
             lay.finish_row(p, b);
         }
     }
@@ -879,6 +897,53 @@ struct EvalTile {
         }
     }
 
+    // The same product over the rows of a list: rows[ii] = byte offsets (i Mpad,
+    // i NS) of the rows i to sum over; a row that is zero in every box of the
+    // tile adds exact zeros, so leaving it out changes no sum.
+    static __device__ __forceinline__ void tile_mac_rows(const Real *wp, const Real *xp, const int2 *rows, int n_rows,
+                                                         bool is_abs, Real (&acc)[8][4]) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+        const uint32_t w0 = (uint32_t)__cvta_generic_to_shared(wp), x0 = (uint32_t)__cvta_generic_to_shared(xp);
+        if (is_abs) {
+#pragma unroll 2
+            for (int ii = 0; ii < n_rows; ++ii) {
+                const int2 o = rows[ii];
+                Real a0[4], a1[4], x[4];
+                lds4<Real>(w0 + (uint32_t)o.x, a0);
+                lds4<Real>(w0 + (uint32_t)o.x + 4 * (uint32_t)sizeof(Real), a1);
+                lds4<Real>(x0 + (uint32_t)o.y, x);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        acc[r][c] = A::fma_rn(A::abs(a0[r]), x[c], acc[r][c]);
+                        acc[r + 4][c] = A::fma_rn(A::abs(a1[r]), x[c], acc[r + 4][c]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int ii = 0; ii < n_rows; ++ii) {
+                const int2 o = rows[ii];
+                Real a0[4], a1[4], x[4];
+                lds4<Real>(w0 + (uint32_t)o.x, a0);
+                lds4<Real>(w0 + (uint32_t)o.x + 4 * (uint32_t)sizeof(Real), a1);
+                lds4<Real>(x0 + (uint32_t)o.y, x);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        acc[r][c] = A::fma_rn(a0[r], x[c], acc[r][c]);
+                        acc[r + 4][c] = A::fma_rn(a1[r], x[c], acc[r + 4][c]);
+                    }
+                }
+            }
+        }
+    }
+
     static __device__ __forceinline__ void tile_mac(const Real *wp, const Real *xp, int n_in, int Mpad, int NS,
                                                     bool is_abs, Real (&acc)[8][4]) {
 #pragma unroll
@@ -923,10 +988,13 @@ struct EvalTile {
     // The next layer's constants (n_const items of const_item) share the phase:
     // they fill the threads that hold fewer product tiles, and they read the
     // state before the barrier like the tiles do.
+    // `rows`: the input rows to sum over (see tile_mac_rows), n_rows of them;
+    // the float tile always passes a list, the float64 one sums over all n_in.
     template <class L>
     static __device__ void contract(const L &lay, Real *sConst, const Real *sRef, const NetParams<Real> &net,
                                     int layer, Real *S, const Real *sW, int n_in, int Mpad, int d, int NS,
-                                    bool delta, uint32_t rW, uint32_t rA) {
+                                    bool delta, uint32_t rW, uint32_t rA, const int2 *rows = nullptr,
+                                    int n_rows = 0) {
         const int QW = (d + 1) * T / 4;       // quads of C coefficient columns and the constant column
         const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
         const int Q = QW + QA;
@@ -954,8 +1022,13 @@ struct EvalTile {
                 item_tile(item, G, QW, QA, rW, rA, g, q);
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-                const int i0 = part * n_in / parts, i1 = (part + 1) * n_in / parts;
-                tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, i1 - i0, Mpad, NS, is_abs, acc[0]);
+                if constexpr (kCompensated) {
+                    const int i0 = part * n_rows / parts, i1 = (part + 1) * n_rows / parts;
+                    tile_mac_rows(sW + g * 8, S + j0, rows + i0, i1 - i0, is_abs, acc[0]);
+                } else {
+                    const int i0 = part * n_in / parts, i1 = (part + 1) * n_in / parts;
+                    tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, i1 - i0, Mpad, NS, is_abs, acc[0]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r)
@@ -973,7 +1046,8 @@ struct EvalTile {
                     item_tile(item, G, QW, QA, rW, rA, g, q);
                     const bool is_abs = q >= QW;
                     const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-                    tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
+                    if constexpr (kCompensated) tile_mac_rows(sW + g * 8, S + j0, rows, n_rows, is_abs, acc[it]);
+                    else tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
                 }
             }
         }
@@ -1171,6 +1245,9 @@ template <typename Real>
 struct TileSmem {
     Real *sS, *sConst, *sRef, *sW, *sMh, *sMl, *sR, *sLo, *sHi, *sErr;
     int64_t *sIdx;
+    int2 *sRows;    // input rows of the next product: byte offsets (i Mpad, i NS)
+    int *sLive;     // per row: not identically zero in some box of the tile
+    int *sNRows;    // length of sRows
 };
 
 template <typename Real, int T>
@@ -1198,6 +1275,12 @@ __device__ __forceinline__ TileSmem<Real> carve_smem(unsigned char *sp, int nmp,
     m.sErr = reinterpret_cast<Real *>(sp);
     sp += (size_t)T * R * sizeof(Real);
     m.sIdx = reinterpret_cast<int64_t *>(sp);
+    sp += (size_t)T * sizeof(int64_t);
+    m.sRows = reinterpret_cast<int2 *>(sp);
+    sp += (size_t)nmp * sizeof(int2);
+    m.sLive = reinterpret_cast<int *>(sp);
+    sp += (size_t)nmp * sizeof(int);
+    m.sNRows = reinterpret_cast<int *>(sp);
     return m;
 }
 
@@ -1236,6 +1319,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         const int64_t k = base + (threadIdx.x < nb ? threadIdx.x : 0);
         sIdx[threadIdx.x] = src.index != nullptr ? src.index[k] : k;
     }
+    for (int i = threadIdx.x; i < net.n_max_pad; i += NT) sm.sLive[i] = 0;
     __syncthreads();
 
     // ---- boxes: centre (hi + lo) and radius, outward ----------------------
@@ -1279,15 +1363,40 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
     const uint32_t rW = Tile::recip32((d + 1) * T / 4), rA = Tile::recip32((d + 3) * T / 4);
     int alpha_off = 0;
     for (int k = 1; k < net.K; ++k) {
-        Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
-                              alpha_off, dconst);
-        alpha_off += net.n[k];
+        // the float tile's products sum over a list of input rows: hidden ->
+        // hidden, only the rows that are not zero in every box of the tile
+        // (inactive ReLUs with no error: their products are exact zeros, so
+        // every sum is unchanged); the property layer, all rows
+        const bool dk = dconst && k + 1 < net.K;
         const int n_out = net.n[k + 1];
         const int Mpad = (n_out + 7) & ~7;
+        if (dconst && !dk) {
+            for (int i = threadIdx.x; i < net.n[k]; i += NT)
+                sm.sRows[i] = make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
+            if (threadIdx.x == 0) *sm.sNRows = net.n[k];
+        }
+        Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
+                              alpha_off, dconst, dk ? sm.sLive : nullptr);
+        alpha_off += net.n[k];
         Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
-        const bool dk = dconst && k + 1 < net.K;
         if (dk) {
             __syncthreads();
+            if (threadIdx.x < 32) {
+                // the live rows in order; the flags reset for the next layer
+                const int lane = threadIdx.x;
+                int count = 0;
+                for (int i0 = 0; i0 < net.n[k]; i0 += 32) {
+                    const int i = i0 + lane;
+                    const bool lv = i < net.n[k] && sm.sLive[i] != 0;
+                    const unsigned bal = __ballot_sync(0xffffffffu, lv);
+                    if (lv)
+                        sm.sRows[count + __popc(bal & ((1u << lane) - 1u))] =
+                            make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
+                    if (i < net.n[k]) sm.sLive[i] = 0;
+                    count += __popc(bal);
+                }
+                if (lane == 0) *sm.sNRows = count;
+            }
             Tile::delta_prep(lay, sm.sRef, net, k);
         }
         __syncthreads();
@@ -1296,7 +1405,8 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
             static_assert(!Tile::kCompensated, "the cluster tile is the float64 re-check's");
             Tile::template contract_cluster<CL>(lay, sConst, net, k, sS, sW, net.n[k], Mpad, d, NS, rW, rA);
         } else {
-            Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA);
+            Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA, sm.sRows,
+                           dconst ? *sm.sNRows : 0);
         }
         __syncthreads();
     }
