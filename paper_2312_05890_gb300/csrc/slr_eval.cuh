@@ -311,9 +311,12 @@ __device__ __forceinline__ void act_eval(int act, Real z, Real &v, Real &ev, Rea
     ed = (Real)8 * A::ulp2;
 }
 
-template <typename Real, int T, int NT, int KI = 2>
+// DC > 0: the network has DC inputs, known at compile time (loops over the
+// input coefficients unrolled, column offsets constant); DC = 0: read from net.d.
+template <typename Real, int T, int NT, int KI = 2, int DC = 0>
 struct EvalTile {
     using A = Arith<Real>;
+    static __device__ __forceinline__ int dim_of(const NetParams<Real> &net) { return DC > 0 ? DC : net.d; }
     // FP32 carries the constants as compensated pairs; FP64 is precise enough
     // with a plain FMA chain (its gamma_n error bound is ~1e-14 relative).
     static constexpr bool kCompensated = sizeof(Real) == 4;
@@ -355,7 +358,7 @@ struct EvalTile {
     template <class L>
     static __device__ void init_layer(const L &lay, const NetParams<Real> &net, const Real *sMh, const Real *sMl,
                                       const Real *sR) {
-        const int d = net.d;
+        const int d = dim_of(net);
         const int n1 = net.n[1];
         for (int item = threadIdx.x; item < n1 * T; item += NT) {
             const int p = item / T;
@@ -415,7 +418,7 @@ struct EvalTile {
     template <class L>
     static __device__ __forceinline__ void const_item(const L &lay, Real *sConst, const Real *sW, int Mpad,
                                                       const NetParams<Real> &net, int layer, int item) {
-        const int d = net.d;
+        const int d = dim_of(net);
         const int n_in = net.n[layer];
         const int n_out = net.n[layer + 1];
         const bool last = layer + 1 == net.K;
@@ -783,7 +786,7 @@ struct EvalTile {
                                            Real gcoef, const float *alpha = nullptr, int64_t alpha_ld = 0,
                                            int64_t base = 0, int64_t n = 0, int alpha_off = 0, bool delta = false,
                                            int *live = nullptr) {
-        const int d = net.d;
+        const int d = dim_of(net);
         const int nrows = net.n[layer];
         const int n_in = net.n[layer - 1];
         for (int item = threadIdx.x; item < nrows * T; item += NT) {
@@ -820,7 +823,7 @@ struct EvalTile {
     // column is left unchanged and ignored after the product.
     template <class L>
     static __device__ void delta_prep(const L &lay, Real *sRef, const NetParams<Real> &net, int layer) {
-        const int d = net.d;
+        const int d = dim_of(net);
         const int n_in = net.n[layer];
         const int nmp = net.n_max_pad;
         for (int item = threadIdx.x; item < n_in * T; item += NT) {
@@ -1186,7 +1189,7 @@ struct EvalTile {
     template <class L>
     static __device__ void final_rows(const L &lay, const Real *sConst, const NetParams<Real> &net, Real gcoef,
                                       Real *sLo, Real *sHi, Real *sErr) {
-        const int d = net.d;
+        const int d = dim_of(net);
         const int R = net.R;
         const int K = net.K;
         const int n_in = net.n[K - 1];
@@ -1303,12 +1306,12 @@ __device__ __forceinline__ int64_t source_count(const BoxSource &src) {
 // pass 1: re-check of such a list in the higher precision (writes the class,
 //         counts the boxes still depending on E as ties).
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int NT, int KI = 2, int CL = 1>
+template <typename Real, int T, int NT, int KI = 2, int CL = 1, int DC = 0>
 __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, const EvalOutputs &out, const int pass,
                           const TileSmem<Real> &sm, const int64_t base, const int64_t n) {
     using A = Arith<Real>;
-    using Tile = EvalTile<Real, T, NT, KI>;
-    const int d = net.d;
+    using Tile = EvalTile<Real, T, NT, KI, DC>;
+    const int d = Tile::dim_of(net);
     const int R = net.R;
     const int NS = state_stride(T, d);
     Real *sS = sm.sS, *sConst = sm.sConst, *sW = sm.sW, *sMh = sm.sMh, *sMl = sm.sMl, *sR = sm.sR;
@@ -1459,14 +1462,15 @@ constexpr int eval_min_blocks() {
     return sizeof(Real) != 4 ? 1 : (KI == 2 ? 2 : (NT == 256 ? 3 : 6));
 }
 
-template <typename Real, int T, int NT, int KI = 2>
+template <typename Real, int T, int NT, int KI = 2, int DC = 0>
 __global__ void __launch_bounds__(NT, (eval_min_blocks<Real, NT, KI>()))
 slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutputs out, const int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileSmem<Real> sm = carve_smem<Real, T>(smem_raw, net.n_max_pad, net.d, net.n_in_max, net.R);
+    const TileSmem<Real> sm =
+        carve_smem<Real, T>(smem_raw, net.n_max_pad, DC > 0 ? DC : net.d, net.n_in_max, net.R);
     const int64_t n = source_count(src);
     for (int64_t base = (int64_t)blockIdx.x * T; base < n; base += (int64_t)gridDim.x * T)
-        eval_tile<Real, T, NT, KI>(net, src, out, pass, sm, base, n);
+        eval_tile<Real, T, NT, KI, 1, DC>(net, src, out, pass, sm, base, n);
 }
 
 // The float64 re-check with each tile on a cluster of kRecheckCluster CTAs (one

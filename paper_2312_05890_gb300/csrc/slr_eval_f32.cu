@@ -4,10 +4,10 @@
 
 namespace slr {
 
-template <int T, int NT, int KI>
+template <int T, int NT, int KI, int DC = 0>
 static cudaError_t launch_t(int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass) {
-    auto k = slr_eval_kernel<float, T, NT, KI>;
+    auto k = slr_eval_kernel<float, T, NT, KI, DC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, s>>>(net, src, out, pass);
@@ -41,9 +41,24 @@ static int items_per_thread(int T, int NT, int items) { return (T <= 8 && items 
         default: break;                                                                        \
     }
 
+// Networks with five inputs (the collision-avoidance shape) on the two-tile,
+// 256-thread tiles: the input count as a compile-time constant.
+static cudaError_t launch_d5(int T, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
+                             const BoxSource &src, const EvalOutputs &out, int pass) {
+    switch (T) {
+        case 32: return launch_t<32, 256, 2, 5>(grid, smem, s, net, src, out, pass);
+        case 20: return launch_t<20, 256, 2, 5>(grid, smem, s, net, src, out, pass);
+        case 16: return launch_t<16, 256, 2, 5>(grid, smem, s, net, src, out, pass);
+        case 12: return launch_t<12, 256, 2, 5>(grid, smem, s, net, src, out, pass);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_eval_f32(int T, int NT, int grid, size_t smem, cudaStream_t s, const NetParams<float> &net,
                             const BoxSource &src, const EvalOutputs &out, int pass) {
     const int KI = items_per_thread(T, NT, eval_gemm_items(T, net.d, net.n_max_pad));
+    if (net.d == 5 && NT == 256 && KI == 2 && (T == 32 || T == 20 || T == 16 || T == 12))
+        return launch_d5(T, grid, smem, s, net, src, out, pass);
     if (NT == 256) {
         SLR_DISPATCH(256, launch_t)
     } else if (NT == 128) {
