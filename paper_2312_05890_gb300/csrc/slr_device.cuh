@@ -229,7 +229,7 @@ __host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max
     s += 3 * (size_t)T * d * sizeof(Real);                 // box centres (hi, lo) and radii
     s += 3 * (size_t)T * R * sizeof(Real);                 // row lo / hi / E
     s += (size_t)T * sizeof(int64_t);                      // box indices
-    s += (size_t)n_max_pad * (sizeof(int2) + sizeof(int)) + 16;   // live-row list and flags, list length
+    s += (size_t)n_max_pad * (sizeof(int2) + 2 * sizeof(int)) + 16;   // live-row list, indices, flags, length
     return (s + 15) & ~(size_t)15;
 }
 

@@ -415,9 +415,12 @@ struct EvalTile {
         for (int item = threadIdx.x; item < pairs * T; item += NT) const_item(lay, sConst, sW, Mpad, net, layer, item);
     }
 
+    // `ridx` (nullable): sum only over the input rows ridx[0 .. n_rows) (the
+    // others are zero in every box of the tile); null: over all n_in rows.
     template <class L>
     static __device__ __forceinline__ void const_item(const L &lay, Real *sConst, const Real *sW, int Mpad,
-                                                      const NetParams<Real> &net, int layer, int item) {
+                                                      const NetParams<Real> &net, int layer, int item,
+                                                      const int *ridx = nullptr, int n_rows = 0) {
         const int d = dim_of(net);
         const int n_in = net.n[layer];
         const int n_out = net.n[layer + 1];
@@ -432,7 +435,9 @@ struct EvalTile {
             Real s0 = bias[p0], e0 = 0, a0 = A::abs(s0);
             Real s1 = two ? bias[p0 + 1] : (Real)0, e1 = 0, a1 = A::abs(s1);
             Real f0 = 0, f1 = 0;
-            for (int i = 0; i < n_in; ++i) {
+            const int nr = ridx != nullptr ? n_rows : n_in;
+            for (int ii = 0; ii < nr; ++ii) {
+                const int i = ridx != nullptr ? ridx[ii] : ii;
                 const auto Ri = lay.row(i, b);
                 const Real h = Ri(cCh(d));
                 const Real l = Ri(cCl(d));
@@ -854,11 +859,14 @@ struct EvalTile {
     // One output row's constant at the reference box: sum_i W[p][i] (h_i + l_i) + b_p,
     // error-free products and compensated sums, written to slot b = 0 of sConst.
     static __device__ __forceinline__ void ref_item(Real *sConst, const Real *sRef, const Real *sW, int Mpad,
-                                                    const NetParams<Real> &net, int layer, int p) {
+                                                    const NetParams<Real> &net, int layer, int p,
+                                                    const int *ridx = nullptr, int n_rows = 0) {
         const int n_in = net.n[layer];
         const int nmp = net.n_max_pad;
         Real s = net.b[layer][p], e = 0, a = A::abs(s);
-        for (int i = 0; i < n_in; ++i) {
+        const int nr = ridx != nullptr ? n_rows : n_in;
+        for (int ii = 0; ii < nr; ++ii) {
+            const int i = ridx != nullptr ? ridx[ii] : ii;
             const Real w = sW[i * Mpad + p];
             Real p1, pe, t, se;
             two_prod<Real>(w, sRef[i], p1, pe);
@@ -996,8 +1004,8 @@ struct EvalTile {
     template <class L>
     static __device__ void contract(const L &lay, Real *sConst, const Real *sRef, const NetParams<Real> &net,
                                     int layer, Real *S, const Real *sW, int n_in, int Mpad, int d, int NS,
-                                    bool delta, uint32_t rW, uint32_t rA, const int2 *rows = nullptr,
-                                    int n_rows = 0) {
+                                    bool delta, uint32_t rW, uint32_t rA, const int2 *rows, const int *ridx,
+                                    int n_rows) {
         const int QW = (d + 1) * T / 4;       // quads of C coefficient columns and the constant column
         const int QA = (d + 3) * T / 4;       // quads of R, N, E columns
         const int Q = QW + QA;
@@ -1025,13 +1033,8 @@ struct EvalTile {
                 item_tile(item, G, QW, QA, rW, rA, g, q);
                 const bool is_abs = q >= QW;
                 const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-                if constexpr (kCompensated) {
-                    const int i0 = part * n_rows / parts, i1 = (part + 1) * n_rows / parts;
-                    tile_mac_rows(sW + g * 8, S + j0, rows + i0, i1 - i0, is_abs, acc[0]);
-                } else {
-                    const int i0 = part * n_in / parts, i1 = (part + 1) * n_in / parts;
-                    tile_mac(sW + g * 8 + i0 * Mpad, S + j0 + i0 * NS, i1 - i0, Mpad, NS, is_abs, acc[0]);
-                }
+                const int i0 = part * n_rows / parts, i1 = (part + 1) * n_rows / parts;
+                tile_mac_rows(sW + g * 8, S + j0, rows + i0, i1 - i0, is_abs, acc[0]);
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r)
@@ -1049,8 +1052,7 @@ struct EvalTile {
                     item_tile(item, G, QW, QA, rW, rA, g, q);
                     const bool is_abs = q >= QW;
                     const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
-                    if constexpr (kCompensated) tile_mac_rows(sW + g * 8, S + j0, rows, n_rows, is_abs, acc[it]);
-                    else tile_mac(sW + g * 8, S + j0, n_in, Mpad, NS, is_abs, acc[it]);
+                    tile_mac_rows(sW + g * 8, S + j0, rows, n_rows, is_abs, acc[it]);
                 }
             }
         }
@@ -1059,8 +1061,8 @@ struct EvalTile {
             int idx = threadIdx.x + ((busy - (int)threadIdx.x + NT - 1) / NT) * NT;
             if (idx < busy) idx += NT;
             for (; idx < busy + n_const; idx += NT) {
-                if (delta) ref_item(sConst, sRef, sW, Mpad, net, layer, idx - busy);
-                else const_item(lay, sConst, sW, Mpad, net, layer, idx - busy);
+                if (delta) ref_item(sConst, sRef, sW, Mpad, net, layer, idx - busy, ridx, n_rows);
+                else const_item(lay, sConst, sW, Mpad, net, layer, idx - busy, ridx, n_rows);
             }
         }
         __syncthreads();
@@ -1249,6 +1251,7 @@ struct TileSmem {
     Real *sS, *sConst, *sRef, *sW, *sMh, *sMl, *sR, *sLo, *sHi, *sErr;
     int64_t *sIdx;
     int2 *sRows;    // input rows of the next product: byte offsets (i Mpad, i NS)
+    int *sRowIdx;   // the same rows' indices i
     int *sLive;     // per row: not identically zero in some box of the tile
     int *sNRows;    // length of sRows
 };
@@ -1281,6 +1284,8 @@ __device__ __forceinline__ TileSmem<Real> carve_smem(unsigned char *sp, int nmp,
     sp += (size_t)T * sizeof(int64_t);
     m.sRows = reinterpret_cast<int2 *>(sp);
     sp += (size_t)nmp * sizeof(int2);
+    m.sRowIdx = reinterpret_cast<int *>(sp);
+    sp += (size_t)nmp * sizeof(int);
     m.sLive = reinterpret_cast<int *>(sp);
     sp += (size_t)nmp * sizeof(int);
     m.sNRows = reinterpret_cast<int *>(sp);
@@ -1370,19 +1375,22 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         // hidden, only the rows that are not zero in every box of the tile
         // (inactive ReLUs with no error: their products are exact zeros, so
         // every sum is unchanged); the property layer, all rows
-        const bool dk = dconst && k + 1 < net.K;
+        const bool lk = k + 1 < net.K;        // a hidden -> hidden product
+        const bool dk = dconst && lk;
         const int n_out = net.n[k + 1];
         const int Mpad = (n_out + 7) & ~7;
-        if (dconst && !dk) {
-            for (int i = threadIdx.x; i < net.n[k]; i += NT)
+        if (!lk && CL == 1) {
+            for (int i = threadIdx.x; i < net.n[k]; i += NT) {
                 sm.sRows[i] = make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
+                sm.sRowIdx[i] = i;
+            }
             if (threadIdx.x == 0) *sm.sNRows = net.n[k];
         }
         Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
-                              alpha_off, dconst, dk ? sm.sLive : nullptr);
+                              alpha_off, dconst, lk && CL == 1 ? sm.sLive : nullptr);
         alpha_off += net.n[k];
         Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
-        if (dk) {
+        if (lk && CL == 1) {
             __syncthreads();
             if (threadIdx.x < 32) {
                 // the live rows in order; the flags reset for the next layer
@@ -1392,15 +1400,17 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
                     const int i = i0 + lane;
                     const bool lv = i < net.n[k] && sm.sLive[i] != 0;
                     const unsigned bal = __ballot_sync(0xffffffffu, lv);
-                    if (lv)
-                        sm.sRows[count + __popc(bal & ((1u << lane) - 1u))] =
-                            make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
+                    if (lv) {
+                        const int at = count + __popc(bal & ((1u << lane) - 1u));
+                        sm.sRows[at] = make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
+                        sm.sRowIdx[at] = i;
+                    }
                     if (i < net.n[k]) sm.sLive[i] = 0;
                     count += __popc(bal);
                 }
                 if (lane == 0) *sm.sNRows = count;
             }
-            Tile::delta_prep(lay, sm.sRef, net, k);
+            if (dk) Tile::delta_prep(lay, sm.sRef, net, k);
         }
         __syncthreads();
         // constants and products; barrier inside, then the in-place store
@@ -1409,7 +1419,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
             Tile::template contract_cluster<CL>(lay, sConst, net, k, sS, sW, net.n[k], Mpad, d, NS, rW, rA);
         } else {
             Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA, sm.sRows,
-                           dconst ? *sm.sNRows : 0);
+                           sm.sRowIdx, *sm.sNRows);
         }
         __syncthreads();
     }
