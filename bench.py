@@ -41,9 +41,9 @@ TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 / BF16 tensor rates of 
 
 # DRAM bytes per box of the FP32 evaluation kernel from one ncu capture of the
 # kernel source hashed below (profiles/slr_eval_f32_acas_D20.md: levels 18 and
-# 19, 8.50 and 8.25 B per box); reported as roofline.traffic only while the
+# 19, 8.56 and 8.29 B per box); reported as roofline.traffic only while the
 # kernel source is unchanged.
-TRAFFIC = {"source_sha": "54ec98a492be300f", "bytes_per_box": 8.5}
+TRAFFIC = {"source_sha": "a1a7636218ad23f3", "bytes_per_box": 8.4}
 KERNEL_SOURCES = ["paper_2312_05890_gb300/csrc/slr_eval.cuh", "paper_2312_05890_gb300/csrc/slr_eval_f32.cu",
                   "paper_2312_05890_gb300/csrc/slr_device.cuh"]
 
