@@ -231,6 +231,9 @@ def main():
                          "level (default: weak scaling, a problem per rank)")
     ap.add_argument("--recheck-cluster", action="store_true",
                     help="FP64 re-check with each tile on a cluster of 4 CTAs instead of one CTA")
+    ap.add_argument("--batch-widths", default="tile", choices=["full", "tile"],
+                    help="batched workload: only the hidden widths a tile holds (32-128, default) or 32-512 as "
+                         "stated (256- and 512-wide members on the wide path; one step takes minutes)")
     ap.add_argument("--no-forms", action="store_true", help="skip the short legs of the chosen forms")
     ap.add_argument("--no-batch-form", action="store_true", help="skip the batched leg among the forms")
     ap.add_argument("--form-steps", type=int, default=3, help="timed counts per form leg")
@@ -542,6 +545,10 @@ def batch_form(pkg, args, flush):
                         "--workload batch times it in full)"}
 
 
+BATCH_WIDTHS = {"full": {"widths": (32, 64, 128, 256, 512), "tile_only": False},
+                "tile": {"widths": (32, 64, 128), "tile_only": True}}
+
+
 def bench_batch(args, world, rank, local_rank):
     """The batched workload: 256 (network, property) problems counted together per step."""
     import torch
@@ -551,7 +558,8 @@ def bench_batch(args, world, rank, local_rank):
     from workloads import generators as gen
     torch.cuda.set_device(local_rank)
     dist = multirank.init(world)
-    probs = gen.batched_uneven(multirank.weak_seed(args.seed, rank))
+    full = args.batch_widths == "full"
+    probs = gen.batched_uneven(multirank.weak_seed(args.seed, rank), **BATCH_WIDTHS[args.batch_widths])
     flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device="cuda")
     c = pkg.Counter(local_rank)
     for _ in range(args.warmup):
@@ -574,6 +582,8 @@ def bench_batch(args, world, rank, local_rank):
     clocks = sampler.stop()
     per_boxes = sorted(r["boxes"] for r in res)
     levels = sorted(r["levels"] for r in res)
+    done = sorted(r["completion_ms"] for r in res)
+    wide = [i for i, p in enumerate(probs) if max(p.net.widths[1:-1]) >= 256]
     max_ms, tot_boxes, value = multirank.job_rate(sum(ms), boxes, dist)
     tot_s = max_ms / 1e3
     _, _, e2e_value = multirank.job_rate(1e3 * sum(e2e), boxes, dist)
@@ -581,11 +591,14 @@ def bench_batch(args, world, rank, local_rank):
     # step's device time (evaluation, re-check and compaction together)
     flops = sum(algorithmic_flops_per_box(p.net.widths, p.prop.R) * r["boxes"] for p, r in zip(probs, res))
     clk = clocks.get("sm_mhz") or 2070.0
-    peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    fp32_peak = pkg.slr_measure_fp32_peak(local_rank)
+    peak = fp32_peak["tflops"]
     achieved = flops * args.steps / (sum(ms) / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "slr_eval_batch_kernel<float>",
-                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk:.0f} MHz (sampled median)",
+                "peak_basis": (f"measured: FFMA-throughput kernel in this process ({fp32_peak['ms']:.1f} ms); "
+                               f"nominal at {clk:.0f} MHz: "
+                               f"{SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12:.1f} TFLOP/s"),
                 "time_basis": "whole step (all kernels), so a lower bound on the kernel's own rate"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -605,12 +618,20 @@ def bench_batch(args, world, rank, local_rank):
             "metric": "slr_subdomain_bounds_per_sec", "value": value, "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched: {len(probs)} problems over 16 networks (d 5-32, widths 32-128, "
-                                   f"2-8 hidden layers), depth caps 12-22, seed {args.seed}",
+            "config": {"workload": f"batched: {len(probs)} problems over 16 networks (d 5-32, widths "
+                                   f"{'32-512' if full else '32-128'}, 2-8 hidden layers), depth caps 12-22, "
+                                   f"seed {args.seed}",
+                       "wide_members": len(wide),
                        "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"weak x{world}",
                        "tile_boxes": res[0]["tile"][0], "launches_per_step": res[0]["launches"]},
             "per_problem": {"boxes_min_median_max": [per_boxes[0], per_boxes[len(per_boxes) // 2], per_boxes[-1]],
-                            "levels_min_max": [levels[0], levels[-1]]},
+                            "levels_min_max": [levels[0], levels[-1]],
+                            "completion_ms_min_median_max": [done[0], done[len(done) // 2], done[-1]],
+                            "wide_members_boxes": sum(res[i]["boxes"] for i in wide),
+                            # wide members run after the tiled ones: their share of the step
+                            "wide_members_ms": (max(res[i]["completion_ms"] for i in wide) - max(
+                                (r["completion_ms"] for j, r in enumerate(res) if j not in wide), default=0.0))
+                            if wide else 0.0},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "boxes/s", "h2d_bytes_per_step": res[0]["h2d_bytes"],
                     "d2h_bytes_per_step": res[0]["d2h_bytes"]},

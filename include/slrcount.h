@@ -158,6 +158,8 @@ typedef struct {
     double gemm_ms;         /* with profile, wide path: device time of the tensor-core products */
     int64_t gemm_launches;  /* wide path: product launches */
     double gemm_flop;       /* wide path: algorithmic FLOP of those products (2 M N K each) */
+    double completion_ms;   /* slr_count_batch: device time from the start of the batch to the end
+                               of this problem's last level (0 for slr_count) */
 } slr_result;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
@@ -334,8 +336,10 @@ typedef struct {
  * replayed while later calls keep the batch's shape (same widths, rows,
  * clauses and depths; weights, boxes and properties may change).  Problems
  * too wide for any tile are counted one by one on the wide path in the same
- * call.  results[i] receives problem i's count as slr_count would return it
- * (device_ms is the time of the whole batch; tile_boxes the problem's tile).
+ * call, after the tiled ones.  results[i] receives problem i's count as
+ * slr_count would return it (device_ms is the time of the whole batch,
+ * completion_ms the time from its start to the end of problem i's last level;
+ * tile_boxes the problem's tile).
  * Inputs are copied.  Each problem's frontier holds up to min(2^depth,
  * frontier_cap) boxes (SLR_EOVERFLOW beyond).  Uses the context's options
  * (relax_mode, fp64_recheck, frontier_cap) and stream; FP32 arithmetic with

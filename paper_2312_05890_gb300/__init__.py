@@ -70,7 +70,8 @@ class slr_result(ctypes.Structure):
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
                 ("rechecked_fp32", ctypes.c_uint64), ("alpha_boxes", ctypes.c_uint64),
                 ("alpha_decided", ctypes.c_uint64), ("alpha_ms", ctypes.c_double),
-                ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_int64), ("gemm_flop", ctypes.c_double)]
+                ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_int64), ("gemm_flop", ctypes.c_double),
+                ("completion_ms", ctypes.c_double)]
 
     def to_dict(self):
         n = self.depth + 1
@@ -83,7 +84,7 @@ class slr_result(ctypes.Structure):
                     rechecked_fp32=int(self.rechecked_fp32), alpha_boxes=int(self.alpha_boxes),
                     alpha_decided=int(self.alpha_decided), alpha_ms=float(self.alpha_ms),
                     gemm_ms=float(self.gemm_ms), gemm_launches=int(self.gemm_launches),
-                    gemm_flop=float(self.gemm_flop),
+                    gemm_flop=float(self.gemm_flop), completion_ms=float(self.completion_ms),
                     level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 

@@ -53,6 +53,7 @@ struct BatchState {
     int64_t launches = 0;
     int T32 = 0, T64 = 0;
     std::vector<int> tile_of;            // per problem: boxes per tile of its class
+    std::vector<cudaEvent_t> step_ev;    // recorded at the end of each level step (graph nodes)
 };
 
 struct slr_ctx {
@@ -2572,6 +2573,11 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
         cudaError_t ce = cudaMemsetAsync(bs->ctrs, 0, (size_t)P * sizeof(slr::LevelCounters), ctx->stream);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(bs->status, 0, 16, ctx->stream);
         if (ce == cudaSuccess) ce = slr::launch_init_batch((const slr::CompactArgs *)(A + o_ca), P, ctx->stream), ++L;
+        while (ce == cudaSuccess && bs->step_ev.size() < nsteps) {
+            cudaEvent_t e;
+            ce = cudaEventCreate(&e);
+            if (ce == cudaSuccess) bs->step_ev.push_back(e);
+        }
         for (size_t t = 0; t < nsteps && ce == cudaSuccess; ++t) {
             const slr::BoxSource *s_m = (const slr::BoxSource *)(A + o_sm) + t * P;
             const slr::BoxSource *s_r = (const slr::BoxSource *)(A + o_sr) + t * P;
@@ -2596,6 +2602,8 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
                 ce = slr::launch_compact_batch((const slr::CompactArgs *)(A + o_ca) + (t & 1) * P, P, (int)t, bs->status,
                                                bpp, ctx->stream);
             ++L;
+            // an event-record node: the end of level step t (per-problem completion times)
+            if (ce == cudaSuccess) ce = cudaEventRecordWithFlags(bs->step_ev[t], ctx->stream, cudaEventRecordExternal);
         }
         const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "capturing the batched count");
@@ -2659,6 +2667,10 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    std::vector<float> step_ms(bs->step_ev.size(), 0.f);
+    for (size_t t = 0; t < step_ms.size() && t < (size_t)bs->Dmax + 1; ++t)
+        cudaEventElapsedTime(&step_ms[t], ctx->ev0, bs->step_ev[t]);
+    (void)cudaGetLastError();
     for (int i = 0; i < P; ++i) {
         const slr::LevelCounters &c = bs->h_ctrs[i];
         slr_result &out = results[i];
@@ -2685,6 +2697,10 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
         out.d2h_bytes = (int64_t)((size_t)P * sizeof(slr::LevelCounters) + sizeof st);
         out.tile_boxes = bs->tile_of[i];
         out.tile_threads = 256;
+        // done at the end of the step of its last level (its depth cap, or
+        // earlier when its frontier empties)
+        const int last = std::max(0, out.levels - 1);
+        out.completion_ms = (size_t)last < step_ms.size() ? step_ms[last] : ms;
     }
     if (st & slr::kStatusOverflow) return fail(ctx, SLR_EOVERFLOW, "a problem's level exceeded its frontier capacity");
     if (st & slr::kStatusNearOverflow) return fail(ctx, SLR_EOVERFLOW, "an FP64 re-check list overflowed");
@@ -2734,6 +2750,7 @@ extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems,
             return fail(ctx, rc, "wide helper context: %s", slr_last_error(nullptr));
     }
     slr_ctx *h = ctx->wide_helper;
+    double done_ms = tile.empty() ? 0.0 : results[tile[0]].device_ms;
     slr_options o = ctx->opt;
     o.wide = 1;
     o.alpha_steps = 0;
@@ -2748,7 +2765,11 @@ extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems,
             (rc = slr_set_property(h, q.n_clauses, q.rows_per_clause, q.widths[q.K], q.C, q.e, q.strict)) ||
             (rc = slr_count(h, q.depth, &results[i])))
             return fail(ctx, rc, "problem %d: %s", i, slr_last_error(h));
+        done_ms += results[i].device_ms;
+        results[i].completion_ms = done_ms;
     }
+    // every result reports the whole batch's device time
+    for (int i = 0; i < n; ++i) results[i].device_ms = done_ms;
     return SLR_OK;
 }
 
