@@ -63,19 +63,37 @@ def test_leaf_brackets_contain_the_closed_form_area():
         assert t.estimate <= 2 ** t.splits * area / 4.0 + 1e-12
 
 
+def _mean_matches_closed_form(seed, scale_shift=0):
+    """400 trials on a linear 2-D net: is the mean of 2^(s + scale_shift)
+    area(leaf) within 5 standard errors of the closed-form rate?"""
+    p, w, c, vr = _linear_case(seed)
+    xs = []
+    for k in range(400):
+        t = approx.one_trial(p.net, p.lo, p.hi, p.prop, k % 64, 5, 256, 0, seed=100 + seed * 1000 + k // 64)
+        area = _halfplane_area(w, c, t.leaf_lo.astype(np.float64), t.leaf_hi.astype(np.float64))
+        xs.append(2.0 ** (t.splits + scale_shift) * area / 4.0)
+    xs = np.array(xs)
+    se = xs.std(ddof=1) / np.sqrt(xs.size)
+    return abs(xs.mean() - vr) <= 5 * se + 1e-12
+
+
 def test_scaled_leaf_areas_average_to_the_root_area():
     """E[2^s area(leaf)] = area(root): over 400 trials the mean lies within 5
-    standard errors of the closed form (a biased coin or a wrong scale fails)."""
+    standard errors of the closed form."""
     for seed in (0, 2):
-        p, w, c, vr = _linear_case(seed)
-        xs = []
-        for k in range(400):
-            t = approx.one_trial(p.net, p.lo, p.hi, p.prop, k % 64, 5, 256, 0, seed=100 + seed * 1000 + k // 64)
-            area = _halfplane_area(w, c, t.leaf_lo.astype(np.float64), t.leaf_hi.astype(np.float64))
-            xs.append(2 ** t.splits * area / 4.0)
-        xs = np.array(xs)
-        se = xs.std(ddof=1) / np.sqrt(xs.size)
-        assert abs(xs.mean() - vr) <= 5 * se + 1e-12, (seed, xs.mean(), vr, se)
+        assert _mean_matches_closed_form(seed)
+
+
+def test_planted_mistakes_fail_the_mean():
+    """A coin that always keeps the lower half, or the
+    scale 2^(s-1) in place of 2^s, moves the mean away from the closed form."""
+    assert not _mean_matches_closed_form(0, scale_shift=-1)
+    orig = approx.coin
+    try:
+        approx.coin = lambda seed, trial, split: 0       # always the lower half
+        assert not _mean_matches_closed_form(0) or not _mean_matches_closed_form(2)
+    finally:
+        approx.coin = orig
 
 
 def test_lower_bound_holds_with_its_confidence():
