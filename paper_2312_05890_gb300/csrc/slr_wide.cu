@@ -36,7 +36,8 @@ using WTile = EvalTile<float, 1, 1>;   // only its static row helpers are used
 
 constexpr int kWN = 256;                          // GEMM tile: columns
 constexpr int kWM = 128;                          // rows (tensor-memory lanes)
-constexpr int kWK = 32;                           // K per pipeline stage
+constexpr int kWK = 16;                           // K per pipeline stage (two stages: 108 KB, 2 CTAs per SM)
+constexpr int kWQ = kWK / 4;                      // float4 of one operand row per stage
 constexpr int kWSbo = (kWK / 4) * kTcLbo;         // bytes between 8-row core-matrix groups
 constexpr int kWABytes = (kWM / 8) * kWSbo;       // one A piece of a stage
 constexpr int kWBBytes = (kWN / 8) * kWSbo;       // one B piece of a stage
@@ -444,15 +445,15 @@ __device__ __forceinline__ void wide_load_stage(const WideGemm &G, int m0, int n
 #pragma unroll
     for (int u = 0; u < kWM * kWK / 4 / kWThreads; ++u) {
         const int q = tid + u * kWThreads;
-        const size_t g = (size_t)(m0 + (q >> 3)) * G.Kpad + k0 + (q & 7) * 4;
+        const size_t g = (size_t)(m0 + q / kWQ) * G.Kpad + k0 + (q % kWQ) * 4;
         r.ah[u] = __ldg(reinterpret_cast<const float4 *>(G.Ahi + g));
         r.al[u] = __ldg(reinterpret_cast<const float4 *>(G.Alo + g));
     }
 #pragma unroll
     for (int u = 0; u < kWN * kWK / 4 / kWThreads; ++u) {
         const int q = tid + u * kWThreads;
-        const int col = n0 + (q >> 3);
-        const int k = k0 + (q & 7) * 4;
+        const int col = n0 + q / kWQ;
+        const int k = k0 + (q % kWQ) * 4;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col < G.ncols) {
             const float *src = G.B + (size_t)col * G.ldb + k;
@@ -473,14 +474,14 @@ __device__ __forceinline__ void wide_store_stage(unsigned char *st, int tid, con
 #pragma unroll
     for (int u = 0; u < kWM * kWK / 4 / kWThreads; ++u) {
         const int q = tid + u * kWThreads;
-        const int o = wboff(q >> 3, (q & 7) * 4);
+        const int o = wboff(q / kWQ, (q % kWQ) * 4);
         *reinterpret_cast<float4 *>(sAh + o) = r.ah[u];
         *reinterpret_cast<float4 *>(sAl + o) = r.al[u];
     }
 #pragma unroll
     for (int u = 0; u < kWN * kWK / 4 / kWThreads; ++u) {
         const int q = tid + u * kWThreads;
-        const int o = wboff(q >> 3, (q & 7) * 4);
+        const int o = wboff(q / kWQ, (q % kWQ) * 4);
         const float4 v = r.b[u];
         float4 h, l;
         h.x = tf32_rna(v.x);
@@ -496,7 +497,7 @@ __device__ __forceinline__ void wide_store_stage(unsigned char *st, int tid, con
     }
 }
 
-__global__ void __launch_bounds__(kWThreads, 1) wide_gemm_kernel(const WideGemmArgs args, int gy) {
+__global__ void __launch_bounds__(kWThreads, 2) wide_gemm_kernel(const WideGemmArgs args, int gy) {
     extern __shared__ __align__(1024) unsigned char smem_w[];
     const WideGemm &G = args.g[blockIdx.z];
     // the M tiles of one column block are neighbours in the launch order, so
