@@ -415,9 +415,9 @@ struct EvalTile {
         for (int item = threadIdx.x; item < pairs * T; item += NT) const_item(lay, sConst, sW, Mpad, net, layer, item);
     }
 
-    // `ridx` (nullable): sum only over the input rows ridx[0 .. n_rows) (the
-    // others are zero in every box of the tile); null: over all n_in rows.
-    template <class L>
+    // kList: sum only over the input rows ridx[0 .. n_rows) (the others are
+    // zero in every box of the tile); else over all n_in rows.
+    template <bool kList = false, class L>
     static __device__ __forceinline__ void const_item(const L &lay, Real *sConst, const Real *sW, int Mpad,
                                                       const NetParams<Real> &net, int layer, int item,
                                                       const int *ridx = nullptr, int n_rows = 0) {
@@ -435,9 +435,9 @@ struct EvalTile {
             Real s0 = bias[p0], e0 = 0, a0 = A::abs(s0);
             Real s1 = two ? bias[p0 + 1] : (Real)0, e1 = 0, a1 = A::abs(s1);
             Real f0 = 0, f1 = 0;
-            const int nr = ridx != nullptr ? n_rows : n_in;
+            const int nr = kList ? n_rows : n_in;
             for (int ii = 0; ii < nr; ++ii) {
-                const int i = ridx != nullptr ? ridx[ii] : ii;
+                const int i = kList ? ridx[ii] : ii;
                 const auto Ri = lay.row(i, b);
                 const Real h = Ri(cCh(d));
                 const Real l = Ri(cCl(d));
@@ -858,15 +858,15 @@ struct EvalTile {
 
     // One output row's constant at the reference box: sum_i W[p][i] (h_i + l_i) + b_p,
     // error-free products and compensated sums, written to slot b = 0 of sConst.
+    // over the input rows ridx[0 .. n_rows) (the others are zero in every box)
     static __device__ __forceinline__ void ref_item(Real *sConst, const Real *sRef, const Real *sW, int Mpad,
-                                                    const NetParams<Real> &net, int layer, int p,
-                                                    const int *ridx = nullptr, int n_rows = 0) {
+                                                    const NetParams<Real> &net, int layer, int p, const int *ridx,
+                                                    int n_rows) {
         const int n_in = net.n[layer];
         const int nmp = net.n_max_pad;
         Real s = net.b[layer][p], e = 0, a = A::abs(s);
-        const int nr = ridx != nullptr ? n_rows : n_in;
-        for (int ii = 0; ii < nr; ++ii) {
-            const int i = ridx != nullptr ? ridx[ii] : ii;
+        for (int ii = 0; ii < n_rows; ++ii) {
+            const int i = ridx[ii];
             const Real w = sW[i * Mpad + p];
             Real p1, pe, t, se;
             two_prod<Real>(w, sRef[i], p1, pe);
@@ -1062,7 +1062,7 @@ struct EvalTile {
             if (idx < busy) idx += NT;
             for (; idx < busy + n_const; idx += NT) {
                 if (delta) ref_item(sConst, sRef, sW, Mpad, net, layer, idx - busy, ridx, n_rows);
-                else const_item(lay, sConst, sW, Mpad, net, layer, idx - busy, ridx, n_rows);
+                else const_item<true>(lay, sConst, sW, Mpad, net, layer, idx - busy, ridx, n_rows);
             }
         }
         __syncthreads();
