@@ -34,6 +34,11 @@ struct HostLayers {
     std::vector<std::vector<Real>> W;
     std::vector<std::vector<Real>> b;
     std::vector<Real> fold_err, fold_berr;
+    // layers >= 1: the fused tile's shared-memory image of W (rows padded to a
+    // multiple of 8 columns); float, at most 4 property rows: the fold's error
+    // bounds in the last image's padding columns R .. 2R - 1
+    std::vector<std::vector<Real>> Ws;
+    bool fold_pad = false;
 };
 
 }  // namespace
@@ -254,6 +259,22 @@ void build_layers(const Src *ctx, HostLayers<Real> &L) {
         const double tot = std::fabs(rounded - bf[r]) + bf_err[r];
         L.fold_berr[r] = sizeof(Real) == 4 ? (Real)round_up_to_float(tot * (1 + 1e-15)) : (Real)(tot * (1 + 1e-15));
     }
+    L.Ws.assign(K, {});
+    for (int k = 1; k < K; ++k) {
+        const int ni = ctx->widths[k];
+        const int no = k == K - 1 ? R : ctx->widths[k + 1];
+        const int mp = (no + 7) & ~7;
+        std::vector<Real> &img = L.Ws[k];
+        img.assign((size_t)ni * mp, (Real)0);
+        for (int i = 0; i < ni; ++i)
+            for (int p = 0; p < no; ++p) img[(size_t)i * mp + p] = L.W[k][(size_t)i * no + p];
+    }
+    L.fold_pad = sizeof(Real) == 4 && K > 1 && 2 * R <= ((R + 7) & ~7);
+    if (L.fold_pad) {
+        const int mp = (R + 7) & ~7;
+        for (int p = 0; p < R; ++p)
+            for (int i = 0; i < n_prev; ++i) L.Ws[K - 1][(size_t)i * mp + R + p] = L.fold_err[(size_t)p * n_prev + i];
+    }
 }
 
 template <typename Real>
@@ -261,6 +282,7 @@ size_t layers_bytes(const HostLayers<Real> &L) {
     size_t s = 0;
     for (auto &w : L.W) s += align_up(w.size() * sizeof(Real));
     for (auto &b : L.b) s += align_up(b.size() * sizeof(Real));
+    for (auto &w : L.Ws) s += align_up(w.size() * sizeof(Real));
     s += align_up(L.fold_err.size() * sizeof(Real)) + align_up(L.fold_berr.size() * sizeof(Real));
     return s;
 }
@@ -288,6 +310,8 @@ void layout_params(const Src *ctx, const HostLayers<Real> &L, unsigned char *dev
     p.n_in_max = std::max(nin, 1);
     p.W0 = put(L.W[0]);
     for (int k = 1; k < K; ++k) p.Wt[k] = put(L.W[k]);
+    for (int k = 1; k < K; ++k) p.Ws[k] = put(L.Ws[k]);
+    p.fold_pad = L.fold_pad ? 1 : 0;
     for (int k = 0; k < K; ++k) p.b[k] = put(L.b[k]);
     p.fold_err = put(L.fold_err);
     p.fold_berr = put(L.fold_berr);

@@ -125,6 +125,9 @@ struct NetParams {
     int n_in_max;                // max over n[0..K-1]
     const Real *W0;              // layer 0, row-major n[1] x d
     const Real *Wt[kMaxLayers];  // layer k >= 1, transposed: n[k] x n[k+1] row-major
+    const Real *Ws[kMaxLayers];  // layer k >= 1, the tile's shared-memory image of Wt[k]:
+                                 // n[k] x Mpad_k, Mpad_k = n[k+1] rounded up to 8, padding 0
+    int fold_pad;                // 1: Ws[K-1] holds fold_err[p][i] in column n[K] + p
     const Real *b[kMaxLayers];   // biases, b[K-1] folded
     const Real *fold_err;        // R x n[K-1]: bound on |W'_fp - C W_K|
     const Real *fold_berr;       // R:          bound on |b'_fp - (C b_K + e)|

@@ -859,28 +859,37 @@ struct EvalTile {
     // One output row's constant at the reference box: sum_i W[p][i] (h_i + l_i) + b_p,
     // error-free products and compensated sums, written to slot b = 0 of sConst.
     // over the input rows ridx[0 .. n_rows) (the others are zero in every box)
+    // On the property layer the error slot also takes the fold's share at the
+    // reference constant, sum_i delta_pi (|h_i| + |l_i|) + the bias fold bound,
+    // delta_pi staged in column n_out + p of sW (see final_rows).
     static __device__ __forceinline__ void ref_item(Real *sConst, const Real *sRef, const Real *sW, int Mpad,
                                                     const NetParams<Real> &net, int layer, int p, const int *ridx,
                                                     int n_rows) {
         const int n_in = net.n[layer];
         const int nmp = net.n_max_pad;
-        Real s = net.b[layer][p], e = 0, a = A::abs(s);
+        const bool last = layer + 1 == net.K;
+        const int pf = net.n[layer + 1] + p;
+        Real s = net.b[layer][p], e = 0, a = A::abs(s), f = 0;
         for (int ii = 0; ii < n_rows; ++ii) {
             const int i = ridx[ii];
             const Real w = sW[i * Mpad + p];
+            const Real h = sRef[i], l = sRef[nmp + i];
             Real p1, pe, t, se;
-            two_prod<Real>(w, sRef[i], p1, pe);
+            two_prod<Real>(w, h, p1, pe);
             two_sum<Real>(s, p1, t, se);
             s = t;
-            e = A::fma_rn(w, sRef[nmp + i], e + (pe + se));
+            e = A::fma_rn(w, l, e + (pe + se));
             a = a + A::abs(p1);
+            if (last) f = A::add_up(f, A::mul_up(sW[i * Mpad + pf], A::add_up(A::abs(h), A::abs(l))));
         }
         const Real g = gam<Real>(n_in + 2);
         Real hi, lo;
         two_sum<Real>(s, e, hi, lo);
         sConst[p * T] = hi;
         sConst[(nmp + p) * T] = lo;
-        sConst[(2 * nmp + p) * T] = A::mul_up(A::mul_up((Real)2 * g, g), A::mul_up(a, (Real)1 + gam<Real>(n_in)));
+        Real err = A::mul_up(A::mul_up((Real)2 * g, g), A::mul_up(a, (Real)1 + gam<Real>(n_in)));
+        if (last) err = A::add_up(err, A::add_up(f, net.fold_berr[p]));
+        sConst[(2 * nmp + p) * T] = err;
     }
 
     // ---- C' = W C, R' = |W| R over the coefficient, N and E columns ---------------
@@ -999,8 +1008,8 @@ struct EvalTile {
     // The next layer's constants (n_const items of const_item) share the phase:
     // they fill the threads that hold fewer product tiles, and they read the
     // state before the barrier like the tiles do.
-    // `rows`: the input rows to sum over (see tile_mac_rows), n_rows of them;
-    // the float tile always passes a list, the float64 one sums over all n_in.
+    // `rows`: the input rows to sum over (see tile_mac_rows), n_rows of them,
+    // and ridx their indices.
     template <class L>
     static __device__ void contract(const L &lay, Real *sConst, const Real *sRef, const NetParams<Real> &net,
                                     int layer, Real *S, const Real *sW, int n_in, int Mpad, int d, int NS,
@@ -1167,30 +1176,37 @@ struct EvalTile {
         cluster_barrier();
     }
 
-    // Rows of the transposed weights, NT / Mpad rows per pass (one division
-    // per thread, not one per element).
-    static __device__ void stage_weights(Real *sW, const Real *Wt, int n_in, int n_out, int Mpad) {
-        const int per = NT / Mpad;
-        if (per >= 1) {
-            const int r0 = (int)threadIdx.x / Mpad;
-            const int p = (int)threadIdx.x - r0 * Mpad;
-            if (r0 < per) {
-                const bool live = p < n_out;
-                for (int i = r0; i < n_in; i += per) sW[i * Mpad + p] = live ? Wt[(size_t)i * n_out + p] : (Real)0;
-            }
-        } else {
-            for (int idx = threadIdx.x; idx < n_in * Mpad; idx += NT) {
-                const int i = idx / Mpad;
-                const int p = idx - i * Mpad;
-                sW[idx] = p < n_out ? Wt[(size_t)i * n_out + p] : (Real)0;
-            }
+    // Starts the copy of a layer's weight image (n_in x Mpad, already padded
+    // in global memory) into sW: 16-byte cp.async pieces spread over the
+    // threads, L2 only.  The epilogue runs while they land; stage_wait, then
+    // a block barrier, make sW readable.  n_in Mpad sizeof(Real) is a multiple
+    // of 32 bytes (Mpad of 8), and both ends are 16-byte aligned.
+    static __device__ __forceinline__ void stage_weights_async(Real *sW, const Real *Ws, int n_in, int Mpad) {
+        const int pieces = n_in * Mpad * (int)sizeof(Real) / 16;
+        const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(sW);
+        const char *g0 = reinterpret_cast<const char *>(Ws);
+        for (int c = threadIdx.x; c < pieces; c += NT) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0 + 16u * (uint32_t)c),
+                         "l"(g0 + 16 * (size_t)c)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    static __device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
     // ---- property rows: constant, error (incl. the fold), sound bounds ----------
+    // `delta`: the property layer ran in reference + offset form with the
+    // fold's error bounds fe in the weight image's padding columns, so that
+    // rows R + r of the product hold sum_i fe_ri N_i and sum_i fe_ri E_i over
+    // the offset rows.  With |h_i + l_i| <= |h_i^0| + |l_i^0| + |delta_i| + err_i
+    // (box 0's constant, the offset, its rounding: the last two joined N_i and
+    // E_i in delta_prep), the fold's share sum_i fe_ri (N_i + |h_i + l_i| + E_i)
+    // is at most the reference term of ref_item plus those two sums, which
+    // add non-negative terms rounded to nearest: each at most its computed
+    // value (1 + 2 gcoef), plus n_in underflows.
     template <class L>
     static __device__ void final_rows(const L &lay, const Real *sConst, const NetParams<Real> &net, Real gcoef,
-                                      Real *sLo, Real *sHi, Real *sErr) {
+                                      Real *sLo, Real *sHi, Real *sErr, bool delta = false) {
         const int d = dim_of(net);
         const int R = net.R;
         const int K = net.K;
@@ -1201,7 +1217,12 @@ struct EvalTile {
             const auto Rw = lay.row(r, b);
             Real chi, clo, E;
             if (K > 1) {
-                finish_contraction(Rw, sConst, net.n_max_pad, r, b, d, n_in, gcoef, chi, clo, E);
+                finish_contraction(Rw, sConst, net.n_max_pad, r, b, d, n_in, gcoef, chi, clo, E, delta);
+                if (delta) {
+                    const auto Rf = lay.row(R + r, b);
+                    const Real fz = A::mul_up(A::add_up(Rf(cN(d)), Rf(cE(d))), (Real)1 + (Real)2 * gcoef);
+                    E = A::add_up(E, A::add_up(fz, (Real)(2 * n_in) * A::tiny));
+                }
             } else {
                 chi = Rw(cCh(d));
                 clo = Rw(cCl(d));
@@ -1370,27 +1391,28 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
     // reciprocals of the product tiles' column-quad counts (see item_tile)
     const uint32_t rW = Tile::recip32((d + 1) * T / 4), rA = Tile::recip32((d + 3) * T / 4);
     int alpha_off = 0;
+    bool pdelta = false;
     for (int k = 1; k < net.K; ++k) {
-        // the float tile's products sum over a list of input rows: hidden ->
-        // hidden, only the rows that are not zero in every box of the tile
-        // (inactive ReLUs with no error: their products are exact zeros, so
-        // every sum is unchanged); the property layer, all rows
+        // the tile's products sum over a list of input rows: only the rows
+        // that are not zero in every box of the tile (inactive ReLUs with no
+        // error: their products, constants and fold terms are exact zeros, so
+        // every sum is unchanged)
         const bool lk = k + 1 < net.K;        // a hidden -> hidden product
-        const bool dk = dconst && lk;
         const int n_out = net.n[k + 1];
         const int Mpad = (n_out + 7) & ~7;
-        if (!lk && CL == 1) {
-            for (int i = threadIdx.x; i < net.n[k]; i += NT) {
-                sm.sRows[i] = make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
-                sm.sRowIdx[i] = i;
-            }
-            if (threadIdx.x == 0) *sm.sNRows = net.n[k];
-        }
+        // float: the property layer too, when its weight image holds the
+        // fold's error bounds in its padding columns (at most 4 property rows)
+        const bool pk = dconst && !lk && net.fold_pad != 0;
+        const bool dk = dconst && (lk || pk);
+        // sW is free (the last product ended with a barrier): its next image
+        // lands while the epilogue runs
+        Tile::stage_weights_async(sW, net.Ws[k], net.n[k], Mpad);
         Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
-                              alpha_off, dconst, lk && CL == 1 ? sm.sLive : nullptr);
+                              alpha_off, dconst, CL == 1 ? sm.sLive : nullptr);
         alpha_off += net.n[k];
-        Tile::stage_weights(sW, net.Wt[k], net.n[k], n_out, Mpad);
-        if (lk && CL == 1) {
+        Tile::stage_wait();
+        pdelta = pk;
+        if (CL == 1) {
             __syncthreads();
             if (threadIdx.x < 32) {
                 // the live rows in order; the flags reset for the next layer
@@ -1423,7 +1445,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         }
         __syncthreads();
     }
-    Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr);
+    Tile::final_rows(lay, sConst, net, gam<Real>(net.n[net.K - 1]), sLo, sHi, sErr, pdelta);
     __syncthreads();
 
     // ---- classify (Sec. 3) and write (one CTA of a cluster) ----------------
