@@ -444,7 +444,8 @@ def main():
             "data": "synthetic", "config": config,
             "count": {"unsafe_lo": job_lo if strong else last["unsafe_lo"],
                       "unsafe_hi": job_hi if strong else last["unsafe_hi"], "boxes": last["boxes"],
-                      "rechecked": last["rechecked"], "tie_leaves": last["tie_leaves"],
+                      "rechecked": last["rechecked"], "rechecked_fp64": last["rechecked_fp64"],
+                      "tie_leaves": last["tie_leaves"],
                       "tile_boxes_threads": last["tile"]},
             "kernel_ms_per_step": {"eval_f32": kern[0] / args.steps, "recheck_f64": kern[1] / args.steps,
                                    "compact": kern[2] / args.steps},

@@ -125,6 +125,13 @@ typedef struct {
                                slopes).  0: every UNDECIDED box up to alpha_cap.  Default 0.2.
                                Not applied under SLR_SPLIT_GRADIENT, whose split choices need the
                                optimised slopes of every UNDECIDED box */
+    int32_t recheck_pairs;  /* FP64 re-check (one CTA per tile): 1 (default) = in two stages, the first
+                               with the hidden-layer products as float-float pairs on the FP32 units
+                               (float64 state, constants and relaxation; the pairs' rounding bound,
+                               about 1e-10 relative, joins the error bound E), the second, with plain
+                               FP64 products, on the boxes whose class the first left depending on E;
+                               0 = plain FP64 products only.  Both give the same classes: a box is
+                               decided by the first stage only when its bound is sound */
 } slr_options;
 
 #define SLR_MAX_LEVELS 63
@@ -135,7 +142,7 @@ typedef struct {
     uint64_t unsafe_lo;     /* volume of the boxes proved UNSAFE */
     uint64_t unsafe_hi;     /* unsafe_lo + boxes still UNDECIDED at depth D */
     uint64_t boxes;         /* boxes bounded over all levels */
-    uint64_t rechecked;     /* boxes re-bounded in FP64 */
+    uint64_t rechecked;     /* boxes re-bounded in FP64 (see recheck_pairs) */
     uint64_t tie_leaves;    /* re-bounded boxes whose FP64 class still depends on its widening */
     int32_t depth;          /* D */
     int32_t levels;         /* levels evaluated (D + 1 unless the frontier emptied first) */
@@ -160,6 +167,8 @@ typedef struct {
     double gemm_flop;       /* wide path: algorithmic FLOP of those products (2 M N K each) */
     double completion_ms;   /* slr_count_batch: device time from the start of the batch to the end
                                of this problem's last level (0 for slr_count) */
+    uint64_t rechecked_fp64; /* of `rechecked`: boxes re-bounded with plain FP64 products (with
+                               recheck_pairs, those the float-float stage left depending on E) */
 } slr_result;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to

@@ -54,7 +54,7 @@ class slr_options(ctypes.Structure):
                 ("tile_boxes", ctypes.c_int32), ("tile_threads", ctypes.c_int32),
                 ("wide", ctypes.c_int32), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
                 ("shard_level", ctypes.c_int32), ("recheck_cluster", ctypes.c_int32),
-                ("alpha_margin", ctypes.c_float)]
+                ("alpha_margin", ctypes.c_float), ("recheck_pairs", ctypes.c_int32)]
 
 
 _U64A = ctypes.c_uint64 * (MAX_LEVELS + 1)
@@ -71,7 +71,7 @@ class slr_result(ctypes.Structure):
                 ("rechecked_fp32", ctypes.c_uint64), ("alpha_boxes", ctypes.c_uint64),
                 ("alpha_decided", ctypes.c_uint64), ("alpha_ms", ctypes.c_double),
                 ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_int64), ("gemm_flop", ctypes.c_double),
-                ("completion_ms", ctypes.c_double)]
+                ("completion_ms", ctypes.c_double), ("rechecked_fp64", ctypes.c_uint64)]
 
     def to_dict(self):
         n = self.depth + 1
@@ -85,6 +85,7 @@ class slr_result(ctypes.Structure):
                     alpha_decided=int(self.alpha_decided), alpha_ms=float(self.alpha_ms),
                     gemm_ms=float(self.gemm_ms), gemm_launches=int(self.gemm_launches),
                     gemm_flop=float(self.gemm_flop), completion_ms=float(self.completion_ms),
+                    rechecked_fp64=int(self.rechecked_fp64),
                     level_boxes=list(self.level_boxes[:n]), level_safe=list(self.level_safe[:n]),
                     level_unsafe=list(self.level_unsafe[:n]), level_undecided=list(self.level_undecided[:n]))
 

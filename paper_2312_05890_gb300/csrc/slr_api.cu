@@ -84,6 +84,7 @@ struct slr_ctx {
     slr::NetParams<float> nf{};
     slr::NetParams<double> nd{};
     int T32 = 0, T64 = 0, NT32 = 0, NT64 = 0;
+    bool pairs_fit = false;   // the FP64 tile's footprint holds the float-float stage's planes
     size_t smem32 = 0, smem64 = 0;
     int grid32 = 0, grid64 = 0;
     int grid64c = 0;   // > 0: the FP64 re-check on clusters (grid of that many CTAs)
@@ -312,6 +313,17 @@ void layout_params(const Src *ctx, const HostLayers<Real> &L, unsigned char *dev
     for (int k = 1; k < K; ++k) p.Wt[k] = put(L.W[k]);
     for (int k = 1; k < K; ++k) p.Ws[k] = put(L.Ws[k]);
     p.fold_pad = L.fold_pad ? 1 : 0;
+    // hidden -> hidden: max_p sum_i |W[p][i]| (float64 sums of float weights, widened)
+    for (int k = 1; k + 1 < K; ++k) {
+        const int ni = p.n[k], no = p.n[k + 1];
+        double m = 0.0;
+        for (int q = 0; q < no; ++q) {
+            double a = 0.0;
+            for (int i = 0; i < ni; ++i) a += std::fabs((double)L.W[k][(size_t)i * no + q]);
+            m = std::max(m, a);
+        }
+        p.wabs[k] = m * (1.0 + 1e-12) + 1e-300;
+    }
     for (int k = 0; k < K; ++k) p.b[k] = put(L.b[k]);
     p.fold_err = put(L.fold_err);
     p.fold_berr = put(L.fold_berr);
@@ -332,15 +344,16 @@ struct TileChoice {
 };
 
 // Every (boxes per CTA, threads per CTA) the fused kernel can run this network with.
+// pairs (float64): with the planes of the float-float re-check stage.
 template <typename Real>
-std::vector<TileChoice> tile_candidates(const slr::NetParams<Real> &p) {
+std::vector<TileChoice> tile_candidates(const slr::NetParams<Real> &p, bool pairs = false) {
     std::vector<TileChoice> out;
     for (int NT : slr::kThreadCounts) {
         for (int T : slr::kTileSizes) {
             TileChoice c;
             c.T = T;
             c.NT = NT;
-            c.smem = slr::eval_smem_bytes<Real>(T, p.d, p.R, p.n_max_pad, p.n_in_max);
+            c.smem = slr::eval_smem_bytes<Real>(T, p.d, p.R, p.n_max_pad, p.n_in_max, pairs);
             if (c.smem > (size_t)kMaxSmem) continue;
             if (slr::eval_gemm_items(T, p.d, p.n_max_pad) > 2 * NT) continue;
             c.blocks = sizeof(Real) == 4 ? slr::eval_blocks_per_sm_f32(T, NT, c.smem,
@@ -848,29 +861,59 @@ int run_adjoint(slr_ctx *ctx, const slr::AdjArgs &a, int grid, int64_t *launches
     return SLR_OK;
 }
 
-// FP64 re-check of a list of boxes (pass 1): on clusters where chosen.
-cudaError_t launch_recheck(slr_ctx *ctx, const slr::BoxSource &src, const slr::EvalOutputs &out) {
+// FP64 re-check of a list of boxes at level t: on clusters where chosen (pass
+// 1); else, with recheck_pairs, the float-float stage (pass 2) lists the
+// boxes it leaves depending on E in the other re-check list, and pass 1
+// re-bounds those with plain FP64 products.  Returns the launches in *n.
+cudaError_t launch_recheck(slr_ctx *ctx, const slr::BoxSource &src, const slr::EvalOutputs &out, int t,
+                           int64_t *n) {
+    *n = 1;
     if (ctx->grid64c > 0)
         return slr::launch_eval_f64_cluster(ctx->T64, ctx->grid64c, ctx->smem64, ctx->stream, ctx->nd, src, out, 1);
+    if (ctx->opt.recheck_pairs && ctx->pairs_fit) {
+        int64_t *rest = src.index == ctx->near_list ? ctx->near_list2 : ctx->near_list;
+        slr::EvalOutputs oa = out;
+        oa.near_list = rest;
+        oa.near_count = &ctx->ctr->near3_n[t];
+        oa.near_cap = ctx->near_cap;
+        oa.tie_count = nullptr;
+        cudaError_t e =
+            slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, src, oa, 2);
+        if (e != cudaSuccess) return e;
+        slr::BoxSource sb = src;
+        sb.index = rest;
+        sb.index_count = &ctx->ctr->near3_n[t];
+        sb.cap = ctx->near_cap;
+        *n = 2;
+        return slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, sb, out, 1);
+    }
     return slr::launch_eval_f64(ctx->T64, ctx->NT64, ctx->grid64, ctx->smem64, ctx->stream, ctx->nd, src, out, 1);
 }
 
 // FP64 re-check: short lists, so the smallest tiles spread them over the
 // most SMs, with the most threads (a tile's products then split their inputs
 // over lane pairs: the per-level latency is what counts).  T64 = 0 when no
-// FP64 tile holds the network.
-void choose_recheck_tile(slr_ctx *ctx) {
-    std::vector<TileChoice> c64 = tile_candidates(ctx->nd);
+// FP64 tile holds the network.  The footprint includes the float-float
+// stage's planes where some tile holds them (pairs_fit), else not.
+std::vector<TileChoice> recheck_candidates(slr_ctx *ctx, bool pairs) {
+    std::vector<TileChoice> c64 = tile_candidates(ctx->nd, pairs);
     if (slr::eval_f64_pair_tile_ok(ctx->nd.d)) {
         TileChoice c;
         c.T = 2;
         c.NT = 256;
-        c.smem = slr::eval_smem_bytes<double>(2, ctx->nd.d, ctx->nd.R, ctx->nd.n_max_pad, ctx->nd.n_in_max);
+        c.smem = slr::eval_smem_bytes<double>(2, ctx->nd.d, ctx->nd.R, ctx->nd.n_max_pad, ctx->nd.n_in_max, pairs);
         if (c.smem <= (size_t)kMaxSmem && slr::eval_gemm_items(2, ctx->nd.d, ctx->nd.n_max_pad) <= 2 * 256) {
             c.blocks = slr::eval_blocks_per_sm_f64(2, 256, c.smem);
             if (c.blocks > 0) c64.push_back(c);
         }
     }
+    return c64;
+}
+
+void choose_recheck_tile(slr_ctx *ctx) {
+    std::vector<TileChoice> c64 = recheck_candidates(ctx, true);
+    ctx->pairs_fit = !c64.empty();
+    if (!ctx->pairs_fit) c64 = recheck_candidates(ctx, false);
     ctx->T64 = 0;
     for (const TileChoice &c : c64) {
         if (ctx->T64 == 0 || c.T < ctx->T64 || (c.T == ctx->T64 && c.NT > ctx->NT64)) {
@@ -913,6 +956,7 @@ int prepare_device(slr_ctx *ctx) {
     size_t off = 0;
     layout_params(ctx, Lf, (unsigned char *)ctx->net_buf, ctx->h_stage, off, ctx->nf);
     layout_params(ctx, Ld, (unsigned char *)ctx->net_buf, ctx->h_stage, off, ctx->nd);
+    for (int k = 1; k + 1 < ctx->K; ++k) ctx->nd.Wsf[k] = ctx->nf.Ws[k];
     std::memcpy(ctx->h_stage + off, ctx->C.data(), ctx->C.size() * sizeof(float));
     ctx->dC = reinterpret_cast<const float *>((unsigned char *)ctx->net_buf + off);
     off += c_bytes;
@@ -1167,6 +1211,7 @@ void slr_default_options(slr_options *opt) {
     opt->alpha_lr = 0.1f;
     opt->alpha_cap = (int64_t)1 << 16;
     opt->alpha_margin = 0.2f;
+    opt->recheck_pairs = 1;
     opt->tile_boxes = 0;
     opt->tile_threads = 0;
     opt->wide = 0;
@@ -1277,6 +1322,8 @@ int slr_set_options(slr_ctx *ctx, const slr_options *opt) {
     }
     if (opt->recheck_cluster != 0 && opt->recheck_cluster != 1)
         return fail(ctx, SLR_EINVAL, "recheck_cluster must be 0 or 1");
+    if (opt->recheck_pairs != 0 && opt->recheck_pairs != 1)
+        return fail(ctx, SLR_EINVAL, "recheck_pairs must be 0 or 1");
     if (opt->shard_count < 1 || opt->shard_index < 0 || opt->shard_index >= opt->shard_count ||
         opt->shard_level < 0 || opt->shard_level > slr::kMaxDepth)
         return fail(ctx, SLR_EINVAL, "shard %d of %d at level %d is not valid", opt->shard_index, opt->shard_count,
@@ -1547,8 +1594,9 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
                 o2.cls = ctx->cls;
                 o2.tie_count = &ctx->ctr->ties;
                 o2.status = ctx->status;
-                CK(ctx, launch_recheck(ctx, s2, o2));
-                ++launches;
+                int64_t nl = 0;
+                CK(ctx, launch_recheck(ctx, s2, o2, t, &nl));
+                launches += nl;
             }
         } else if (use_tc) {
             // tier 1 on the tensor cores; boxes whose class depends on its
@@ -1576,8 +1624,9 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
                 o2.cls = ctx->cls;
                 o2.tie_count = &ctx->ctr->ties;
                 o2.status = ctx->status;
-                CK(ctx, launch_recheck(ctx, s2, o2));
-                ++launches;
+                int64_t nl = 0;
+                CK(ctx, launch_recheck(ctx, s2, o2, t, &nl));
+                launches += nl;
             }
         } else {
         CK(ctx, slr::launch_eval_f32(ctx->T32, ctx->NT32, ctx->grid32, ctx->smem32, ctx->stream, ctx->nf, src, o, 0));
@@ -1592,8 +1641,9 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
             o2.cls = ctx->cls;
             o2.tie_count = &ctx->ctr->ties;
             o2.status = ctx->status;
-            CK(ctx, launch_recheck(ctx, s2, o2));
-            ++launches;
+            int64_t nl = 0;
+            CK(ctx, launch_recheck(ctx, s2, o2, t, &nl));
+            launches += nl;
         }
         }
         CK(ctx, mark(t, 2));
@@ -1690,9 +1740,10 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
     out->tie_leaves = c.ties;
     out->depth = D;
     int levels = 0;
-    unsigned long long rech = 0, rech2 = 0;
+    unsigned long long rech = 0, rech2 = 0, rech3 = 0;
     for (int t = 0; t <= D; ++t) {
         rech2 += std::min<unsigned long long>(c.near2_n[t], (unsigned long long)ctx->near_cap);
+        rech3 += std::min<unsigned long long>(c.near3_n[t], (unsigned long long)ctx->near_cap);
         out->level_boxes[t] = c.level_boxes[t];
         out->level_safe[t] = c.level_safe[t];
         out->level_unsafe[t] = c.level_unsafe[t];
@@ -1702,6 +1753,7 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
     }
     out->rechecked = recheck ? (use_tc ? rech2 : rech) : 0;
     out->rechecked_fp32 = use_tc ? rech : 0;
+    out->rechecked_fp64 = (ctx->opt.recheck_pairs && ctx->pairs_fit && ctx->grid64c == 0) ? rech3 : out->rechecked;
     out->levels = levels;
     out->device_ms = ms;
     out->launches = launches;
@@ -2449,6 +2501,7 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
         for (int i = 0; i < P; ++i) {
             layout_params(&ph[i], Lf[i], A, bs->h_upload, woff, n32[i]);
             layout_params(&ph[i], Ld[i], A, bs->h_upload, woff, n64[i]);
+            for (int k = 1; k + 1 < n64[i].K; ++k) n64[i].Wsf[k] = n32[i].Ws[k];
             for (slr::BatchShape *sh : {&sh32, &sh64}) {
                 sh->nmp = std::max(sh->nmp, n32[i].n_max_pad);
                 sh->d = std::max(sh->d, n32[i].d);
@@ -2647,6 +2700,7 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
         for (int i = 0; i < P; ++i) {
             layout_params(&ph[i], Lf[i], A, bs->h_upload, woff, n32[i]);
             layout_params(&ph[i], Ld[i], A, bs->h_upload, woff, n64[i]);
+            for (int k = 1; k + 1 < n64[i].K; ++k) n64[i].Wsf[k] = n32[i].Ws[k];
         }
         const size_t o_n32 = al(wbytes);
         const size_t o_n64 = o_n32 + al((size_t)P * sizeof(slr::NetParams<float>));
@@ -2715,6 +2769,7 @@ int count_batch_sorted(slr_ctx *ctx, int n, const slr_problem *problems, slr_res
             if (c.level_boxes[t]) out.levels = t + 1;
         }
         out.rechecked = recheck ? rech : 0;
+        out.rechecked_fp64 = out.rechecked;
         out.device_ms = ms;              // the whole batch
         out.launches = bs->launches;
         out.h2d_bytes = (int64_t)bs->upload_bytes;

@@ -128,6 +128,11 @@ struct NetParams {
     const Real *Ws[kMaxLayers];  // layer k >= 1, the tile's shared-memory image of Wt[k]:
                                  // n[k] x Mpad_k, Mpad_k = n[k+1] rounded up to 8, padding 0
     int fold_pad;                // 1: Ws[K-1] holds fold_err[p][i] in column n[K] + p
+    // float64 tile, hidden -> hidden layers k (1 <= k < K-1): the same weights
+    // as float (exact: the network's weights are float32), for the re-check's
+    // float-float products, and wabs[k] >= max_p sum_i |W_k[p][i]|
+    const float *Wsf[kMaxLayers];
+    double wabs[kMaxLayers];
     const Real *b[kMaxLayers];   // biases, b[K-1] folded
     const Real *fold_err;        // R x n[K-1]: bound on |W'_fp - C W_K|
     const Real *fold_berr;       // R:          bound on |b'_fp - (C b_K + e)|
@@ -195,6 +200,7 @@ struct LevelCounters {
     unsigned long long frontier_n[kMaxDepth + 2];   // boxes at each level
     unsigned long long near_n[kMaxDepth + 2];       // re-check list length at each level
     unsigned long long near2_n[kMaxDepth + 2];      // second re-check list (tensor-core path)
+    unsigned long long near3_n[kMaxDepth + 2];      // boxes the float-float re-check left to plain FP64
     unsigned int block_count[kCompactBlocks];       // order-preserving compaction: per-block undecided
 };
 
@@ -220,9 +226,15 @@ __host__ __device__ inline int eval_gemm_items(int T, int d, int n_max_pad) {
     return (n_max_pad / 8) * ((2 * d + 4) * T / 4);
 }
 
-// Shared-memory footprint of the fused evaluation kernel for a tile of T boxes.
+// Row stride (floats) of the float64 tile's float-float planes: NS rounded up
+// to 4, so that every row starts on 16 bytes.
+__host__ __device__ inline int eval_plane_stride(int T, int d) { return (state_stride(T, d) + 3) & ~3; }
+
+// Shared-memory footprint of the fused evaluation kernel for a tile of T boxes;
+// `pairs` (float64): with the planes of the float-float re-check stage.
 template <typename Real>
-__host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max_pad, int n_in_max) {
+__host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max_pad, int n_in_max,
+                                                  bool pairs = false) {
     const int NS = state_stride(T, d);
     size_t s = 0;
     s += (size_t)n_max_pad * NS * sizeof(Real);            // state, updated in place
@@ -233,7 +245,16 @@ __host__ __device__ inline size_t eval_smem_bytes(int T, int d, int R, int n_max
     s += 3 * (size_t)T * R * sizeof(Real);                 // row lo / hi / E
     s += (size_t)T * sizeof(int64_t);                      // box indices
     s += (size_t)n_max_pad * (sizeof(int2) + 2 * sizeof(int)) + 16;   // live-row list, indices, flags, length
-    return (s + 15) & ~(size_t)15;
+    s = (s + 15) & ~(size_t)15;
+    // float64: the state split into float hi and lo planes for the float-float products
+    if (sizeof(Real) == 8 && pairs) s += 2 * (size_t)n_max_pad * eval_plane_stride(T, d) * sizeof(float);
+    return s;
+}
+
+// Offset of the float-float planes in the float64 tile's shared memory (they
+// follow everything else).
+__host__ __device__ inline size_t eval_split_offset(int T, int d, int R, int n_max_pad, int n_in_max) {
+    return eval_smem_bytes<double>(T, d, R, n_max_pad, n_in_max, false);
 }
 
 }  // namespace slr

@@ -65,13 +65,18 @@ __device__ __forceinline__ void st_cluster4(uint32_t addr, const double (&v)[4])
 }
 
 // Four consecutive values from shared memory at a 32-bit shared address.
+// volatile: the asm names no memory operand, so without it the compiler could
+// move these loads across the block barriers and cp.async waits that order
+// them after the stores they read.
 template <typename Real> __device__ __forceinline__ void lds4(uint32_t addr, Real (&v)[4]);
 template <> __device__ __forceinline__ void lds4<float>(uint32_t addr, float (&v)[4]) {
-    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(addr));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(addr));
 }
 template <> __device__ __forceinline__ void lds4<double>(uint32_t addr, double (&v)[4]) {
-    asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(addr));
-    asm("ld.shared.v2.f64 {%0, %1}, [%2+16];" : "=d"(v[2]), "=d"(v[3]) : "r"(addr));
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(addr));
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2+16];" : "=d"(v[2]), "=d"(v[3]) : "r"(addr));
 }
 
 template <typename Real> struct V4;
@@ -193,6 +198,40 @@ __device__ __forceinline__ Real gam(int n) {
 template <typename Real>
 __device__ __forceinline__ Real uerr(Real x) {
     return Arith<Real>::mul_up(x, (Real)0.50001 * Arith<Real>::ulp2);
+}
+
+// Relative rounding bound of an n-term float-float dot product sum_i w_i x_i
+// (w_i float, x_i float64 split into float hi + lo, products exact by
+// TwoProduct, hi parts added by TwoSum, the error terms and w_i lo_i summed
+// in float; Ogita, Rump and Oishi, "Accurate sum and dot product", 2005:
+// gamma_n^2 sum |w_i x_i|, taken here with a factor 4 and n + 2 terms for the
+// lo products and the combination of partial sums), plus the split of the
+// inputs (2^-48 relative) and the rounding of hi + lo to float64 (2^-53),
+// rounded upward.  The underflow of these float operations is bounded apart
+// (ff_abs).
+__device__ __forceinline__ double gam_ff(int n) {
+    const double g = (double)(n + 4) * 0x1p-24;     // >= gamma_{n+2} in float
+    const double gn = (double)(n + 2) * 0x1p-24;    // >= gamma_n
+    return __dadd_ru(__dmul_ru(__dmul_ru(4.0 * g, g), 1.0 + gn), 0x1p-47);
+}
+
+// Absolute bound of what the float-float products lose to underflow in one
+// bound of a row: every split input and float operation loses at most 2^-150,
+// times the row's weight magnitude (wabs >= sum_i |w_i|) or once per term,
+// over the 2d + 3 product columns a bound reads (taken as 2d + 8, doubled).
+__device__ __forceinline__ double ff_abs(double wabs, int n, int d) {
+    return __dmul_ru((double)(2 * d + 8) * 0x1p-149, __dadd_ru(wabs, (double)(2 * n + 8)));
+}
+
+// Multiply-add of a float weight and a float-float input into a float-float
+// accumulator (s, e): the product exactly as p + pe, p added to s by TwoSum,
+// the error terms and w lo added to e in float.
+__device__ __forceinline__ void ff_mac(float w, float h, float l, float &s, float &e) {
+    float p, pe, t, se;
+    two_prod<float>(w, h, p, pe);
+    two_sum<float>(s, p, t, se);
+    s = t;
+    e = __fmaf_rn(w, l, __fadd_rn(e, __fadd_rn(pe, se)));
 }
 
 // Row accessors.  A row view R maps a column of one row (SIMT numbering: C
@@ -416,9 +455,11 @@ struct EvalTile {
     }
 
     // kList: sum only over the input rows ridx[0 .. n_rows) (the others are
-    // zero in every box of the tile); else over all n_in rows.
-    template <bool kList = false, class L>
-    static __device__ __forceinline__ void const_item(const L &lay, Real *sConst, const Real *sW, int Mpad,
+    // zero in every box of the tile); else over all n_in rows.  WT: the type
+    // of the staged weights (float for the float64 tile's float-float
+    // products; exact either way).
+    template <bool kList = false, class L, class WT>
+    static __device__ __forceinline__ void const_item(const L &lay, Real *sConst, const WT *sW, int Mpad,
                                                       const NetParams<Real> &net, int layer, int item,
                                                       const int *ridx = nullptr, int n_rows = 0) {
         const int d = dim_of(net);
@@ -441,8 +482,8 @@ struct EvalTile {
                 const auto Ri = lay.row(i, b);
                 const Real h = Ri(cCh(d));
                 const Real l = Ri(cCl(d));
-                const Real w0 = sW[i * Mpad + p0];
-                const Real w1 = sW[i * Mpad + p0 + 1];
+                const Real w0 = (Real)sW[i * Mpad + p0];
+                const Real w1 = (Real)sW[i * Mpad + p0 + 1];
                 if (kCompensated) {
                     Real p1, pe, t, se;
                     two_prod<Real>(w0, h, p1, pe);
@@ -495,10 +536,12 @@ struct EvalTile {
     // columns (gamma_n * sum_i |W_pi| N_i, from the |W| N column).
     // With `delta`, the constant is the reference box's (slot b = 0 of sConst)
     // plus the product W delta the contraction left in the constant column.
+    // gabs: an absolute bound the products lose beyond gcoef (float-float
+    // products: underflow, ff_abs), else 0.
     template <class Row>
     static __device__ __forceinline__ void finish_contraction(const Row &R, const Real *sConst, int nmp, int p, int b,
                                                               int d, int n_in, Real gcoef, Real &chi, Real &clo,
-                                                              Real &E, bool delta = false) {
+                                                              Real &E, bool delta = false, Real gabs = 0) {
         Real cerr;
         if (delta) {
             const Real ch = sConst[p * T], cl = sConst[(nmp + p) * T];
@@ -519,7 +562,7 @@ struct EvalTile {
         }
         const Real wN = R(cN(d));
         Real eps = A::mul_up(gcoef, A::mul_up(wN, (Real)1 + gcoef));
-        eps = A::add_up(A::add_up(eps, cerr), (Real)(n_in + 4) * A::tiny);
+        eps = A::add_up(A::add_up(eps, cerr), A::add_up((Real)(n_in + 4) * A::tiny, gabs));
         // |W| E was summed from non-negative terms with the same relative rounding
         E = A::add_up(A::mul_up(R(cE(d)), (Real)1 + (Real)2 * gcoef), eps);
     }
@@ -790,7 +833,7 @@ struct EvalTile {
     static __device__ void hidden_epilogue(const L &lay, const Real *sConst, const NetParams<Real> &net, int layer,
                                            Real gcoef, const float *alpha = nullptr, int64_t alpha_ld = 0,
                                            int64_t base = 0, int64_t n = 0, int alpha_off = 0, bool delta = false,
-                                           int *live = nullptr) {
+                                           int *live = nullptr, Real gabs = 0) {
         const int d = dim_of(net);
         const int nrows = net.n[layer];
         const int n_in = net.n[layer - 1];
@@ -800,7 +843,7 @@ struct EvalTile {
             const auto R = lay.row(p, b);
             Real chi, clo, E;
             if (layer > 1) {
-                finish_contraction(R, sConst, net.n_max_pad, p, b, d, n_in, gcoef, chi, clo, E, delta);
+                finish_contraction(R, sConst, net.n_max_pad, p, b, d, n_in, gcoef, chi, clo, E, delta, gabs);
             } else {
                 chi = R(cCh(d));
                 clo = R(cCl(d));
@@ -1099,6 +1142,150 @@ struct EvalTile {
         }
     }
 
+    // ---- float64 tile: hidden -> hidden products as float-float pairs -----------
+    // The float64 pipes are a small fraction of the float32 ones; the
+    // products, most of a layer's float64 work, run on the float32 pipes
+    // instead: every input x of the state is split into float hi + lo
+    // (x - hi is exact, lo = fl(x - hi): |x - hi - lo| <= 2^-48 |x| + 2^-150),
+    // each term w hi is formed exactly, and the sums carry a float error term
+    // (ff_mac).  The result hi + lo, rounded to float64, is within
+    // gam_ff(n) sum_i |w_i| |x_i| + ff_abs of the exact product: the
+    // contraction's rounding bound that the next epilogue takes in place of
+    // gamma_n.
+
+    // The state's product columns (0 .. 2d + 3) of rows 0 .. n_in - 1 as planes
+    // of row stride NP (eval_plane_stride: rows on 16 bytes).
+    static __device__ void split_state(const Real *S, float *Xh, float *Xl, int n_in, int NS, int NP, int d) {
+        const int per = (2 * d + 4) * T;
+        for (int item = threadIdx.x; item < n_in * per; item += NT) {
+            const int i = item / per;
+            const int j = item - i * per;
+            const double x = (double)S[i * NS + j];
+            const float h = __double2float_rn(x);
+            Xh[i * NP + j] = h;
+            Xl[i * NP + j] = __double2float_rn(__dsub_rn(x, (double)h));
+        }
+    }
+
+    // An 8 x 4 product tile over the input rows ridx[0 .. n_rows) (see
+    // tile_mac_rows): float weights of row stride Mpad, planes of stride NP.
+    static __device__ __forceinline__ void tile_mac_rows_ff(const float *wp, const float *xh, const float *xl,
+                                                            const int *ridx, int n_rows, int Mpad, int NP,
+                                                            bool is_abs, float (&sh)[8][4], float (&sl)[8][4]) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[r][c] = sl[r][c] = 0.f;
+        const uint32_t w0 = (uint32_t)__cvta_generic_to_shared(wp);
+        const uint32_t h0 = (uint32_t)__cvta_generic_to_shared(xh), l0 = (uint32_t)__cvta_generic_to_shared(xl);
+        for (int ii = 0; ii < n_rows; ++ii) {
+            const uint32_t i = (uint32_t)ridx[ii];
+            const uint32_t ow = i * (uint32_t)(Mpad * 4), ox = i * (uint32_t)(NP * 4);
+            float a0[4], a1[4], h[4], l[4];
+            lds4<float>(w0 + ow, a0);
+            lds4<float>(w0 + ow + 16u, a1);
+            lds4<float>(h0 + ox, h);
+            lds4<float>(l0 + ox, l);
+            if (is_abs) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    a0[r] = fabsf(a0[r]);
+                    a1[r] = fabsf(a1[r]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    ff_mac(a0[r], h[c], l[c], sh[r][c], sl[r][c]);
+                    ff_mac(a1[r], h[c], l[c], sh[r + 4][c], sl[r + 4][c]);
+                }
+        }
+    }
+
+    // hi + lo of a finished tile into the state, all but the constant column
+    // (its product is not used; the constants' items read that column of the
+    // input rows during this phase, so it is left alone).
+    static __device__ __forceinline__ void store_ff(Real *S, int g, int j0, int d, int NS, const float (&sh)[8][4],
+                                                    const float (&sl)[8][4]) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + c;
+            if (j / T == d) continue;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) S[(g * 8 + r) * NS + j] = (Real)__dadd_rn((double)sh[r][c], (double)sl[r][c]);
+        }
+    }
+
+    // The phase of contract() with float-float products.  No product reads
+    // the state (they read the planes), so each tile is stored as soon as it
+    // is done; the constants (float64, as in contract) read the constant
+    // columns, which no tile writes.
+    template <class L>
+    static __device__ void contract_ff(const L &lay, Real *sConst, const NetParams<Real> &net, int layer, Real *S,
+                                       const float *sWf, const float *Xh, const float *Xl, int n_in, int Mpad,
+                                       int d, int NS, int NP, uint32_t rW, uint32_t rA, const int *ridx,
+                                       int n_rows) {
+        const int QW = (d + 1) * T / 4;
+        const int QA = (d + 3) * T / 4;
+        const int Q = QW + QA;
+        const int G = Mpad / 8;
+        const int total = G * Q;
+        const int n_const = ((net.n[layer + 1] + 1) / 2) * T;
+        const int parts = (4 * total <= NT && n_in >= 16) ? 4 : ((2 * total <= NT && n_in >= 8) ? 2 : 1);
+        const int busy = parts * total;
+        float sh[8][4], sl[8][4];
+        if (parts > 1) {
+            const int item = (int)threadIdx.x / parts, part = (int)threadIdx.x % parts;
+            int g = 0, q = 0, j0 = 0;
+            if (item < total) {
+                item_tile(item, G, QW, QA, rW, rA, g, q);
+                const bool is_abs = q >= QW;
+                j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
+                const int i0 = part * n_rows / parts, i1 = (part + 1) * n_rows / parts;
+                tile_mac_rows_ff(sWf + g * 8, Xh + j0, Xl + j0, ridx + i0, i1 - i0, Mpad, NP, is_abs, sh, sl);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) sh[r][c] = sl[r][c] = 0.f;
+            }
+            // the parts' pairs added by TwoSum, in a fixed order
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    for (int m = 1; m < parts; m <<= 1) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, sh[r][c], m);
+                        const float ol = __shfl_xor_sync(0xffffffffu, sl[r][c], m);
+                        float t, se;
+                        two_sum<float>(sh[r][c], oh, t, se);
+                        sh[r][c] = t;
+                        sl[r][c] = __fadd_rn(sl[r][c], __fadd_rn(ol, se));
+                    }
+                }
+            if (item < total && part == 0) store_ff(S, g, j0, d, NS, sh, sl);
+        } else {
+#pragma unroll 1
+            for (int it = 0; it < kItems; ++it) {
+                const int item = threadIdx.x + it * NT;
+                if (item < total) {
+                    int g, q;
+                    item_tile(item, G, QW, QA, rW, rA, g, q);
+                    const bool is_abs = q >= QW;
+                    const int j0 = is_abs ? (d + 1) * T + (q - QW) * 4 : q * 4;
+                    tile_mac_rows_ff(sWf + g * 8, Xh + j0, Xl + j0, ridx, n_rows, Mpad, NP, is_abs, sh, sl);
+                    store_ff(S, g, j0, d, NS, sh, sl);
+                }
+            }
+        }
+        {
+            int idx = threadIdx.x + ((busy - (int)threadIdx.x + NT - 1) / NT) * NT;
+            if (idx < busy) idx += NT;
+            for (; idx < busy + n_const; idx += NT) const_item<true>(lay, sConst, sWf, Mpad, net, layer, idx - busy, ridx, n_rows);
+        }
+    }
+
     // ---- the same phase split over the CL CTAs of a thread-block cluster (float64) ----
     // Every CTA of the cluster holds the tile's whole state and does the
     // per-row work itself; the product tiles and the constant items are dealt
@@ -1181,8 +1368,9 @@ struct EvalTile {
     // threads, L2 only.  The epilogue runs while they land; stage_wait, then
     // a block barrier, make sW readable.  n_in Mpad sizeof(Real) is a multiple
     // of 32 bytes (Mpad of 8), and both ends are 16-byte aligned.
-    static __device__ __forceinline__ void stage_weights_async(Real *sW, const Real *Ws, int n_in, int Mpad) {
-        const int pieces = n_in * Mpad * (int)sizeof(Real) / 16;
+    template <typename W>
+    static __device__ __forceinline__ void stage_weights_async(void *sW, const W *Ws, int n_in, int Mpad) {
+        const int pieces = n_in * Mpad * (int)sizeof(W) / 16;
         const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(sW);
         const char *g0 = reinterpret_cast<const char *>(Ws);
         for (int c = threadIdx.x; c < pieces; c += NT) {
@@ -1275,12 +1463,19 @@ struct TileSmem {
     int *sRowIdx;   // the same rows' indices i
     int *sLive;     // per row: not identically zero in some box of the tile
     int *sNRows;    // length of sRows
+    float *sXh, *sXl;   // float64 tile: the state as float hi + lo planes (allocated where
+                        // pass 2 runs: the single-problem kernel with that footprint)
 };
 
 template <typename Real, int T>
 __device__ __forceinline__ TileSmem<Real> carve_smem(unsigned char *sp, int nmp, int d, int n_in_max, int R) {
     TileSmem<Real> m;
     const int NS = state_stride(T, d);
+    m.sXh = m.sXl = nullptr;
+    if (sizeof(Real) == 8) {
+        m.sXh = reinterpret_cast<float *>(sp + eval_split_offset(T, d, R, nmp, n_in_max));
+        m.sXl = m.sXh + (size_t)nmp * eval_plane_stride(T, d);
+    }
     m.sS = reinterpret_cast<Real *>(sp);
     sp += (size_t)nmp * NS * sizeof(Real);
     m.sConst = reinterpret_cast<Real *>(sp);
@@ -1329,10 +1524,13 @@ __device__ __forceinline__ int64_t source_count(const BoxSource &src) {
 // One tile: boxes base .. base + T - 1 of the source (n boxes in all).
 // pass 0: working precision; writes the sound class and lists the undecided
 //         boxes whose class depends on E (their optimistic class differs);
+// pass 2: float64 with float-float hidden products (see contract_ff): writes
+//         the class and lists the boxes whose class still depends on E;
 // pass 1: re-check of such a list in the higher precision (writes the class,
 //         counts the boxes still depending on E as ties).
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int NT, int KI = 2, int CL = 1, int DC = 0>
+// kPairs: pass 2 is compiled in (the single-problem float64 kernel).
+template <typename Real, int T, int NT, int KI = 2, int CL = 1, int DC = 0, bool kPairs = false>
 __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, const EvalOutputs &out, const int pass,
                           const TileSmem<Real> &sm, const int64_t base, const int64_t n) {
     using A = Arith<Real>;
@@ -1392,6 +1590,8 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
     const uint32_t rW = Tile::recip32((d + 1) * T / 4), rA = Tile::recip32((d + 3) * T / 4);
     int alpha_off = 0;
     bool pdelta = false;
+    // rounding bound of the last contraction (relative, absolute)
+    Real gprev = gam<Real>(net.n[0]), aprev = 0;
     for (int k = 1; k < net.K; ++k) {
         // the tile's products sum over a list of input rows: only the rows
         // that are not zero in every box of the tile (inactive ReLUs with no
@@ -1404,11 +1604,14 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         // fold's error bounds in its padding columns (at most 4 property rows)
         const bool pk = dconst && !lk && net.fold_pad != 0;
         const bool dk = dconst && (lk || pk);
+        // float64 tile, pass 2: hidden -> hidden products as float-float pairs
+        const bool ffk = kPairs && sizeof(Real) == 8 && CL == 1 && pass == 2 && lk;
         // sW is free (the last product ended with a barrier): its next image
         // lands while the epilogue runs
-        Tile::stage_weights_async(sW, net.Ws[k], net.n[k], Mpad);
-        Tile::hidden_epilogue(lay, sConst, net, k, gam<Real>(net.n[k - 1]), src.alpha, src.alpha_ld, base, n,
-                              alpha_off, dconst, CL == 1 ? sm.sLive : nullptr);
+        if (ffk) Tile::stage_weights_async(sW, net.Wsf[k], net.n[k], Mpad);
+        else Tile::stage_weights_async(sW, net.Ws[k], net.n[k], Mpad);
+        Tile::hidden_epilogue(lay, sConst, net, k, gprev, src.alpha, src.alpha_ld, base, n, alpha_off, dconst,
+                              CL == 1 ? sm.sLive : nullptr, aprev);
         alpha_off += net.n[k];
         Tile::stage_wait();
         pdelta = pk;
@@ -1433,6 +1636,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
                 if (lane == 0) *sm.sNRows = count;
             }
             if (dk) Tile::delta_prep(lay, sm.sRef, net, k);
+            if (ffk) Tile::split_state(sS, sm.sXh, sm.sXl, net.n[k], NS, eval_plane_stride(T, d), d);
         }
         __syncthreads();
         // constants and products; barrier inside, then the in-place store
@@ -1440,8 +1644,19 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
             static_assert(!Tile::kCompensated, "the cluster tile is the float64 re-check's");
             Tile::template contract_cluster<CL>(lay, sConst, net, k, sS, sW, net.n[k], Mpad, d, NS, rW, rA);
         } else {
-            Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA, sm.sRows,
-                           sm.sRowIdx, *sm.sNRows);
+            if (ffk) {
+                Tile::contract_ff(lay, sConst, net, k, sS, reinterpret_cast<const float *>(sW), sm.sXh, sm.sXl,
+                                  net.n[k], Mpad, d, NS, eval_plane_stride(T, d), rW, rA, sm.sRowIdx, *sm.sNRows);
+            } else {
+                Tile::contract(lay, sConst, sm.sRef, net, k, sS, sW, net.n[k], Mpad, d, NS, dk, rW, rA, sm.sRows,
+                               sm.sRowIdx, *sm.sNRows);
+            }
+        }
+        if constexpr (sizeof(Real) == 8) {
+            gprev = ffk ? (Real)gam_ff(net.n[k]) : gam<Real>(net.n[k]);
+            aprev = ffk ? (Real)ff_abs(net.wabs[k], net.n[k], d) : (Real)0;
+        } else {
+            gprev = gam<Real>(net.n[k]);
         }
         __syncthreads();
     }
@@ -1468,7 +1683,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
             for (int r = 0; r < R; ++r) out.row_err[oidx * R + r] = to_hi<Real>(sErr[r * T + b]);
         }
         if (near) {
-            if (pass == 0 && out.near_list != nullptr) {
+            if ((pass == 0 || pass == 2) && out.near_list != nullptr) {
                 const unsigned long long pos = atomicAdd(out.near_count, 1ull);
                 if ((int64_t)pos < out.near_cap) {
                     out.near_list[pos] = idx;
@@ -1502,7 +1717,7 @@ slr_eval_kernel(const NetParams<Real> net, const BoxSource src, const EvalOutput
         carve_smem<Real, T>(smem_raw, net.n_max_pad, DC > 0 ? DC : net.d, net.n_in_max, net.R);
     const int64_t n = source_count(src);
     for (int64_t base = (int64_t)blockIdx.x * T; base < n; base += (int64_t)gridDim.x * T)
-        eval_tile<Real, T, NT, KI, 1, DC>(net, src, out, pass, sm, base, n);
+        eval_tile<Real, T, NT, KI, 1, DC, sizeof(Real) == 8>(net, src, out, pass, sm, base, n);
 }
 
 // The float64 re-check with each tile on a cluster of kRecheckCluster CTAs (one

@@ -182,6 +182,7 @@ extern "C" int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out) {
         if (c.level_boxes[t]) out->levels = t + 1;
     }
     out->rechecked = recheck ? rech : 0;
+    out->rechecked_fp64 = out->rechecked;
     out->device_ms = ms;
     out->launches = launches;
     out->h2d_bytes = (int64_t)(2 * d * sizeof(double) + d * sizeof(unsigned long long));

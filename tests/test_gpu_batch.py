@@ -106,3 +106,19 @@ def test_batch_with_wide_members(pkg):
             assert (g["unsafe_lo"], g["unsafe_hi"]) == (w.unsafe_lo, w.unsafe_hi), p.name
         else:
             assert g["unsafe_lo"] <= w.unsafe_lo <= w.unsafe_hi <= g["unsafe_hi"], p.name
+
+
+def test_batch_rechecks_beside_wide_members(pkg):
+    """A problem whose every level needs the FP64 re-check, batched with the
+    widest members of the mixed batch: the batch's FP64 tile must hold the
+    largest shape, and the re-checked problem still equals its single count."""
+    from .test_gpu_parity import _margin_at_a_corner
+    corner = _margin_at_a_corner()
+    probs, depths = _mixed()
+    probs, depths = [corner] + probs[8:], [corner.depth] + depths[8:]
+    with pkg.Counter(0) as c:
+        got = c.count_batch(probs, depths)
+    assert got[0]["rechecked"] > 0 and got[0]["tie_leaves"] == 0
+    want = _single(pkg, corner, corner.depth)
+    for k in KEYS:
+        assert got[0][k] == want[k], k
