@@ -809,7 +809,13 @@ struct EvalTile {
         RowBounds<Real> bd;
         bd.compute(R, d, chi, clo);
         const RelaxPlan<Real> pl = plan_row(bd, d, relax_mode, chi, clo, R(cr + d), E, a_ptr, act);
-        if (pl.kind != 0) {
+        if (pl.kind == 1) {
+            // a constant row: the coefficients are zeros, nothing to read
+            for (int j = 0; j < d; ++j) {
+                R(j) = 0;
+                R(cr + j) = 0;
+            }
+        } else if (pl.kind == 2) {
             for (int j = 0; j < d; ++j) {
                 Real c = R(j), r = R(cr + j);
                 apply_plan(pl, c, r);
@@ -869,14 +875,18 @@ struct EvalTile {
     // rounding of delta joins the row's E, and |delta| its magnitude N (the
     // product's rounding is bounded by gamma |W| N).  Box 0's own constant
     // column is left unchanged and ignored after the product.
+    // `live` (nullable): rows with live[i] == 0 are zero in every box and are
+    // left out of every sum of the next product, so they are skipped here.
     template <class L>
-    static __device__ void delta_prep(const L &lay, Real *sRef, const NetParams<Real> &net, int layer) {
+    static __device__ void delta_prep(const L &lay, Real *sRef, const NetParams<Real> &net, int layer,
+                                      const int *live = nullptr) {
         const int d = dim_of(net);
         const int n_in = net.n[layer];
         const int nmp = net.n_max_pad;
         for (int item = threadIdx.x; item < n_in * T; item += NT) {
             const int i = item / T;
             const int b = item - i * T;
+            if (live != nullptr && live[i] == 0) continue;
             const auto Rb = lay.row(i, b);
             const auto R0 = lay.row(i, 0);
             const Real hr = R0(cCh(d)), lr = R0(cCl(d));
@@ -1618,7 +1628,7 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
         if (CL == 1) {
             __syncthreads();
             if (threadIdx.x < 32) {
-                // the live rows in order; the flags reset for the next layer
+                // the live rows in order (the flags are cleared in the product phase)
                 const int lane = threadIdx.x;
                 int count = 0;
                 for (int i0 = 0; i0 < net.n[k]; i0 += 32) {
@@ -1630,15 +1640,17 @@ __device__ void eval_tile(const NetParams<Real> &net, const BoxSource &src, cons
                         sm.sRows[at] = make_int2(i * Mpad * (int)sizeof(Real), i * NS * (int)sizeof(Real));
                         sm.sRowIdx[at] = i;
                     }
-                    if (i < net.n[k]) sm.sLive[i] = 0;
                     count += __popc(bal);
                 }
                 if (lane == 0) *sm.sNRows = count;
             }
-            if (dk) Tile::delta_prep(lay, sm.sRef, net, k);
+            if (dk) Tile::delta_prep(lay, sm.sRef, net, k, sm.sLive);
             if (ffk) Tile::split_state(sS, sm.sXh, sm.sXl, net.n[k], NS, eval_plane_stride(T, d), d);
         }
         __syncthreads();
+        // the flags for the next layer's epilogue (read above, before the barrier)
+        if (CL == 1)
+            for (int i = threadIdx.x; i < net.n[k]; i += NT) sm.sLive[i] = 0;
         // constants and products; barrier inside, then the in-place store
         if constexpr (CL > 1) {
             static_assert(!Tile::kCompensated, "the cluster tile is the float64 re-check's");
