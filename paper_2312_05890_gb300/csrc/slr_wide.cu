@@ -109,12 +109,20 @@ constexpr int kRowsX = 32, kSlicesY = 16;
 
 // Layer 1: C = [W_1 diag(r) | W_1 m + b_1], R = 0 (Sec. 3), then its ReLU
 // relaxation when it is a hidden layer.  W0t: W_1 transposed (d x n_1).
+// The coefficients c_j = W_1[p][j] r_j are formed twice, bit for bit the same:
+// for the concrete bounds, then, once the plan is known, to be stored as
+// relaxed (one write per value).  The constant's terms W_1[p][j] m_j are
+// summed in the slices' share (error-free products, compensated sums), and
+// the 16 partial pairs added by TwoSum with their error terms in float: a
+// summation tree whose partial sums add up to no more than the sequential
+// chain's, so the chain's bound 2 gamma_{d+2}^2 (1 + gamma_d) sum |p_j| holds.
 __global__ void __launch_bounds__(kRowsX * kSlicesY)
 wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const float *mh, const float *ml,
                  const float *rr, float *C, float *Rr, float *Ch, float *Cl, const float *alpha, int64_t alpha_ld,
                  int64_t base) {
     using A = Arith<float>;
     __shared__ RowBounds<float> part[kSlicesY][kRowsX];
+    __shared__ float cpart[3][kSlicesY][kRowsX];
     __shared__ RelaxPlan<float> plan[kRowsX];
     const int d = net.d;
     const int n1 = net.n[1];
@@ -124,33 +132,42 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
     const bool live = p < n1;
     const WideRow R{C, Rr, Ch, Cl, b, live ? p : 0, d, NP};
     const float *rb = rr + b * d;
+    const float *mb = mh + b * d, *lb = ml + b * d;
     RowBounds<float> bd;
     bd.reset();
+    float s = 0.f, e = 0.f, sabs = 0.f;
     if (live) {
+        if (sl == 0) {
+            s = net.b[0][p];
+            sabs = fabsf(s);
+        }
 #pragma unroll 4
         for (int j = sl; j < d; j += kSlicesY) {
-            const float c = A::mul_rn(W0t[(size_t)j * n1 + p], rb[j]);
-            R(j) = c;
-            R(WTile::cR(d) + j) = 0.f;
-            bd.add(c, 0.f);
+            const float wj = W0t[(size_t)j * n1 + p];
+            bd.add(A::mul_rn(wj, rb[j]), 0.f);
+            float p1, pe, tt, se;
+            two_prod<float>(wj, mb[j], p1, pe);
+            two_sum<float>(s, p1, tt, se);
+            s = tt;
+            e = A::fma_rn(wj, lb[j], e + (pe + se));
+            sabs = sabs + fabsf(p1);
         }
     }
     part[sl][lane] = bd;
+    cpart[0][sl][lane] = s;
+    cpart[1][sl][lane] = e;
+    cpart[2][sl][lane] = sabs;
     __syncthreads();
     if (sl == 0 && live) {
         RowBounds<float> t = part[0][lane];
         for (int y = 1; y < kSlicesY; ++y) t.merge(part[y][lane]);
-        // the constant W_1 m + b_1, error-free products and a compensated sum
-        const float bp = net.b[0][p];
-        float s = bp, e = 0.f, sabs = fabsf(bp);
-        for (int j = 0; j < d; ++j) {
-            const float wj = W0t[(size_t)j * n1 + p];
-            float p1, pe, tt, se;
-            two_prod<float>(wj, mh[b * d + j], p1, pe);
-            two_sum<float>(s, p1, tt, se);
+        // the constant W_1 m + b_1: the slices' partial pairs, in slice order
+        for (int y = 1; y < kSlicesY; ++y) {
+            float tt, se;
+            two_sum<float>(s, cpart[0][y][lane], tt, se);
             s = tt;
-            e = A::fma_rn(wj, ml[b * d + j], e + (pe + se));
-            sabs = sabs + fabsf(p1);
+            e = e + (cpart[1][y][lane] + se);
+            sabs = sabs + cpart[2][y][lane];
         }
         float chi, clo;
         two_sum<float>(s, e, chi, clo);
@@ -186,14 +203,12 @@ wide_init_kernel(const NetParams<float> net, const float *W0t, int NP, const flo
     __syncthreads();
     if (live) {
         const RelaxPlan<float> pl = plan[lane];
-        if (pl.kind != 0) {
-    #pragma unroll 4
+#pragma unroll 4
         for (int j = sl; j < d; j += kSlicesY) {
-                float c = R(j), r = R(WTile::cR(d) + j);
-                WTile::apply_plan(pl, c, r);
-                R(j) = c;
-                R(WTile::cR(d) + j) = r;
-            }
+            float c = pl.kind == 1 ? 0.f : A::mul_rn(W0t[(size_t)j * n1 + p], rb[j]), r = 0.f;
+            WTile::apply_plan(pl, c, r);
+            R(j) = c;
+            R(WTile::cR(d) + j) = r;
         }
         if (sl == 0) {
             R(WTile::cCh(d)) = pl.nh;
@@ -288,7 +303,7 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
     RowBounds<float> bd;
     bd.reset();
     if (live)
-#pragma unroll 4
+#pragma unroll 8
         for (int j = sl; j < d; j += kSlicesY) bd.add(R(j), R(WTile::cR(d) + j));
     part[sl][lane] = bd;
     __syncthreads();
@@ -310,9 +325,16 @@ wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, f
     __syncthreads();
     if (live) {
         const RelaxPlan<float> pl = plan[lane];
-        if (pl.kind != 0) {
-    #pragma unroll 4
-        for (int j = sl; j < d; j += kSlicesY) {
+        if (pl.kind == 1) {
+            // a constant row: zeros, nothing to read
+#pragma unroll 8
+            for (int j = sl; j < d; j += kSlicesY) {
+                R(j) = 0.f;
+                R(WTile::cR(d) + j) = 0.f;
+            }
+        } else if (pl.kind == 2) {
+#pragma unroll 8
+            for (int j = sl; j < d; j += kSlicesY) {
                 float c = R(j), r = R(WTile::cR(d) + j);
                 WTile::apply_plan(pl, c, r);
                 R(j) = c;
@@ -346,7 +368,7 @@ wide_final_kernel(const NetParams<float> net, int NP, float gcoef, float *C, flo
     RowBounds<float> bd;
     bd.reset();
     if (live)
-#pragma unroll 4
+#pragma unroll 8
         for (int j = sl; j < d; j += kSlicesY) bd.add(Rw(j), Rw(WTile::cR(d) + j));
     part[sl][lane] = bd;
     __syncthreads();
