@@ -100,7 +100,7 @@ __global__ void wide_box_kernel(const BoxSource src, int64_t base, int nb, int d
 
 // ---------------------------------------------------------------------------
 // Row kernels: a block is 32 rows (threadIdx.x) of one box (blockIdx.y) with
-// the d coefficients of each row split over 8 slices (threadIdx.y), so that a
+// the d coefficients of each row split over 16 slices (threadIdx.y), so that a
 // warp reads 32 consecutive neurons of one coefficient column.  The slices'
 // partial sums are merged in shared memory, one thread per row plans the
 // relaxation, and all slices apply it.
