@@ -344,8 +344,9 @@ typedef struct {
  * per group and step.  The step loop is captured once as a CUDA graph and
  * replayed while later calls keep the batch's shape (same widths, rows,
  * clauses and depths; weights, boxes and properties may change).  Problems
- * too wide for any tile are counted one by one on the wide path in the same
- * call, after the tiled ones.  results[i] receives problem i's count as
+ * too wide for any tile are counted on the wide path in the same call, after
+ * the tiled ones, four at a time (host threads, each with a helper context
+ * and stream of its own).  results[i] receives problem i's count as
  * slr_count would return it (device_ms is the time of the whole batch,
  * completion_ms the time from its start to the end of problem i's last level;
  * tile_boxes the problem's tile).

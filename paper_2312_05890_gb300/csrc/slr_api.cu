@@ -1,11 +1,13 @@
 // C ABI of the SLR counter: context, validation, device copies of the
 // network and the level-by-level driver of the count (Alg. 1, Sec. 3).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "slrcount.h"
@@ -95,7 +97,7 @@ struct slr_ctx {
     bool tc_ok = false;
     int64_t *near_list2 = nullptr;
     BatchState *batch = nullptr;
-    slr_ctx *wide_helper = nullptr;       // batched counts: problems too wide for a tile
+    std::vector<slr_ctx *> wide_helpers;  // batched counts: problems too wide for a tile (own streams)
     void *split_buf = nullptr;            // gradient split rule: set, dimension map, root gradient
     uint64_t dev_version = 0;             // bumped whenever the device images of the problem are rebuilt
     cudaGraphExec_t count_graph = nullptr;  // the tile path's level loop, captured once per configuration
@@ -1271,7 +1273,7 @@ int slr_destroy(slr_ctx *ctx) {
     cudaFree(ctx->wide_img);
     cudaFree(ctx->wide_buf);
     cudaFree(ctx->adj_scratch);
-    if (ctx->wide_helper) slr_destroy(ctx->wide_helper);
+    for (slr_ctx *h : ctx->wide_helpers) slr_destroy(h);
     cudaFree(ctx->split_buf);
     cudaFree(ctx->wadj_buf);
     cudaFree(ctx->approx_buf);
@@ -2823,32 +2825,81 @@ extern "C" int slr_count_batch(slr_ctx *ctx, int n, const slr_problem *problems,
         if ((rc = count_batch_tile(ctx, (int)sub.size(), sub.data(), res.data()))) return rc;
         for (size_t j = 0; j < tile.size(); ++j) results[tile[j]] = res[j];
     }
-    // wider problems: one wide-path count each, on a helper context sharing the stream
-    if (!ctx->wide_helper) {
-        if ((rc = slr_create(&ctx->wide_helper, ctx->device, ctx->stream)))
+    // wider problems: one wide-path count each, kWideWorkers at a time, each
+    // worker a host thread with a helper context and stream of its own (a
+    // wide count reads its level sizes on the host, so one problem alone
+    // leaves the GPU idle between its launches)
+    constexpr int kWideWorkers = 4;
+    const int K = std::min<int>(kWideWorkers, (int)wide.size());
+    while ((int)ctx->wide_helpers.size() < K) {
+        slr_ctx *h = nullptr;
+        if ((rc = slr_create(&h, ctx->device, nullptr)))
             return fail(ctx, rc, "wide helper context: %s", slr_last_error(nullptr));
+        ctx->wide_helpers.push_back(h);
     }
-    slr_ctx *h = ctx->wide_helper;
-    double done_ms = tile.empty() ? 0.0 : results[tile[0]].device_ms;
+    const double tile_ms = tile.empty() ? 0.0 : results[tile[0]].device_ms;
     slr_options o = ctx->opt;
     o.wide = 1;
     o.alpha_steps = 0;
     o.record_leaves = 0;
     o.tile_boxes = o.tile_threads = 0;
-    if ((rc = slr_set_options(h, &o))) return fail(ctx, rc, "problem batch: %s", slr_last_error(h));
-    for (int i : wide) {
-        const slr_problem &q = problems[i];
-        int R = 0;
-        for (int c = 0; c < q.n_clauses; ++c) R += q.rows_per_clause ? q.rows_per_clause[c] : 0;
-        if ((rc = slr_load_network(h, q.K, q.widths, q.W, q.b)) || (rc = slr_set_box(h, q.widths[0], q.lo, q.hi)) ||
-            (rc = slr_set_property(h, q.n_clauses, q.rows_per_clause, q.widths[q.K], q.C, q.e, q.strict)) ||
-            (rc = slr_count(h, q.depth, &results[i])))
-            return fail(ctx, rc, "problem %d: %s", i, slr_last_error(h));
-        done_ms += results[i].device_ms;
-        results[i].completion_ms = done_ms;
+    for (int w = 0; w < K; ++w)
+        if ((rc = slr_set_options(ctx->wide_helpers[w], &o)))
+            return fail(ctx, rc, "problem batch: %s", slr_last_error(ctx->wide_helpers[w]));
+    // the wide phase starts when the context stream's work is done
+    cudaEvent_t ev_start = nullptr;
+    std::vector<cudaEvent_t> ev_end(wide.size(), nullptr);
+    cudaError_t ce = cudaEventCreate(&ev_start);
+    for (size_t j = 0; j < wide.size() && ce == cudaSuccess; ++j) ce = cudaEventCreate(&ev_end[j]);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev_start, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(ev_start);
+    std::atomic<int> next{0};
+    std::vector<int> wrc(K, SLR_OK);
+    std::vector<std::string> wmsg(K);
+    auto worker = [&](int w) {
+        slr_ctx *h = ctx->wide_helpers[w];
+        cudaSetDevice(ctx->device);
+        for (int j = next.fetch_add(1); j < (int)wide.size(); j = next.fetch_add(1)) {
+            const int i = wide[j];
+            const slr_problem &q = problems[i];
+            int r = SLR_OK;
+            if ((r = slr_load_network(h, q.K, q.widths, q.W, q.b)) || (r = slr_set_box(h, q.widths[0], q.lo, q.hi)) ||
+                (r = slr_set_property(h, q.n_clauses, q.rows_per_clause, q.widths[q.K], q.C, q.e, q.strict)) ||
+                (r = slr_count(h, q.depth, &results[i]))) {
+                wrc[w] = r;
+                wmsg[w] = "problem " + std::to_string(i) + ": " + slr_last_error(h);
+                next.store((int)wide.size());   // the others stop at their next problem
+                return;
+            }
+            if (cudaEventRecord(ev_end[j], h->stream) != cudaSuccess || cudaEventSynchronize(ev_end[j]) != cudaSuccess) {
+                wrc[w] = SLR_ECUDA;
+                wmsg[w] = "problem " + std::to_string(i) + ": completion event";
+                next.store((int)wide.size());
+                return;
+            }
+        }
+    };
+    if (ce == cudaSuccess) {
+        std::vector<std::thread> th;
+        for (int w = 0; w < K; ++w) th.emplace_back(worker, w);
+        for (std::thread &t : th) t.join();
     }
+    double wide_ms = 0.0;
+    for (int w = 0; w < K && rc == SLR_OK && ce == cudaSuccess; ++w)
+        if (wrc[w] != SLR_OK) rc = fail(ctx, wrc[w], "%s", wmsg[w].c_str());
+    for (size_t j = 0; j < wide.size() && rc == SLR_OK && ce == cudaSuccess; ++j) {
+        float ms = 0.f;
+        ce = cudaEventElapsedTime(&ms, ev_start, ev_end[j]);
+        results[wide[j]].completion_ms = tile_ms + ms;
+        wide_ms = std::max(wide_ms, (double)ms);
+    }
+    for (cudaEvent_t e : ev_end)
+        if (e) cudaEventDestroy(e);
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (rc != SLR_OK) return rc;
+    if (ce != cudaSuccess) return fail(ctx, SLR_ECUDA, "batch of wide problems: %s", cudaGetErrorString(ce));
     // every result reports the whole batch's device time
-    for (int i = 0; i < n; ++i) results[i].device_ms = done_ms;
+    for (int i = 0; i < n; ++i) results[i].device_ms = tile_ms + wide_ms;
     return SLR_OK;
 }
 
