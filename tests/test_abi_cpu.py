@@ -82,3 +82,31 @@ def test_result_struct_matches_header_size(lib):
     assert sizes[1] == ctypes.sizeof(pkg.slr_options)
     assert sizes[2] == pkg.slr_result.device_ms.offset
     assert sizes[3] == pkg.slr_options.frontier_cap.offset
+
+
+def test_every_struct_field_matches_the_header(lib):
+    """Every field of every ctypes mirror sits at the header's offset, and each
+    struct has the header's size (the binding and include/slrcount.h agree)."""
+    import tempfile
+    import paper_2312_05890_gb300 as pkg
+    structs = [pkg.slr_options, pkg.slr_result, pkg.slr_approx_options, pkg.slr_approx_result, pkg.slr_problem]
+    lines = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in st._fields_:
+            lines.append(f'printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    src = ('#include <stdio.h>\n#include <stddef.h>\n#include "slrcount.h"\nint main(void){\n' +
+           "\n".join(lines) + "\nreturn 0;}\n")
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "t.c")
+        exe = os.path.join(td, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f in st._fields_:
+            assert int(got[f"{name}.{f[0]}"]) == getattr(st, f[0]).offset, (name, f[0])
