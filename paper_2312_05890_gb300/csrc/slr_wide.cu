@@ -285,68 +285,107 @@ __device__ __forceinline__ void wide_finish(const WideRow &R, const float *Kh, c
 }  // namespace
 
 // Hidden layer `layer` after its product: error, bounds, ReLU relaxation in place.
-__global__ void __launch_bounds__(kRowsX * kSlicesY)
+// A block is 128 rows of one box: each thread holds four neighbouring rows
+// (one float4 of every coefficient column: 512-byte accesses per warp) for
+// its eighth of the d columns; the slices' partial bounds are merged in
+// shared memory, one thread per row plans the relaxation, and every thread
+// applies its rows' plans, reading and writing a float4 only where a row
+// changes.  Rows from n to the next multiple of 4 lie inside the row stride
+// and are planned as zero rows (nothing reads them).
+constexpr int kH4X = 32, kH4Y = 8, kH4Rows = 4 * kH4X;
+
+__global__ void __launch_bounds__(kH4X * kH4Y, 2)
 wide_hidden_kernel(const NetParams<float> net, int layer, int NP, float gcoef, float *C, float *Rr, float *Ch,
                    float *Cl, const float *Kh, const float *Kl, const float *Ke, const float *alpha, int64_t alpha_ld,
                    int64_t base) {
-    using A = Arith<float>;
-    __shared__ RowBounds<float> part[kSlicesY][kRowsX];
-    __shared__ RelaxPlan<float> plan[kRowsX];
+    __shared__ RowBounds<float> part[kH4Y][kH4Rows];
+    __shared__ RelaxPlan<float> plan[kH4Rows];
     const int d = net.d;
     const int n = net.n[layer];
     const int n_in = net.n[layer - 1];
     const int lane = threadIdx.x, sl = threadIdx.y;
-    const int p = blockIdx.x * kRowsX + lane;
+    const int pb = blockIdx.x * kH4Rows;
+    const int p0 = pb + 4 * lane;
     const int64_t b = blockIdx.y;
-    const bool live = p < n;
-    const WideRow R{C, Rr, Ch, Cl, b, live ? p : 0, d, NP};
-    RowBounds<float> bd;
-    bd.reset();
-    if (live)
-#pragma unroll 8
-        for (int j = sl; j < d; j += kSlicesY) bd.add(R(j), R(WTile::cR(d) + j));
-    part[sl][lane] = bd;
-    __syncthreads();
-    if (sl == 0 && live) {
-        RowBounds<float> t = part[0][lane];
-        for (int y = 1; y < kSlicesY; ++y) t.merge(part[y][lane]);
-        float chi, clo, E;
-        wide_finish(R, Kh, Kl, Ke, NP, n_in, gcoef, chi, clo, E);
-        const float rd = R(WTile::cRd(d));
-        t.finish(chi, clo, rd);
-        const float *a_ptr = nullptr;
-        if (alpha != nullptr) {
-            int off = 0;
-            for (int j = 1; j < layer; ++j) off += net.n[j];
-            a_ptr = alpha + (base + b) * alpha_ld + off + p;
+    const bool any = p0 < n;
+    float *Cb = C + (size_t)b * d * NP + p0;
+    float *Rb = Rr + (size_t)b * (d + 3) * NP + p0;
+    RowBounds<float> bd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bd[u].reset();
+    if (any) {
+#pragma unroll 4
+        for (int j = sl; j < d; j += kH4Y) {
+            const float4 c = *reinterpret_cast<const float4 *>(Cb + (size_t)j * NP);
+            const float4 r = *reinterpret_cast<const float4 *>(Rb + (size_t)j * NP);
+            bd[0].add(c.x, r.x);
+            bd[1].add(c.y, r.y);
+            bd[2].add(c.z, r.z);
+            bd[3].add(c.w, r.w);
         }
-        plan[lane] = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, a_ptr, net.act[layer - 1]);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) part[sl][4 * lane + u] = bd[u];
     __syncthreads();
-    if (live) {
-        const RelaxPlan<float> pl = plan[lane];
-        if (pl.kind == 1) {
-            // a constant row: zeros, nothing to read
-#pragma unroll 8
-            for (int j = sl; j < d; j += kSlicesY) {
-                R(j) = 0.f;
-                R(WTile::cR(d) + j) = 0.f;
+    if (sl < kH4Rows / kH4X) {
+        const int rr = sl * kH4X + lane;
+        const int p = pb + rr;
+        RelaxPlan<float> pl;
+        pl.kind = 1;
+        pl.pp = pl.qq = 0.f;
+        pl.nh = pl.nl = pl.rd = pl.N = pl.E = 0.f;
+        if (p < n) {
+            const WideRow R{C, Rr, Ch, Cl, b, p, d, NP};
+            RowBounds<float> t = part[0][rr];
+            for (int y = 1; y < kH4Y; ++y) t.merge(part[y][rr]);
+            float chi, clo, E;
+            wide_finish(R, Kh, Kl, Ke, NP, n_in, gcoef, chi, clo, E);
+            const float rd = R(WTile::cRd(d));
+            t.finish(chi, clo, rd);
+            const float *a_ptr = nullptr;
+            if (alpha != nullptr) {
+                int off = 0;
+                for (int j = 1; j < layer; ++j) off += net.n[j];
+                a_ptr = alpha + (base + b) * alpha_ld + off + p;
             }
-        } else if (pl.kind == 2) {
-#pragma unroll 8
-            for (int j = sl; j < d; j += kSlicesY) {
-                float c = R(j), r = R(WTile::cR(d) + j);
-                WTile::apply_plan(pl, c, r);
-                R(j) = c;
-                R(WTile::cR(d) + j) = r;
-            }
-        }
-        if (sl == 0) {
+            pl = WTile::plan_row(t, d, net.relax_mode, chi, clo, rd, E, a_ptr, net.act[layer - 1]);
             R(WTile::cCh(d)) = pl.nh;
             R(WTile::cCl(d)) = pl.nl;
             R(WTile::cRd(d)) = pl.rd;
             R(WTile::cN(d)) = pl.N;
             R(WTile::cE(d)) = pl.E;
+        }
+        plan[rr] = pl;
+    }
+    __syncthreads();
+    if (any) {
+        RelaxPlan<float> pl[4];
+        bool keep = false, zero = false, mix = false;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            pl[u] = plan[4 * lane + u];
+            keep = keep || pl[u].kind == 0;
+            zero = zero || pl[u].kind == 1;
+            mix = mix || pl[u].kind == 2;
+        }
+        // a float4 is read when a row's values are needed (kept beside changed
+        // rows, or mixed by the plan) and written when some row changes
+        const bool load = mix || (keep && zero);
+        if (zero || mix) {
+#pragma unroll 4
+            for (int j = sl; j < d; j += kH4Y) {
+                float4 c = make_float4(0.f, 0.f, 0.f, 0.f), r = c;
+                if (load) {
+                    c = *reinterpret_cast<const float4 *>(Cb + (size_t)j * NP);
+                    r = *reinterpret_cast<const float4 *>(Rb + (size_t)j * NP);
+                }
+                WTile::apply_plan(pl[0], c.x, r.x);
+                WTile::apply_plan(pl[1], c.y, r.y);
+                WTile::apply_plan(pl[2], c.z, r.z);
+                WTile::apply_plan(pl[3], c.w, r.w);
+                *reinterpret_cast<float4 *>(Cb + (size_t)j * NP) = c;
+                *reinterpret_cast<float4 *>(Rb + (size_t)j * NP) = r;
+            }
         }
     }
 }
@@ -722,7 +761,7 @@ cudaError_t launch_wide_const(const NetParams<float> &net, int k, int nb, int NP
 cudaError_t launch_wide_hidden(const NetParams<float> &net, int layer, int nb, int NP, float gcoef, float *C, float *Rr,
                                float *Ch, float *Cl, const float *Kh, const float *Kl, const float *Ke,
                                const float *alpha, int64_t alpha_ld, int64_t base, cudaStream_t s) {
-    const dim3 grid((net.n[layer] + kRowsX - 1) / kRowsX, nb), block(kRowsX, kSlicesY);
+    const dim3 grid((net.n[layer] + kH4Rows - 1) / kH4Rows, nb), block(kH4X, kH4Y);
     wide_hidden_kernel<<<grid, block, 0, s>>>(net, layer, NP, gcoef, C, Rr, Ch, Cl, Kh, Kl, Ke, alpha, alpha_ld, base);
     return cudaGetLastError();
 }
