@@ -141,3 +141,43 @@ def test_the_bound_is_not_vacuous():
     rel = _check(w, x, 4)
     assert rel <= gam_ff(n)
     assert gam_ff(n) < 1e-4 * (n * 2.0 ** -24)
+
+
+def _slice_tree_constant(w, mh, ml, bias, slices):
+    """The wide path's layer-1 constant: each slice sums its share of
+    w_j (mh_j + ml_j) with exact products and TwoSum (bias in slice 0), then
+    the slices' pairs are added in slice order by TwoSum; returns hi + lo
+    exactly and sum |fl(w_j mh_j)| as the kernel accumulates it."""
+    n = len(w)
+    parts = []
+    for sl in range(slices):
+        s = F32(bias) if sl == 0 else F32(0)
+        e = F32(0)
+        a = abs(F32(bias)) if sl == 0 else F32(0)
+        for j in range(sl, n, slices):
+            s, e = ff_mac(w[j], mh[j], ml[j], s, e)
+            a = add(a, abs(mul(w[j], mh[j])))
+        parts.append((s, e, a))
+    s, e, a = parts[0]
+    for s1, e1, a1 in parts[1:]:
+        t, se = two_sum(s, s1)
+        s, e, a = t, add(e, add(e1, se)), add(a, a1)
+    hi, lo = two_sum(s, e)
+    return fr(hi) + fr(lo), fr(a)
+
+
+@pytest.mark.parametrize("d", [5, 64, 784])
+def test_layer1_constant_slice_tree_within_its_bound(d):
+    """2 gamma_{d+2}^2 (1 + gamma_d) sum |p_j| (the bound of the sequential
+    compensated chain) also holds for 16 slices merged by TwoSum."""
+    rng = np.random.default_rng(d)
+    w = rng.standard_normal(d).astype(np.float32)
+    m = rng.standard_normal(d)
+    mh = m.astype(np.float32)
+    ml = (m - mh.astype(np.float64)).astype(np.float32)
+    bias = F32(rng.standard_normal())
+    got, sabs = _slice_tree_constant(w, mh, ml, bias, 16)
+    exact = fr(bias) + sum(fr(wi) * (fr(hi) + fr(lo)) for wi, hi, lo in zip(w, mh, ml))
+    g = Fraction((d + 4) * 2.0 ** -24)       # gam<float>(d + 2) = (d + 4) u
+    bound = 2 * g * g * sabs * (1 + Fraction((d + 2) * 2.0 ** -24))
+    assert abs(got - exact) <= bound
