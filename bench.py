@@ -43,7 +43,7 @@ TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 / BF16 tensor rates of 
 # kernel source hashed below (profiles/slr_eval_f32_acas_D20.md: levels 18 and
 # 19, 8.56 and 8.29 B per box); reported as roofline.traffic only while the
 # kernel source is unchanged.
-TRAFFIC = {"source_sha": "d5b7cd9c51782dd7", "bytes_per_box": 8.4}
+TRAFFIC = {"source_sha": "45590470a99640c4", "bytes_per_box": 8.4}
 KERNEL_SOURCES = ["paper_2312_05890_gb300/csrc/slr_eval.cuh", "paper_2312_05890_gb300/csrc/slr_eval_f32.cu",
                   "paper_2312_05890_gb300/csrc/slr_device.cuh"]
 

@@ -370,29 +370,6 @@ struct EvalTile {
     static __device__ __forceinline__ int cE(int d) { return 2 * d + 3; }
     static __device__ __forceinline__ int cCl(int d) { return 2 * d + 4; }
 
-    // Constant of one output row as an exact-product, compensated sum:
-    // sum_i W[p][i] (hi_i + lo_i) + bias, returned as a normalised pair, and a
-    // bound of its rounding error (2 gamma^2 sum |terms|, Ogita-Rump-Oishi).
-    static __device__ __forceinline__ void const_dot(const Real *sW, int Mpad, int p, const Real *hcol,
-                                                     const Real *lcol, int n_in, int NS, Real bias,
-                                                     Real &chi, Real &clo, Real &err) {
-        Real s = bias, e = 0, sabs = A::abs(bias);
-        for (int i = 0; i < n_in; ++i) {
-            const Real w = sW[i * Mpad + p];
-            const Real h = hcol[i * NS];
-            const Real l = lcol[i * NS];
-            Real p1, pe, t, se;
-            two_prod<Real>(w, h, p1, pe);
-            two_sum<Real>(s, p1, t, se);
-            s = t;
-            e = A::fma_rn(w, l, e + (pe + se));
-            sabs = sabs + A::abs(p1);
-        }
-        two_sum<Real>(s, e, chi, clo);
-        const Real g = gam<Real>(n_in + 2);
-        err = A::mul_up(A::mul_up((Real)2 * g, g), A::mul_up(sabs, (Real)1 + gam<Real>(n_in)));
-    }
-
     // ---- layer 1: C = [W_1 diag(r) | W_1 m + b_1], R = 0 ------------------------
     template <class L>
     static __device__ void init_layer(const L &lay, const NetParams<Real> &net, const Real *sMh, const Real *sMl,
