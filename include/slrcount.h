@@ -128,7 +128,7 @@ typedef struct {
     int32_t recheck_pairs;  /* FP64 re-check (one CTA per tile): 1 (default) = in two stages, the first
                                with the hidden-layer products as float-float pairs on the FP32 units
                                (float64 state, constants and relaxation; the pairs' rounding bound,
-                               about 1e-10 relative, joins the error bound E), the second, with plain
+                               a few 1e-11 relative at 50 inputs, joins the error bound E), the second, with plain
                                FP64 products, on the boxes whose class the first left depending on E;
                                0 = plain FP64 products only.  Both give the same classes: a box is
                                decided by the first stage only when its bound is sound */
