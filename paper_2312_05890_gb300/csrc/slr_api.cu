@@ -1433,6 +1433,10 @@ struct ResumeState {
 // Levels t_first .. t_last of a count to depth D (t_first = 0 without a
 // resume state, t_last = D for a whole count); the result covers every level
 // counted so far.
+namespace {
+uint64_t fnv1a(uint64_t h, const void *p, size_t n);
+}  // namespace
+
 static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const ResumeState *rs) {
     int rc = check_ready(ctx);
     if (rc) return rc;
@@ -1670,19 +1674,27 @@ static int count_levels(slr_ctx *ctx, int D, slr_result *out, int t_last, const 
     };
     // The tile path reads no count on the host between levels: its level loop
     // is captured as a CUDA graph once per configuration and buffer set, and
-    // replayed (fewer launch gaps between the small kernels of a level).
+    // replayed (fewer launch gaps between the small kernels of a level).  The
+    // key holds everything the captured launches take by value (the network
+    // parameters' bytes, hashed, so that a problem uploaded again into the
+    // same buffers replays the graph), the buffers and the launch shapes;
+    // the values in those buffers are read when the graph runs.
     const bool graphable = !ctx->wide && !slopes && !grad_split && !rs && t_last == D;
     if (graphable) {
-        char key[512];
+        uint64_t hp = fnv1a(14695981039346656037ull, &ctx->nf, sizeof ctx->nf);
+        hp = fnv1a(hp, &ctx->nd, sizeof ctx->nd);
+        if (use_tc) hp = fnv1a(hp, &ctx->tcp, sizeof ctx->tcp);
+        char key[640];
         std::snprintf(key, sizeof key,
-                      "%d|%d|%d|%d|%d|%d|%d|%d|%llu|%p|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%lld|%lld|%d|%d|%d|%d|%d|%d",
+                      "%d|%d|%d|%d|%d|%d|%d|%d|%llu|%p|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%lld|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d",
                       D, leaves ? 1 : 0, recheck ? 1 : 0, use_tc ? 1 : 0, prof ? 1 : 0, ctx->opt.shard_count,
                       ctx->opt.shard_index, shard_g,
-                      (unsigned long long)ctx->dev_version, (void *)ctx->codes[0], (void *)ctx->codes[1],
+                      (unsigned long long)hp, (void *)ctx->codes[0], (void *)ctx->codes[1],
                       (void *)ctx->cls, (void *)ctx->ctr, (void *)ctx->near_list, (void *)ctx->near_list2,
                       (void *)ctx->leaf_codes, (void *)ctx->masks, (void *)ctx->root, (long long)ctx->cap,
                       (long long)ctx->near_cap, (long long)ctx->opt.leaf_cap, ctx->T32, ctx->NT32, ctx->T64,
-                      ctx->NT64, ctx->grid32, ctx->grid64);
+                      ctx->NT64, ctx->grid32, ctx->grid64, ctx->grid64c, ctx->opt.recheck_pairs,
+                      ctx->pairs_fit ? 1 : 0, use_tc ? ctx->T_tc : 0, use_tc ? ctx->grid_tc : 0);
         if (!ctx->count_graph || ctx->count_graph_key != key) {
             if (ctx->count_graph) cudaGraphExecDestroy(ctx->count_graph);
             ctx->count_graph = nullptr;
