@@ -407,7 +407,7 @@ int slr_count_noalloc(slr_ctx *ctx, int D, slr_result *out);
  * statistics of every level; device_ms, launches and kernel_ms cover the
  * resumed levels only).  The context must hold the same network, box,
  * property and result options (precision, relax_mode, fp64_recheck,
- * recheck_cluster, wide), else SLR_EINVAL; a blob that is truncated or not a
+ * recheck_cluster, recheck_pairs, wide), else SLR_EINVAL; a blob that is truncated or not a
  * checkpoint gives SLR_EINVAL.  The blob also records the FP32 tile (boxes
  * and threads per CTA) of the checkpointed levels: the resumed levels run
  * that tile, whatever the context's own choice, because the tile fixes the

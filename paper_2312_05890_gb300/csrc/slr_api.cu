@@ -1823,7 +1823,7 @@ int slr_count(slr_ctx *ctx, int D, slr_result *out) { return count_levels(ctx, D
 // ---- checkpoint / resume ----------------------------------------------------
 namespace {
 constexpr uint32_t kCkptMagic = 0x43524c53u;   // "SLRC"
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 // The FP32 tile (boxes and threads per CTA) is part of the state: small tiles
 // split a product's inputs over lanes, so the summation order, and with it
@@ -1862,8 +1862,8 @@ uint64_t problem_fingerprint(const slr_ctx *ctx) {
     h = fnv1a(h, ctx->e.data(), ctx->e.size() * sizeof(float));
     h = fnv1a(h, ctx->strict.data(), ctx->strict.size());
     h = fnv1a(h, ctx->act.data(), ctx->act.size() * sizeof(int));
-    const int32_t o[5] = {ctx->opt.precision, ctx->opt.relax_mode, ctx->opt.fp64_recheck, ctx->wide ? 1 : 0,
-                          ctx->opt.recheck_cluster};
+    const int32_t o[6] = {ctx->opt.precision, ctx->opt.relax_mode, ctx->opt.fp64_recheck, ctx->wide ? 1 : 0,
+                          ctx->opt.recheck_cluster, ctx->opt.recheck_pairs};
     return fnv1a(h, o, sizeof o);
 }
 

@@ -66,6 +66,10 @@ def test_checkpoint_errors(pkg):
             with pytest.raises(pkg.SlrError) as ei:
                 c.checkpoint(D, t)
             assert ei.value.code == -1
+        c.set_options(recheck_pairs=0)          # the one-stage re-check
+        with pytest.raises(pkg.SlrError) as ei:
+            c.resume(state)
+        assert ei.value.code == -1
         c.set_options(relax_mode=1)             # another result option
         with pytest.raises(pkg.SlrError) as ei:
             c.resume(state)
