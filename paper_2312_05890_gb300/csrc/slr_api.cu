@@ -99,7 +99,6 @@ struct slr_ctx {
     BatchState *batch = nullptr;
     std::vector<slr_ctx *> wide_helpers;  // batched counts: problems too wide for a tile (own streams)
     void *split_buf = nullptr;            // gradient split rule: set, dimension map, root gradient
-    uint64_t dev_version = 0;             // bumped whenever the device images of the problem are rebuilt
     cudaGraphExec_t count_graph = nullptr;  // the tile path's level loop, captured once per configuration
     std::string count_graph_key;
     int64_t count_graph_launches = 0;
@@ -994,7 +993,6 @@ int prepare_device(slr_ctx *ctx) {
         ctx->adj_gmem = true;
         ctx->adj_grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)2 * ctx->sm_count, ((size_t)4 << 30) / box));
         ctx->dev_dirty = false;
-        ++ctx->dev_version;
         return SLR_OK;
     }
     TileChoice best = c32[0];
@@ -1053,7 +1051,6 @@ int prepare_device(slr_ctx *ctx) {
         ctx->tc_ok = false;
     }
     ctx->dev_dirty = false;
-    ++ctx->dev_version;
     return SLR_OK;
 }
 
