@@ -130,3 +130,12 @@ def test_split_point_is_the_lower_median_of_the_violations():
         else:
             lo[i] = m
     assert np.array_equal(lo, t.leaf_lo) and np.array_equal(hi, t.leaf_hi)
+
+
+def test_ties_split_the_lowest_index():
+    """The widest side, ties to the lowest index: on the square root box of
+    the linear 2-D case the first split is along x_0, the second along x_1
+    (x_0 is then half as wide), and so on alternately."""
+    p, _, _, _ = _linear_case(1)
+    t = approx.one_trial(p.net, p.lo, p.hi, p.prop, 0, 6, 256, 0, seed=5)
+    assert t.dims == [0, 1, 0, 1, 0, 1][:len(t.dims)] and len(t.dims) >= 2
