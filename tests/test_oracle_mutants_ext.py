@@ -1,6 +1,7 @@
 """Planted mistakes in the oracle's later functions (CPU): the Moore-interval
-pass, the gradient split rule's decision weights, the approximate counter's
-leaf volume and split side, and the S-shaped relaxation.
+pass, the finite-difference gradients and their objective, the gradient
+split rule's decision weights and radius derivative, the approximate
+counter's leaf volume and split side, and the S-shaped relaxation.
 
 Each mutant is the oracle function's own source with one plausible slip (a
 dropped clamp, swapped interval ends, a flipped comparison, a dropped factor,
@@ -16,11 +17,13 @@ import pytest
 import oracle
 from oracle import approx as oapprox
 from oracle import counter as ocnt
+from oracle import grad as ograd
 from oracle import slr as oslr
 from oracle import split as osplit
 
 from . import pins
 from . import test_oracle_approx as tapprox
+from . import test_oracle_pins as topins
 from . import test_oracle_split as tsplit
 from . import test_oracle_sshaped as tsshaped
 
@@ -58,6 +61,19 @@ MUTANTS = [
     ("split_ties_to_highest_index", oapprox, "widest_side",
      "return int(np.argmax(w)), float(np.max(w))", "return int(len(w) - 1 - np.argmax(w[::-1])), float(np.max(w))",
      (oapprox,), tapprox.test_ties_split_the_lowest_index),
+    ("central_difference_over_h", ograd, "_central",
+     "g.flat[i] = (f(x0 + e) - f(x0 - e)) / (2 * h)", "g.flat[i] = (f(x0 + e) - f(x0 - e)) / h",
+     (ograd,), topins.test_box_gradient_of_an_affine_network_closed_form),
+    ("central_difference_sign", ograd, "_central",
+     "g.flat[i] = (f(x0 + e) - f(x0 - e)) / (2 * h)", "g.flat[i] = (f(x0 - e) - f(x0 + e)) / (2 * h)",
+     (ograd,), topins.test_default_slope_box_gradient_closed_form),
+    ("objective_weights_on_the_other_bound", ograd, "objective",
+     "np.dot(w_hi, rhi[0]) + np.dot(w_lo, rlo[0])", "np.dot(w_hi, rlo[0]) + np.dot(w_lo, rhi[0])",
+     (oracle, ograd, osplit), topins.test_slope_gradient_hand_worked),
+    ("radius_stencil_shifts_the_box", osplit, "radius_gradient",
+     "objective(net, lo - s * e, hi + s * e, prop, None, w_hi, w_lo)",
+     "objective(net, lo + s * e, hi + s * e, prop, None, w_hi, w_lo)",
+     (oracle, osplit), lambda: tsplit.test_radius_gradient_of_an_affine_map_is_abs_weight(0)),
     ("straddling_slope_max", oslr, "_relax_s",
      "lam = np.minimum(act_slope(name, l), act_slope(name, u))",
      "lam = np.maximum(act_slope(name, l), act_slope(name, u))",
