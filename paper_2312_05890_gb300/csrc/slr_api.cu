@@ -1,5 +1,5 @@
 // C ABI of the SLR counter: context, validation, device copies of the
-// network and the level-by-level driver of the count (Alg. 1, Sec. 3).
+// network and the level loop of the count (Alg. 1, Sec. 3).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
